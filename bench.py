@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Throughput of the two-detector AI-ensemble detector (arXiv:2201.11133) on
+one hour of 4096 Hz Hanford + Livingston strain.
+
+One step = the whole inference hot path over the hour: ensemble forward of 4
+models (3 stacks x dilations 1..512 = 30 layers, R = 64, S = 128, Hc = 256) on
+every 1 s window at 0.5 s stride (7199 windows), then peak finding and
+ensemble coincidence on the device.  Metric: strain-seconds (two detectors,
+whole ensemble) processed per wall-second.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workload  # noqa: E402
+
+FS = workload.FS
+WINDOW, STRIDE = workload.WINDOW, workload.STRIDE
+HOUR = 3600
+METRIC = "strain-sec/s (2-det, ensemble)"
+UNIT = "strain-s/s"
+PREC_NAMES = {"fp32": 0, "bf16": 1, "fp8": 2}
+L2_BYTES = 129 * 1024 * 1024
+
+
+def flops_per_sample(cfg) -> int:
+    """Algorithmic FLOPs per output sample of one model (both branches and the head)."""
+    R, S, Hc, L = cfg["r_ch"], cfg["s_ch"], cfg["head_ch"], workload.n_layers(cfg)
+    per_layer = 2 * (2 * R) * (2 * R) + 2 * (R + S) * R
+    return 2 * (2 * R + L * per_layer) + 2 * (2 * S) * Hc + 2 * Hc
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel: str, src_file: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when
+    the kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e:
+        return None
+    sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
+    if e.get("src_sha") != sha:
+        return None
+    return e.get("bytes_per_launch")
+
+
+def make_inputs(seed: int):
+    n = HOUR * FS
+    sh, sl, mergers = workload.stream(n, seed=seed, n_inj=200, snr_range=(6.0, 20.0), mc_range=(5.0, 30.0))
+    return sh, sl, mergers
+
+
+# ---------------------------------------------------------------------------
+# Reference arm / CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_sample(sh, sl, cfg, wb, n_win: int):
+    """Oracle forward + triggers on the first n_win windows; returns (strain-s credited, seconds, threads)."""
+    import oracle
+    n_s = (n_win - 1) * STRIDE + WINDOW
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    prob = oracle.forward_stream(cfg, wb, sh[:n_s], sl[:n_s], WINDOW, STRIDE, nthreads=threads)
+    oracle.triggers(prob.astype(np.float32), WINDOW, STRIDE, 0.5, 2048.0, 2048)
+    dt = time.perf_counter() - t0
+    return n_win * STRIDE / FS, dt, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = workload.config("ensemble")
+    wb = workload.init_weights(cfg, seed=3000)
+    sh, sl, _ = make_inputs(1000)
+    import oracle
+    oracle.build()
+    n_win = args.ref_windows
+    for _ in range(args.warmup):
+        oracle_sample(sh, sl, cfg, wb, 1)
+    secs, tot = 0.0, 0.0
+    threads = 1
+    for _ in range(args.steps):
+        s, dt, threads = oracle_sample(sh, sl, cfg, wb, n_win)
+        secs += s
+        tot += dt
+    v = secs / tot
+    sample = (f"{n_win} windows (1 s at 0.5 s stride) x 4 models per step, forward + triggers, credited "
+              f"{n_win} x 0.5 s of strain")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "1h-2det-4model-30layer", "window": WINDOW, "stride": STRIDE,
+                   "sample_windows": n_win},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gwe", choices=["gwe", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("GWE_BENCH_PRECISION", "fp32"), choices=list(PREC_NAMES))
+    ap.add_argument("--ref-windows", type=int, default=2)
+    ap.add_argument("--cpu-windows", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2201_11133_gb300 as gwe
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    gwe.build()
+    cfg = workload.config("ensemble")
+    wb = workload.init_weights(cfg, seed=3000)
+    prec = PREC_NAMES[args.precision]
+    model = gwe.Model(cfg, wb, prec)
+    sh, sl, mergers = make_inputs(1000 + 7 * rank)      # each rank its own hour (weak scaling)
+    n = sh.shape[0]
+    nw = gwe.gwe_n_windows(n, WINDOW, STRIDE)
+    H = torch.from_numpy(sh).to(dev)
+    L = torch.from_numpy(sl).to(dev)
+    out = torch.empty((1, cfg["n_models"], nw, WINDOW), dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # trigger threshold: the 99.9th percentile of one forward's probabilities (fixed before timing)
+    model.forward(H, L, WINDOW, STRIDE, out=out)
+    torch.cuda.synchronize()
+    thr = float(torch.quantile(out[0, 0, :, ::97].reshape(-1).float(), 0.999).item())
+    min_width, coinc = 2048.0, 2048
+
+    def step(h, l_):
+        gwe.gwe_forward(model.handle, h, l_, n, WINDOW, STRIDE, None, out, stream)
+        return gwe.gwe_triggers(out, cfg["n_models"], 1, nw, WINDOW, STRIDE, thr, min_width, coinc, flags=0,
+                                stream=stream)
+
+    for _ in range(args.warmup):
+        step(H, L)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    gwe.gwe_profile_enable(True)
+    launches0 = gwe.load().gwe_launch_count()
+    times = []
+    n_trig = 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)                                  # evict L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        recs = step(H, L)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        n_trig = len(recs)
+    launches = gwe.load().gwe_launch_count() - launches0
+    prof = gwe.gwe_profile_read()
+    gwe.gwe_profile_enable(False)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    strain_s = n / FS
+    value = world * strain_s * args.steps / (total_ms / 1000.0)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hH = torch.from_numpy(sh).pin_memory()
+        hL = torch.from_numpy(sl).pin_memory()
+        dH = torch.empty_like(H)
+        dL = torch.empty_like(L)
+        e2e_steps = max(1, min(args.steps, 3))
+        t_tot = 0.0
+        d2h = 0
+        for _ in range(e2e_steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            t0 = time.perf_counter()
+            dH.copy_(hH, non_blocking=True)
+            dL.copy_(hL, non_blocking=True)
+            recs = step(dH, dL)            # trigger records come back to host memory
+            torch.cuda.synchronize()
+            t_tot += time.perf_counter() - t0
+            d2h = recs.nbytes + 8
+        if dist:
+            t = torch.tensor([t_tot], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_tot = float(t.item())
+        e2e = {"value": world * strain_s * e2e_steps / t_tot, "unit": UNIT,
+               "h2d_bytes_per_step": int(hH.nbytes + hL.nbytes), "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel
+    peaks, peak_kind = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
+    roof = None
+    if dom:
+        kname, (kms, kn) = dom
+        fps = flops_per_sample(cfg)
+        per_layer = 2 * (2 * cfg["r_ch"]) ** 2 + 2 * (cfg["r_ch"] + cfg["s_ch"]) * cfg["r_ch"]
+        if kname == "k_fp32_layer":
+            # one launch = one layer over 2 branches x all windows of a chunk: all windows of the step
+            flops_step = cfg["n_models"] * nw * WINDOW * 2 * workload.n_layers(cfg) * per_layer
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            bound, unit, src = "alu", "TFLOP/s", "fp32_path.cu"
+        else:
+            flops_step = cfg["n_models"] * nw * WINDOW * fps
+            peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == 2 else 1.0)
+            bound, unit, src = "tensor", "TFLOP/s", "branch_tc.cu"
+        flops_launch = flops_step * args.steps / kn
+        achieved = flops_launch / (kms / kn / 1000.0) / 1e12
+        src_path = os.path.join(ROOT, "paper_2201_11133_gb300", "csrc", src)
+        traffic = traffic_for(kname, src_path) if os.path.exists(src_path) else None
+        roof = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "peak_source": f"of {peak_kind}",
+                "traffic": traffic, "launches": kn, "kernel_ms_per_step": kms / args.steps,
+                "flops_per_launch": flops_launch}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        s, dt, threads = oracle_sample(sh, sl, cfg, wb, args.cpu_windows)
+        cpu = {"value": s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {args.cpu_windows} windows x 4 models, FP64 forward + triggers, "
+                         f"{dt:.1f} s on {threads} host threads, credited {args.cpu_windows} x 0.5 s of strain"}
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec], "data": "synthetic",
+        "config": {"workload": "1h-2det-4model-30layer", "n_samples_per_detector": n, "window": WINDOW,
+                   "stride": STRIDE, "n_windows": nw, "models": cfg["n_models"], "layers": workload.n_layers(cfg),
+                   "r_ch": cfg["r_ch"], "s_ch": cfg["s_ch"], "head_ch": cfg["head_ch"],
+                   "precision": args.precision, "injections": len(mergers), "trigger_thr": thr,
+                   "l2": "flushed before every timed step (256 MiB write)", "triggers_last_step": n_trig},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                    for k, v in prof.items()},
+    }
+    print(json.dumps(res), flush=True)
+    model.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * gwe.h — C ABI of libgwe, the GB300 (sm_103a) implementation of the
+ * inference and training hot path of the two-detector gravitational-wave
+ * detector ensemble of arXiv:2201.11133 ("Inference-optimized AI and HPC for
+ * gravitational wave detection at scale").
+ *
+ * The method (paper, section "Materials and Methods", paragraphs "AI
+ * architecture" and "AI ensemble construction", caption of Fig. 1):
+ *   - two WaveNet-style branches, one per detector (Hanford H1, Livingston L1),
+ *     each a stack of dilated causal convolutions (kernel 2, dilation 2^j) with
+ *     a gated tanh*sigmoid activation, residual and skip connections;
+ *   - the two branch outputs are concatenated and fed to a pair of 1x1
+ *     convolutions whose sigmoid output is a per-time-step probability that
+ *     the input contains a waveform;
+ *   - an ensemble of models with the same architecture and different random
+ *     initialisation;
+ *   - the probabilities of each model are searched with find_peaks (height
+ *     threshold, width >= 0.5 s), and a trigger is kept when all models of the
+ *     ensemble report one within 0.5 s (section "Event Detection");
+ *   - background is estimated by time-sliding one detector against the other
+ *     (section "Statistical Analysis").
+ * Layer counts and widths are not stated in the paper; the caller chooses them
+ * in gwe_model_config.
+ *
+ * Conventions shared by every call:
+ *   - Pointers documented as "device" are CUDA device pointers owned by the
+ *     caller; pointers documented as "host" are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated otherwise.
+ *   - Argument errors are detected before any launch and return GWE_ERR_ARG.
+ *     A CUDA error returns GWE_ERR_CUDA.  gwe_last_error() returns a
+ *     thread-local description of the most recent failure.
+ *   - No call falls back to the CPU: when no suitable GPU is present the call
+ *     returns GWE_ERR_CUDA.
+ *
+ * Weight blob (FP32, one blob of gwe_param_count() floats per model, models
+ * contiguous), in order:
+ *   for branch b in {H, L}:
+ *     w_in[R], b_in[R]                         input 1x1 conv (1 -> R)
+ *     for layer l in 0 .. stacks*layers_per_stack-1, dilation 2^(l mod layers_per_stack):
+ *       w_conv[2R][kernel][R]   (out, tap, in): tap kernel-1 multiplies x[t],
+ *                               tap 0 the most lagged sample x[t-(kernel-1)d]
+ *       b_conv[2R]              outputs 0..R-1 feed tanh, R..2R-1 the sigmoid gate
+ *       w_res[R][R], b_res[R]   residual 1x1 conv (out, in)
+ *       w_skip[S][R], b_skip[S] skip 1x1 conv (out, in)
+ *   w_h1[Hc][2S], b_h1[Hc]      head conv 1 on ReLU([skip_H ; skip_L])
+ *   w_h2[Hc],     b_h2[1]       head conv 2 on ReLU(conv 1) -> logit
+ */
+#ifndef GWE_H
+#define GWE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gwe_model gwe_model;   /* opaque; owns device weights and workspace */
+
+typedef enum {
+    GWE_OK = 0,
+    GWE_ERR_ARG = 1,          /* invalid argument or shape */
+    GWE_ERR_CUDA = 2,         /* CUDA runtime / driver error, or no usable GPU */
+    GWE_ERR_OOM = 3,          /* device allocation failed */
+    GWE_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    GWE_ERR_UNSUPPORTED = 5,  /* configuration not implemented for this precision */
+    GWE_ERR_CAPACITY = 6      /* output buffer too small (count still reported) */
+} gwe_status;
+
+typedef enum {
+    GWE_FP32 = 0,   /* FP32 SIMT path, accurate tanhf/expf */
+    GWE_BF16 = 1,   /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
+    GWE_FP8 = 2     /* FP8 E4M3 operands with per-channel scales, FP32 accumulate */
+} gwe_precision;
+
+typedef struct {
+    int n_models;          /* ensemble size (paper: 4) */
+    int stacks;            /* number of dilation stacks */
+    int layers_per_stack;  /* dilations 1, 2, ..., 2^(layers_per_stack-1) */
+    int kernel;            /* convolution kernel size (only 2 is implemented) */
+    int r_ch;              /* residual channels R */
+    int s_ch;              /* skip channels S */
+    int head_ch;           /* head hidden channels Hc */
+} gwe_model_config;
+
+/* One peak or ensemble trigger (section "Event Detection"). */
+typedef struct {
+    int64_t index;       /* sample index in the stitched series (Hanford time) */
+    int32_t slide;       /* ordinal of the time slide (0 when no slides) */
+    int32_t model;       /* model index, or -1 for an ensemble trigger */
+    double height;       /* probability at the peak (model 0's peak for ensemble triggers) */
+    double prominence;   /* prominence of that peak */
+    double width;        /* width at half prominence, in samples */
+} gwe_trigger;
+
+/* Parameters per model of a configuration (layout above); -1 if invalid. */
+int64_t gwe_param_count(const gwe_model_config *cfg);
+
+/* Number of windows of length `window` at `stride` in n_samples (tail dropped). */
+int64_t gwe_n_windows(int64_t n_samples, int window, int stride);
+
+/*
+ * Create a model handle on the current CUDA device.
+ *   cfg           configuration (copied).
+ *   host_weights  host, FP32, n_models * gwe_param_count(cfg) floats, layout above
+ *                 (copied; the caller keeps ownership).
+ *   precision     gwe_precision of the forward path; the FP32 copy is always kept
+ *                 (for gwe_backward and the FP32 path).
+ *   out           receives the handle; release with gwe_model_destroy.
+ * Returns GWE_ERR_UNSUPPORTED when kernel != 2 or when the precision does not
+ * support the channel counts.
+ */
+gwe_status gwe_model_create(const gwe_model_config *cfg, const float *host_weights, int precision,
+                            gwe_model **out);
+
+/* Replace the weights of an existing handle (host FP32 blob, same layout);
+ * derived low-precision copies are rebuilt.  Synchronous. */
+gwe_status gwe_model_set_weights(gwe_model *model, const float *host_weights);
+
+void gwe_model_destroy(gwe_model *model);
+
+/*
+ * Ensemble forward over one segment of two-detector whitened strain
+ * (section "Materials and Methods"; inference batch layout (batch, 4096, 2)
+ * -> (batch, 4096, 1) of paragraph "Optimization with NVIDIA TensorRT").
+ *   strain_H, strain_L  device, FP32, n_samples each.
+ *   window, stride      window w covers samples [w*stride, w*stride + window);
+ *                       n_windows = gwe_n_windows(n_samples, window, stride);
+ *                       each window is an independent input with causal zero
+ *                       padding at its start.
+ *   slides              host, n_slides offsets in windows, or NULL / n_slides = 0
+ *                       for zero lag only.  For slide k, Hanford window w is
+ *                       paired with Livingston window (w + k) mod n_windows
+ *                       (section "Statistical Analysis").
+ *   out_prob            device, FP32 [max(n_slides,1)][n_models][n_windows][window],
+ *                       per-sample probability of each model.
+ * Uses the handle's precision.  Returns GWE_ERR_ARG if window <= 0, stride <= 0
+ * or n_samples < window.
+ */
+gwe_status gwe_forward(gwe_model *model, const float *strain_H, const float *strain_L, int64_t n_samples,
+                       int window, int stride, const int32_t *slides, int n_slides, float *out_prob,
+                       void *stream);
+
+/*
+ * As gwe_forward for explicit windows (no slides), returning logits instead of
+ * probabilities: x_H, x_L device FP32 [batch][window]; out_logit device FP32
+ * [n_models][batch][window].  Used by the autograd wrapper (BCE on logits).
+ */
+gwe_status gwe_forward_logits(gwe_model *model, const float *x_H, const float *x_L, int batch, int window,
+                              float *out_logit, void *stream);
+
+/*
+ * Backward pass of one model (training; paper paragraph "AI ensemble
+ * construction": per-time-step labels, BCE on logits).
+ *   model_index  which ensemble member.
+ *   x_H, x_L     device FP32 [batch][window] inputs of the forward.
+ *   dlogit       device FP32 [batch][window], dLoss/dlogit.
+ *   grad_weights device FP32 [gwe_param_count], overwritten with dLoss/dweights
+ *                (summed over the batch), blob layout.
+ *   grad_H, grad_L device FP32 [batch][window] dLoss/dstrain, or NULL.
+ * Activations are recomputed from the inputs, stack by stack.  Uses the FP32
+ * weights unless the handle's precision is GWE_BF16 (BF16 operands, FP32
+ * accumulation and FP32 master gradients).
+ */
+gwe_status gwe_backward(gwe_model *model, int model_index, const float *x_H, const float *x_L, int batch,
+                        int window, const float *dlogit, float *grad_weights, float *grad_H, float *grad_L,
+                        void *stream);
+
+/* Flags of gwe_triggers. */
+#define GWE_TRIG_PER_MODEL 1   /* also return every model's kept peaks (model >= 0) */
+
+/*
+ * Peak finding and ensemble coincidence on the device (paper paragraph "AI
+ * ensemble construction": find_peaks; section "Event Detection": all models
+ * coincident within 0.5 s; section "Statistical Analysis": ROC threshold and
+ * width >= 0.5 s).
+ *   prob         device FP32 [n_slides][n_models][n_windows][window] as written by
+ *                gwe_forward.
+ *   Each (slide, model) series is stitched: window 0 gives samples [0, window),
+ *   every later window w its last `stride` samples.  Peaks follow SciPy's
+ *   find_peaks(x, height=height_thr, width=min_width) semantics (rel_height 0.5,
+ *   no window limit), bit-exact for identical probabilities.  An ensemble
+ *   trigger is a model-0 peak p0 for which every other model has a peak such
+ *   that max - min of the chosen indices and p0 is <= coinc samples.
+ *   out          host array of `cap` records, sorted by (slide, model, index);
+ *                ensemble records have model = -1 and follow the per-model ones
+ *                of the same slide.
+ *   n_out        host, receives the total number of records (may exceed cap, in
+ *                which case GWE_ERR_CAPACITY is returned and `cap` records written).
+ * Synchronises `stream` before returning.
+ */
+gwe_status gwe_triggers(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,
+                        int stride, float height_thr, double min_width, int64_t coinc, int flags,
+                        gwe_trigger *out, int64_t cap, int64_t *n_out, void *stream);
+
+/*
+ * Whitening front end (paper section "Data curation": the strain is whitened
+ * with power spectral densities estimated from the data, then normalised to
+ * unit standard deviation).  Welch PSD with a Hann window, segments of
+ * seg_len samples at 50 % overlap, accumulated in FP64; the strain spectrum
+ * is divided by sqrt(fs * PSD / 2) (PSD interpolated linearly onto the data's
+ * frequency grid), zeroed below 15 Hz, transformed back and scaled to unit
+ * standard deviation.
+ *   strain   device FP32 [n] (one detector).
+ *   n        samples; must be >= seg_len.
+ *   fs       sample rate in Hz.
+ *   seg_len  Welch segment length, a power of two (16384 = 4 s at 4096 Hz).
+ *   flags    0.
+ *   out      device FP32 [n] whitened strain (may not alias strain).
+ */
+gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream);
+
+/*
+ * Per-kernel device timing.  gwe_profile_enable(1) clears the accumulators and
+ * makes the library record a pair of CUDA events on the launch stream around
+ * each of its main kernel launches; gwe_profile_enable(0) stops it.
+ * gwe_profile_read(i, ...) synchronises on the recorded events of the i-th
+ * kernel name and returns its name (copied into `name`, at most name_cap
+ * bytes including the terminator), the summed device time in milliseconds and
+ * the number of launches; GWE_ERR_ARG when i is out of range.  Host-side only;
+ * the paper has no counterpart (it is the measurement harness).
+ */
+gwe_status gwe_profile_enable(int on);
+gwe_status gwe_profile_read(int idx, char *name, int name_cap, double *total_ms, int64_t *launches);
+
+/* Total number of kernels this library has launched in the process (all calls). */
+int64_t gwe_launch_count(void);
+
+/* Thread-local description of the last error ("" if none). */
+const char *gwe_last_error(void);
+
+/* Library version string. */
+const char *gwe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWE_H */

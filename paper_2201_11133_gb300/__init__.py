@@ -1,0 +1,271 @@
+"""Python binding of libgwe, the GB300 (sm_103a) two-detector gravitational-wave
+ensemble detector of arXiv:2201.11133.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library's kernels.  The functions carry the C-ABI names declared in
+``include/gwe.h``; device buffers are passed as torch CUDA tensors (their
+``data_ptr()``), host buffers as numpy arrays.  There is no CPU fallback: if
+the library is missing or no GB300 is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "GWE_FP32", "GWE_BF16", "GWE_FP8", "GweError", "load", "build",
+    "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_destroy",
+    "gwe_forward", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
+    "gwe_version", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
+]
+
+GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
+GWE_TRIG_PER_MODEL = 1
+_STATUS = {0: "GWE_OK", 1: "GWE_ERR_ARG", 2: "GWE_ERR_CUDA", 3: "GWE_ERR_OOM", 4: "GWE_ERR_TIMEOUT",
+           5: "GWE_ERR_UNSUPPORTED", 6: "GWE_ERR_CAPACITY"}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class GweError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_models", ctypes.c_int), ("stacks", ctypes.c_int), ("layers_per_stack", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("r_ch", ctypes.c_int), ("s_ch", ctypes.c_int),
+                ("head_ch", ctypes.c_int)]
+
+
+class _Trigger(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int64), ("slide", ctypes.c_int32), ("model", ctypes.c_int32),
+                ("height", ctypes.c_double), ("prominence", ctypes.c_double), ("width", ctypes.c_double)]
+
+
+TRIGGER_DTYPE = np.dtype([("index", np.int64), ("slide", np.int32), ("model", np.int32),
+                          ("height", np.float64), ("prominence", np.float64), ("width", np.float64)])
+assert TRIGGER_DTYPE.itemsize == ctypes.sizeof(_Trigger)
+
+
+def build(force: bool = False) -> str:
+    """Compile libgwe.so in-tree for sm_103a (nvcc); returns its path."""
+    return _build.build(force=force)
+
+
+def load():
+    """Load libgwe.so (built in-tree); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgwe.so not built ({path}); call paper_2201_11133_gb300.build() first")
+        lib = ctypes.CDLL(path)
+        P, I, I64, F, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+        sig = {
+            "gwe_param_count": (I64, [P]),
+            "gwe_n_windows": (I64, [I64, I, I]),
+            "gwe_model_create": (I, [P, P, I, P]),
+            "gwe_model_set_weights": (I, [P, P]),
+            "gwe_model_destroy": (None, [P]),
+            "gwe_forward": (I, [P, P, P, I64, I, I, P, I, P, P]),
+            "gwe_forward_logits": (I, [P, P, P, I, I, P, P]),
+            "gwe_backward": (I, [P, I, P, P, I, I, P, P, P, P, P]),
+            "gwe_triggers": (I, [P, I, I, I64, I, I, F, D, I64, I, P, I64, P, P]),
+            "gwe_whiten": (I, [P, I64, D, I, I, P, P]),
+            "gwe_profile_enable": (I, [I]),
+            "gwe_profile_read": (I, [I, P, I, P, P]),
+            "gwe_last_error": (ctypes.c_char_p, []),
+            "gwe_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise GweError(status, where, load().gwe_last_error().decode())
+
+
+def _cfg(cfg) -> _Config:
+    return _Config(int(cfg["n_models"]), int(cfg["stacks"]), int(cfg["layers_per_stack"]), int(cfg["kernel"]),
+                   int(cfg["r_ch"]), int(cfg["s_ch"]), int(cfg["head_ch"]))
+
+
+def _dptr(t) -> int:
+    """Device pointer of a CUDA tensor (or 0 for None)."""
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def gwe_version() -> str:
+    return load().gwe_version().decode()
+
+
+def gwe_last_error() -> str:
+    return load().gwe_last_error().decode()
+
+
+def gwe_param_count(cfg) -> int:
+    c = _cfg(cfg)
+    return int(load().gwe_param_count(ctypes.byref(c)))
+
+
+def gwe_n_windows(n_samples: int, window: int, stride: int) -> int:
+    return int(load().gwe_n_windows(int(n_samples), int(window), int(stride)))
+
+
+def gwe_model_create(cfg, host_weights: np.ndarray, precision: int = GWE_FP32) -> int:
+    """Create a model handle on the current device from an FP32 host blob [n_models, P]."""
+    lib = load()
+    c = _cfg(cfg)
+    w = np.ascontiguousarray(host_weights, dtype=np.float32)
+    expect = int(cfg["n_models"]) * gwe_param_count(cfg)
+    if w.size != expect:
+        raise ValueError(f"weights have {w.size} floats, expected {expect}")
+    h = ctypes.c_void_p()
+    _check(lib.gwe_model_create(ctypes.byref(c), w.ctypes.data, int(precision), ctypes.byref(h)),
+           "gwe_model_create")
+    return h.value
+
+
+def gwe_model_set_weights(model: int, host_weights: np.ndarray) -> None:
+    w = np.ascontiguousarray(host_weights, dtype=np.float32)
+    _check(load().gwe_model_set_weights(model, w.ctypes.data), "gwe_model_set_weights")
+
+
+def gwe_model_destroy(model: int) -> None:
+    if model:
+        load().gwe_model_destroy(model)
+
+
+def gwe_forward(model: int, strain_H, strain_L, n_samples: int, window: int, stride: int, slides,
+                out_prob, stream=None) -> None:
+    """Ensemble forward over one segment; out_prob [max(n_slides,1), n_models, n_windows, window] (device)."""
+    if slides is None or len(slides) == 0:
+        sl = None
+        ns = 0
+    else:
+        sl = np.ascontiguousarray(slides, dtype=np.int32)
+        ns = int(sl.shape[0])
+    _check(load().gwe_forward(model, _dptr(strain_H), _dptr(strain_L), int(n_samples), int(window), int(stride),
+                              sl.ctypes.data if sl is not None else None, ns, _dptr(out_prob), _stream(stream)),
+           "gwe_forward")
+
+
+def gwe_forward_logits(model: int, x_H, x_L, batch: int, window: int, out_logit, stream=None) -> None:
+    """Logits [n_models, batch, window] for explicit windows x_H, x_L [batch, window] (device)."""
+    _check(load().gwe_forward_logits(model, _dptr(x_H), _dptr(x_L), int(batch), int(window), _dptr(out_logit),
+                                     _stream(stream)), "gwe_forward_logits")
+
+
+def gwe_backward(model: int, model_index: int, x_H, x_L, batch: int, window: int, dlogit, grad_weights,
+                 grad_H=None, grad_L=None, stream=None) -> None:
+    _check(load().gwe_backward(model, int(model_index), _dptr(x_H), _dptr(x_L), int(batch), int(window),
+                               _dptr(dlogit), _dptr(grad_weights), _dptr(grad_H), _dptr(grad_L), _stream(stream)),
+           "gwe_backward")
+
+
+def gwe_triggers(prob, n_models: int, n_slides: int, n_windows: int, window: int, stride: int, height_thr: float,
+                 min_width: float, coinc: int, flags: int = GWE_TRIG_PER_MODEL, cap: int = 1 << 20,
+                 stream=None) -> np.ndarray:
+    """Peaks and ensemble triggers (structured array of TRIGGER_DTYPE records)."""
+    lib = load()
+    out = np.zeros(max(1, int(cap)), dtype=TRIGGER_DTYPE)
+    n_out = ctypes.c_int64(0)
+    st = lib.gwe_triggers(_dptr(prob), int(n_models), int(n_slides), int(n_windows), int(window), int(stride),
+                          float(height_thr), float(min_width), int(coinc), int(flags), out.ctypes.data, int(cap),
+                          ctypes.byref(n_out), _stream(stream))
+    _check(st, "gwe_triggers")
+    return out[:n_out.value].copy()
+
+
+def gwe_whiten(strain, n: int, fs: float, seg_len: int, out, flags: int = 0, stream=None) -> None:
+    _check(load().gwe_whiten(_dptr(strain), int(n), float(fs), int(seg_len), int(flags), _dptr(out),
+                             _stream(stream)), "gwe_whiten")
+
+
+def gwe_profile_enable(on: bool = True) -> None:
+    _check(load().gwe_profile_enable(1 if on else 0), "gwe_profile_enable")
+
+
+def gwe_profile_read() -> dict:
+    """{kernel name: (total device ms, launches)} of the launches recorded since gwe_profile_enable."""
+    lib = load()
+    out = {}
+    i = 0
+    buf = ctypes.create_string_buffer(128)
+    while True:
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        if lib.gwe_profile_read(i, buf, 128, ctypes.byref(ms), ctypes.byref(n)) != 0:
+            break
+        out[buf.value.decode()] = (ms.value, n.value)
+        i += 1
+    return out
+
+
+class Model:
+    """Owning wrapper of a gwe_model handle."""
+
+    def __init__(self, cfg, host_weights: np.ndarray, precision: int = GWE_FP32):
+        self.cfg = dict(cfg)
+        self.precision = int(precision)
+        self.handle = gwe_model_create(cfg, host_weights, precision)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gwe_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, strain_H, strain_L, window: int, stride: int, slides=None, out=None, stream=None):
+        import torch
+        n = int(strain_H.shape[0])
+        nw = gwe_n_windows(n, window, stride)
+        ns = 1 if slides is None or len(slides) == 0 else len(slides)
+        if out is None:
+            out = torch.empty((ns, int(self.cfg["n_models"]), nw, window), dtype=torch.float32,
+                              device=strain_H.device)
+        gwe_forward(self.handle, strain_H, strain_L, n, window, stride, slides, out, stream)
+        return out
+
+    def logits(self, x_H, x_L, out=None, stream=None):
+        import torch
+        B, W = int(x_H.shape[0]), int(x_H.shape[1])
+        if out is None:
+            out = torch.empty((int(self.cfg["n_models"]), B, W), dtype=torch.float32, device=x_H.device)
+        gwe_forward_logits(self.handle, x_H, x_L, B, W, out, stream)
+        return out

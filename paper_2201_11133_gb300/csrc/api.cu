@@ -1,0 +1,220 @@
+// C-ABI entry points of libgwe (declared in include/gwe.h): argument checks,
+// model handles and dispatch to the precision-specific paths.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "gwe_internal.h"
+
+namespace gwe {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+
+cudaError_t DevBuf::ensure(size_t want) {
+    if (want <= bytes && ptr) return cudaSuccess;
+    release();
+    size_t sz = want < 256 ? 256 : want;
+    cudaError_t e = cudaMalloc(&ptr, sz);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        return e;
+    }
+    bytes = sz;
+    return cudaSuccess;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+bool make_dims(const gwe_model_config *c, Dims *d) {
+    if (!c) return false;
+    if (c->n_models <= 0 || c->stacks <= 0 || c->layers_per_stack <= 0 || c->layers_per_stack > 24 ||
+        c->kernel <= 0 || c->r_ch <= 0 || c->s_ch <= 0 || c->head_ch <= 0)
+        return false;
+    d->n_models = c->n_models;
+    d->stacks = c->stacks;
+    d->lps = c->layers_per_stack;
+    d->k = c->kernel;
+    d->R = c->r_ch;
+    d->S = c->s_ch;
+    d->Hc = c->head_ch;
+    d->L = c->stacks * c->layers_per_stack;
+    d->Pl = (int64_t)2 * d->R * d->k * d->R + 2 * d->R + (int64_t)d->R * d->R + d->R + (int64_t)d->S * d->R + d->S;
+    d->Pb = 2 * d->R + (int64_t)d->L * d->Pl;
+    d->head_off = 2 * d->Pb;
+    d->P = d->head_off + (int64_t)d->Hc * 2 * d->S + 2 * d->Hc + 1;
+    return true;
+}
+
+static cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static gwe_status check_device() {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error(std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+        return GWE_ERR_CUDA;
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) {
+        set_error("libgwe is built for sm_103a (GB300); current device is sm_" + std::to_string(major * 10 + minor));
+        return GWE_ERR_CUDA;
+    }
+    return GWE_OK;
+}
+
+}  // namespace gwe
+
+using namespace gwe;
+
+extern "C" {
+
+const char *gwe_last_error(void) { return g_err.c_str(); }
+
+const char *gwe_version(void) { return "gwe 0.1 (sm_103a)"; }
+
+int64_t gwe_param_count(const gwe_model_config *cfg) {
+    Dims d;
+    if (!make_dims(cfg, &d)) return -1;
+    return d.P;
+}
+
+int64_t gwe_n_windows(int64_t n, int window, int stride) {
+    if (window <= 0 || stride <= 0 || n < window) return 0;
+    return (n - window) / stride + 1;
+}
+
+gwe_status gwe_model_create(const gwe_model_config *cfg, const float *host_weights, int precision,
+                            gwe_model **out) {
+    clear_error();
+    GWE_ARG_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    Dims d;
+    GWE_ARG_CHECK(make_dims(cfg, &d), "invalid configuration");
+    GWE_ARG_CHECK(host_weights != nullptr, "host_weights is NULL");
+    GWE_ARG_CHECK(precision == GWE_FP32 || precision == GWE_BF16 || precision == GWE_FP8, "unknown precision");
+    if (d.k != 2) {
+        set_error("only kernel size 2 is implemented");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    gwe_status st = check_device();
+    if (st != GWE_OK) return st;
+    gwe_model *m = new (std::nothrow) gwe_model();
+    if (!m) {
+        set_error("host allocation failed");
+        return GWE_ERR_OOM;
+    }
+    m->cfg = *cfg;
+    m->dims = d;
+    m->precision = precision;
+    cudaGetDevice(&m->device);
+    st = gwe_model_set_weights(m, host_weights);
+    if (st != GWE_OK) {
+        gwe_model_destroy(m);
+        return st;
+    }
+    *out = m;
+    return GWE_OK;
+}
+
+gwe_status gwe_model_set_weights(gwe_model *m, const float *hb) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr && hb != nullptr, "NULL argument");
+    const size_t bytes = (size_t)m->dims.P * m->dims.n_models * sizeof(float);
+    GWE_CUDA_TRY(m->w32.ensure(bytes));
+    GWE_CUDA_TRY(cudaMemcpy(m->w32.ptr, hb, bytes, cudaMemcpyHostToDevice));
+    gwe_status st = fp32_prepare(m, hb);
+    if (st != GWE_OK && m->precision == GWE_FP32) return st;
+    if (m->precision == GWE_BF16 || m->precision == GWE_FP8) {
+        st = bf16_prepare(m, hb);
+        if (st != GWE_OK) return st;
+    }
+    return GWE_OK;
+}
+
+void gwe_model_destroy(gwe_model *m) {
+    if (!m) return;
+    bf16_release(m);
+    m->w32.release();
+    m->f32.buf.release();
+    m->ws.x0.release();
+    m->ws.x1.release();
+    m->ws.skip.release();
+    m->ws.proj.release();
+    m->ws.logit.release();
+    m->ws.aux.release();
+    delete m;
+}
+
+static gwe_status dispatch_forward(gwe_model *m, const float *sH, const float *sL, int64_t n, int window, int stride,
+                                   int64_t nw, const int32_t *slides, int n_slides, float *out, bool logits,
+                                   cudaStream_t st) {
+    if (m->precision == GWE_FP32) return fp32_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out, logits, st);
+    return bf16_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out, logits, st);
+}
+
+gwe_status gwe_forward(gwe_model *m, const float *sH, const float *sL, int64_t n, int window, int stride,
+                       const int32_t *slides, int n_slides, float *out_prob, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    GWE_ARG_CHECK(sH != nullptr && sL != nullptr && out_prob != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(window > 0 && stride > 0, "window and stride must be positive");
+    GWE_ARG_CHECK(stride <= window, "stride must not exceed window");
+    GWE_ARG_CHECK(n >= window, "n_samples < window");
+    GWE_ARG_CHECK(n_slides >= 0 && (n_slides == 0 || slides != nullptr), "slides is NULL with n_slides > 0");
+    const int64_t nw = gwe_n_windows(n, window, stride);
+    return dispatch_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out_prob, false, as_stream(stream));
+}
+
+gwe_status gwe_forward_logits(gwe_model *m, const float *xH, const float *xL, int batch, int window,
+                              float *out_logit, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    GWE_ARG_CHECK(xH != nullptr && xL != nullptr && out_logit != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(batch > 0 && window > 0, "batch and window must be positive");
+    return dispatch_forward(m, xH, xL, (int64_t)batch * window, window, window, batch, nullptr, 0, out_logit, true,
+                            as_stream(stream));
+}
+
+gwe_status gwe_backward(gwe_model *m, int model_index, const float *xH, const float *xL, int batch, int window,
+                        const float *dlogit, float *grad_w, float *grad_H, float *grad_L, void *stream) {
+    clear_error();
+    (void)model_index; (void)xH; (void)xL; (void)batch; (void)window; (void)dlogit; (void)grad_w;
+    (void)grad_H; (void)grad_L; (void)stream;
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    set_error("gwe_backward: not built yet");
+    return GWE_ERR_UNSUPPORTED;
+}
+
+gwe_status gwe_triggers(const float *prob, int n_models, int n_slides, int64_t n_windows, int window, int stride,
+                        float height_thr, double min_width, int64_t coinc, int flags, gwe_trigger *out, int64_t cap,
+                        int64_t *n_out, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(prob != nullptr && n_out != nullptr, "NULL argument");
+    GWE_ARG_CHECK(n_models > 0 && n_slides >= 0 && n_windows >= 0, "bad counts");
+    GWE_ARG_CHECK(window > 0 && stride > 0 && stride <= window, "bad window/stride");
+    GWE_ARG_CHECK(coinc >= 0, "coinc must be >= 0");
+    GWE_ARG_CHECK(cap >= 0 && (cap == 0 || out != nullptr), "out is NULL with cap > 0");
+    return triggers_run(prob, n_models, n_slides, n_windows, window, stride, height_thr, min_width, coinc, flags, out,
+                        cap, n_out, as_stream(stream));
+}
+
+gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream) {
+    clear_error();
+    (void)strain; (void)n; (void)fs; (void)seg_len; (void)flags; (void)out; (void)stream;
+    set_error("gwe_whiten: not built yet");
+    return GWE_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

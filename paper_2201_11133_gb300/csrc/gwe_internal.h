@@ -1,0 +1,135 @@
+// Internal declarations of libgwe (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gwe.h"
+
+namespace gwe {
+
+// Thread-local error reporting.
+void set_error(const std::string &msg);
+void clear_error();
+
+#define GWE_CUDA_TRY(expr)                                                                    \
+    do {                                                                                      \
+        cudaError_t _e = (expr);                                                              \
+        if (_e != cudaSuccess) {                                                              \
+            ::gwe::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));             \
+            return (_e == cudaErrorMemoryAllocation) ? GWE_ERR_OOM : GWE_ERR_CUDA;            \
+        }                                                                                     \
+    } while (0)
+
+#define GWE_ARG_CHECK(cond, msg)                                                              \
+    do {                                                                                      \
+        if (!(cond)) {                                                                        \
+            ::gwe::set_error(std::string("argument error: ") + (msg));                        \
+            return GWE_ERR_ARG;                                                               \
+        }                                                                                     \
+    } while (0)
+
+// Sizes derived from a configuration.
+struct Dims {
+    int n_models, stacks, lps, k, R, S, Hc, L;
+    int64_t P;    // parameters per model
+    int64_t Pb;   // per branch
+    int64_t Pl;   // per layer
+    int64_t head_off;  // offset of w_h1 in a model blob
+};
+bool make_dims(const gwe_model_config *cfg, Dims *d);
+
+// Offsets (in floats) inside one model's FP32 blob.
+inline int64_t off_branch(const Dims &d, int b) { return (int64_t)b * d.Pb; }
+inline int64_t off_layer(const Dims &d, int b, int l) { return off_branch(d, b) + 2 * d.R + (int64_t)l * d.Pl; }
+inline int64_t off_wconv(const Dims &d, int b, int l) { return off_layer(d, b, l); }
+inline int64_t off_bconv(const Dims &d, int b, int l) { return off_wconv(d, b, l) + (int64_t)2 * d.R * d.k * d.R; }
+inline int64_t off_wres(const Dims &d, int b, int l) { return off_bconv(d, b, l) + 2 * d.R; }
+inline int64_t off_bres(const Dims &d, int b, int l) { return off_wres(d, b, l) + (int64_t)d.R * d.R; }
+inline int64_t off_wskip(const Dims &d, int b, int l) { return off_bres(d, b, l) + d.R; }
+inline int64_t off_bskip(const Dims &d, int b, int l) { return off_wskip(d, b, l) + (int64_t)d.S * d.R; }
+inline int64_t off_wh1(const Dims &d) { return d.head_off; }
+inline int64_t off_bh1(const Dims &d) { return d.head_off + (int64_t)d.Hc * 2 * d.S; }
+inline int64_t off_wh2(const Dims &d) { return off_bh1(d) + d.Hc; }
+inline int64_t off_bh2(const Dims &d) { return off_wh2(d) + d.Hc; }
+
+// Records CUDA events around one launch when profiling is enabled
+// (gwe_profile_enable); a no-op otherwise.
+struct ProfScope {
+    int slot;
+    cudaStream_t st;
+    ProfScope(const char *name, cudaStream_t s);
+    ~ProfScope();
+};
+
+// Counts the library's kernel launches (read with gwe_launch_count).
+void note_launch(int n = 1);
+
+// Grow-only device buffer.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want);
+    void release();
+    template <class T> T *as() const { return reinterpret_cast<T *>(ptr); }
+};
+
+// FP32 path: per model, per branch, per layer weights re-laid out for the
+// SIMT kernels (transposed so that output channels are contiguous).
+//   conv   [2R (k: lagged inputs then current inputs)][2R (out)]
+//   rs     [R (k)][R + S (out: residual then skip)]
+//   bias   b_conv[2R], b_res[R], b_skip[S]
+// head, per branch X: w1t [S (k)][Hc (out)] = W_h1[:, X*S + k]^T.
+struct Fp32Weights {
+    DevBuf buf;
+    int64_t layer_stride = 0;   // floats per (branch, layer) block
+    int64_t conv_off = 0, rs_off = 0, bconv_off = 0, bres_off = 0, bskip_off = 0;
+    int64_t model_stride = 0;   // floats per model
+    int64_t win_off = 0;        // w_in[2][R], b_in[2][R] per model
+    int64_t head_off = 0;       // w1t[2][S][Hc], b1[Hc], w2[Hc], b2[1] per model
+};
+
+struct Workspace {
+    DevBuf x0, x1, skip, proj, logit;
+    DevBuf aux;
+};
+
+}  // namespace gwe
+
+struct gwe_model {
+    gwe_model_config cfg;
+    gwe::Dims dims;
+    int precision = GWE_FP32;
+    int device = 0;
+    gwe::DevBuf w32;              // FP32 blob [n_models][P] as given
+    gwe::Fp32Weights f32;         // FP32 kernel layout
+    void *bf16 = nullptr;         // BF16 path state (opaque, bf16_path.cu)
+    gwe::Workspace ws;
+};
+
+namespace gwe {
+
+// fp32_path.cu
+gwe_status fp32_prepare(gwe_model *m, const float *host_blob);
+// Forward of all models over one segment; writes probabilities (or logits).
+gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
+                        int stride, int64_t n_windows, const int32_t *slides, int n_slides, float *out,
+                        bool logits, cudaStream_t st);
+
+// bf16_path.cu
+gwe_status bf16_prepare(gwe_model *m, const float *host_blob);
+void bf16_release(gwe_model *m);
+gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
+                        int stride, int64_t n_windows, const int32_t *slides, int n_slides, float *out,
+                        bool logits, cudaStream_t st);
+bool bf16_supported(const Dims &d);
+
+// triggers.cu
+gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,
+                        int stride, float thr, double min_width, int64_t coinc, int flags, gwe_trigger *out,
+                        int64_t cap, int64_t *n_out, cudaStream_t st);
+
+}  // namespace gwe
