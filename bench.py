@@ -131,9 +131,10 @@ def traffic_for(kernel: str, src_file: str):
     return e.get("bytes_per_launch")
 
 
-def make_inputs(seed: int):
-    n = HOUR * FS
-    sh, sl, mergers = workload.stream(n, seed=seed, n_inj=200, snr_range=(6.0, 20.0), mc_range=(5.0, 30.0))
+def make_inputs(seed: int, minutes: float = 60.0):
+    n = int(round(minutes * 60)) * FS
+    n_inj = max(1, int(round(200 * minutes / 60.0)))
+    sh, sl, mergers = workload.stream(n, seed=seed, n_inj=n_inj, snr_range=(6.0, 20.0), mc_range=(5.0, 30.0))
     return sh, sl, mergers
 
 
@@ -178,7 +179,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "1h-2det-4model-30layer", "window": WINDOW, "stride": STRIDE,
+        "config": {"workload": "1h-2det-4model-30layer" if args.minutes == 60 else f"{args.minutes:g}min-2det-4model-30layer", "window": WINDOW, "stride": STRIDE,
                    "sample_windows": n_win},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -195,7 +196,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gwe", choices=["gwe", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("GWE_BENCH_PRECISION", "fp32"), choices=list(PREC_NAMES))
+    ap.add_argument("--precision", default=os.environ.get("GWE_BENCH_PRECISION", "bf16"), choices=list(PREC_NAMES))
+    ap.add_argument("--minutes", type=float, default=60.0,
+                    help="strain duration per detector (60 = the one-hour workload; smaller only for profiler captures)")
     ap.add_argument("--ref-windows", type=int, default=2)
     ap.add_argument("--cpu-windows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -222,7 +225,7 @@ def main():
     wb = workload.init_weights(cfg, seed=3000)
     prec = PREC_NAMES[args.precision]
     model = gwe.Model(cfg, wb, prec)
-    sh, sl, mergers = make_inputs(1000 + 7 * rank)      # each rank its own hour (weak scaling)
+    sh, sl, mergers = make_inputs(1000 + 7 * rank, args.minutes)   # each rank its own hour (weak scaling)
     n = sh.shape[0]
     nw = gwe.gwe_n_windows(n, WINDOW, STRIDE)
     H = torch.from_numpy(sh).to(dev)
@@ -352,7 +355,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec], "data": "synthetic",
-        "config": {"workload": "1h-2det-4model-30layer", "n_samples_per_detector": n, "window": WINDOW,
+        "config": {"workload": "1h-2det-4model-30layer" if args.minutes == 60 else f"{args.minutes:g}min-2det-4model-30layer", "n_samples_per_detector": n, "window": WINDOW,
                    "stride": STRIDE, "n_windows": nw, "models": cfg["n_models"], "layers": workload.n_layers(cfg),
                    "r_ch": cfg["r_ch"], "s_ch": cfg["s_ch"], "head_ch": cfg["head_ch"],
                    "precision": args.precision, "injections": len(mergers), "trigger_thr": thr,

@@ -167,6 +167,14 @@ gwe_status gwe_backward(gwe_model *model, int model_index, const float *x_H, con
                         int window, const float *dlogit, float *grad_weights, float *grad_H, float *grad_L,
                         void *stream);
 
+/*
+ * Wait for the work queued on `stream` and report device-side failures of the
+ * handle's kernels: GWE_ERR_TIMEOUT when a bounded wait inside a tensor-core
+ * kernel gave up (its outputs are then invalid), GWE_ERR_CUDA for a CUDA
+ * error.  Clears the recorded failure.
+ */
+gwe_status gwe_sync(gwe_model *model, void *stream);
+
 /* Flags of gwe_triggers. */
 #define GWE_TRIG_PER_MODEL 1   /* also return every model's kept peaks (model >= 0) */
 

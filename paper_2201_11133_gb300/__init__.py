@@ -21,7 +21,7 @@ __all__ = [
     "GWE_FP32", "GWE_BF16", "GWE_FP8", "GweError", "load", "build",
     "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_destroy",
     "gwe_forward", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
-    "gwe_version", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
+    "gwe_version", "gwe_sync", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
 
 GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
@@ -82,6 +82,7 @@ def load():
             "gwe_backward": (I, [P, I, P, P, I, I, P, P, P, P, P]),
             "gwe_triggers": (I, [P, I, I, I64, I, I, F, D, I64, I, P, I64, P, P]),
             "gwe_whiten": (I, [P, I64, D, I, I, P, P]),
+            "gwe_sync": (I, [P, P]),
             "gwe_profile_enable": (I, [I]),
             "gwe_profile_read": (I, [I, P, I, P, P]),
             "gwe_last_error": (ctypes.c_char_p, []),
@@ -207,6 +208,11 @@ def gwe_triggers(prob, n_models: int, n_slides: int, n_windows: int, window: int
     return out[:n_out.value].copy()
 
 
+def gwe_sync(model: int, stream=None) -> None:
+    """Wait for the stream and raise if a device-side wait of the handle's kernels timed out."""
+    _check(load().gwe_sync(model, _stream(stream)), "gwe_sync")
+
+
 def gwe_whiten(strain, n: int, fs: float, seg_len: int, out, flags: int = 0, stream=None) -> None:
     _check(load().gwe_whiten(_dptr(strain), int(n), float(fs), int(seg_len), int(flags), _dptr(out),
                              _stream(stream)), "gwe_whiten")
@@ -261,6 +267,9 @@ class Model:
                               device=strain_H.device)
         gwe_forward(self.handle, strain_H, strain_L, n, window, stride, slides, out, stream)
         return out
+
+    def sync(self, stream=None):
+        gwe_sync(self.handle, stream)
 
     def logits(self, x_H, x_L, out=None, stream=None):
         import torch

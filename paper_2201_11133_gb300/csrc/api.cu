@@ -136,9 +136,12 @@ gwe_status gwe_model_set_weights(gwe_model *m, const float *hb) {
     GWE_CUDA_TRY(cudaMemcpy(m->w32.ptr, hb, bytes, cudaMemcpyHostToDevice));
     gwe_status st = fp32_prepare(m, hb);
     if (st != GWE_OK && m->precision == GWE_FP32) return st;
-    if (m->precision == GWE_BF16 || m->precision == GWE_FP8) {
+    if (m->precision == GWE_BF16) {
         st = bf16_prepare(m, hb);
         if (st != GWE_OK) return st;
+    } else if (m->precision == GWE_FP8) {
+        set_error("FP8 path not built yet");
+        return GWE_ERR_UNSUPPORTED;
     }
     return GWE_OK;
 }
@@ -208,6 +211,16 @@ gwe_status gwe_triggers(const float *prob, int n_models, int n_slides, int64_t n
     GWE_ARG_CHECK(cap >= 0 && (cap == 0 || out != nullptr), "out is NULL with cap > 0");
     return triggers_run(prob, n_models, n_slides, n_windows, window, stride, height_thr, min_width, coinc, flags, out,
                         cap, n_out, as_stream(stream));
+}
+
+gwe_status gwe_sync(gwe_model *m, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    cudaStream_t st = as_stream(stream);
+    GWE_CUDA_TRY(cudaStreamSynchronize(st));
+    GWE_CUDA_TRY(cudaGetLastError());
+    if (m->precision == GWE_BF16) return bf16_check(m, st);
+    return GWE_OK;
 }
 
 gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream) {

@@ -1,0 +1,887 @@
+// Fused tensor-core forward of the two-branch WaveNet detector ensemble
+// (arXiv:2201.11133, section "Materials and Methods", paragraph "AI
+// architecture", Fig. 1), 16-bit operands on tcgen05 with FP32 accumulation.
+//
+// One persistent CTA per SM walks a static list of jobs; a job is one
+// (slide, model, window): both detector branches of one 1 s window, followed
+// by the head.  A job runs as a stream of 128-sample time tiles in time order;
+// every tile goes through all layers of both branches and then the head, so
+// activations never leave the SM except the lagged rows of the dilated
+// convolutions (below).
+//
+// Per layer l (dilation d), per branch, on a tile of 128 rows t0..t0+127:
+//   conv   a = [x_l(t-d) | x_l(t)] . Wconv^T        tcgen05, BF16 x BF16 -> FP32 TMEM
+//          (K = 2R: the lagged and the current rows are two descriptors into
+//           one staging buffer whose first 128 rows hold the lag history)
+//   gate   z = tanh(a_f + b_f) * sigmoid(a_g + b_g)   registers, FP16x2 tanh.approx
+//          (the g half of Wconv and b_conv are pre-halved, so that
+//           sigmoid(g) = 0.5 tanh(g/2) + 0.5 costs one tanh)
+//   res    r = z . Wres^T  -> TMEM (reuses the conv columns), FP16 x FP16
+//          x_{l+1} = x_l + r + b_res                   FP32, held in registers
+//   skip   s += z . Wskip^T                            FP32, accumulated in TMEM
+// Head, per tile, on h = ReLU([s_H + sum b_skip ; s_L + sum b_skip]) (FP16):
+//   u = h . W_h1^T (TMEM), logit = b_h2 + w_h2 . ReLU(u + b_h1), p = sigmoid(logit) (FP32)
+//
+// Lag history: the rows x_l(t0-d .. ) needed by the next tiles are written to
+// a per-CTA ring in global memory (d rows per layer, L2-resident) and brought
+// back into the staging buffer with bulk async copies one layer ahead.
+//
+// Warp roles (384 threads): warp 0 weight producer (bulk copies of each
+// layer's prepared weight image into a 4-entry ring), warp 1 TMEM owner and
+// MMA issuer, warps 4-7 epilogue of branch H, warps 8-11 epilogue of branch L
+// (thread = row).  Warps 2-3 are idle.  The two branches ping-pong on the
+// tensor core: one branch's MMAs run while the other's gate runs.
+//
+// Every wait is bounded (wall clock); on timeout the kernel records the wait
+// site in an error word, lets every role leave its loops and frees TMEM.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gwe_internal.h"
+#include "tc_ptx.cuh"
+
+namespace gwe {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 384;
+constexpr int kTile = 128;
+constexpr int kNEnt = 4;
+constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s per wait
+
+constexpr uint32_t pow2ceil(uint32_t x) {
+    uint32_t p = 32;
+    while (p < x) p <<= 1;
+    return p;
+}
+constexpr uint32_t cmax(uint32_t a, uint32_t b) { return a > b ? a : b; }
+
+template <int R, int S, int HC>
+struct TcShape {
+    static constexpr int N1 = 2 * R;              // conv outputs: f then g
+    static constexpr int RC = R / 8;              // 16-byte chunks of an R-wide row
+    static constexpr int SC = S / 8;
+    static constexpr int NH = HC <= 128 ? 1 : 2;  // head output pieces
+    static constexpr int HP = HC / NH;
+    static constexpr uint32_t STAGE_ROWS = 256;
+    static constexpr uint32_t STAGE_LBO = STAGE_ROWS * 16;
+    static constexpr uint32_t STAGE_BYTES = STAGE_LBO * RC;
+    static constexpr uint32_t Z_LBO = kTile * 16;
+    static constexpr uint32_t Z_BYTES = Z_LBO * RC;
+    static constexpr uint32_t CONV_BYTES = N1 * 2 * R * 2;
+    static constexpr uint32_t RES_BYTES = R * R * 2;
+    static constexpr uint32_t SKIP_BYTES = S * R * 2;
+    static constexpr uint32_t RS_BYTES = RES_BYTES + SKIP_BYTES;
+    static constexpr uint32_t HEAD_BYTES = HP * S * 2;
+    static constexpr uint32_t ENT_BYTES = cmax(CONV_BYTES, cmax(RS_BYTES, HEAD_BYTES));
+    static constexpr uint32_t TMEM_BR = 2 * R + S;
+    static constexpr uint32_t TMEM_COLS = pow2ceil(2 * TMEM_BR);
+    static constexpr uint32_t TMEM_BSTRIDE = TMEM_COLS / 2;
+    // shared memory map
+    static constexpr uint32_t OFF_STAGE = 0;
+    static constexpr uint32_t OFF_Z = 2 * STAGE_BYTES;
+    static constexpr uint32_t OFF_ENT = OFF_Z + 2 * Z_BYTES;
+    static constexpr uint32_t OFF_PART = OFF_ENT + kNEnt * ENT_BYTES;
+    static constexpr uint32_t OFF_BAR = OFF_PART + 2 * 2 * kTile * 4;
+    static constexpr uint32_t N_BAR = 32;
+    static constexpr uint32_t OFF_MISC = OFF_BAR + N_BAR * 8;
+    static constexpr uint32_t SMEM = OFF_MISC + 64 + 128;    // + alignment slack
+    // per-branch float parameter block (bytes): w_in[R], b_in[R], bskip_sum[S], then per layer
+    // b_conv as FP16 [2R] (g half pre-halved) and b_res FP32 [R]
+    static constexpr uint32_t PL_BYTES = 4 * R + 4 * R;
+    static __host__ __device__ constexpr uint32_t pb_bytes(int L) { return 8 * R + 4 * S + L * PL_BYTES; }
+    static __host__ __device__ constexpr uint32_t ph_bytes() { return ((8 * HC + 4) + 15) & ~15u; }
+    static __host__ __device__ constexpr uint32_t pm_bytes(int L) { return 2 * pb_bytes(L) + ph_bytes(); }
+    // per-model weight image: per layer [conv H][conv L][rs H][rs L], then head pieces (nh, kh)
+    static constexpr uint32_t LAYER_IMG = 2 * CONV_BYTES + 2 * RS_BYTES;
+    static __host__ __device__ constexpr uint64_t img_bytes(int L) {
+        return (uint64_t)L * LAYER_IMG + 2ull * NH * HEAD_BYTES;
+    }
+    static_assert(R % 16 == 0 && S % 16 == 0 && HP % 16 == 0, "channel counts must be multiples of 16");
+    static_assert(N1 <= 256 && S <= 256 && HP <= 256, "MMA N limit");
+    static_assert(HP <= 2 * R, "head piece must fit the conv TMEM columns");
+    static_assert(256 * S <= STAGE_BYTES, "head operand must fit one staging buffer");
+    static_assert(TMEM_COLS <= 512, "TMEM");
+    static_assert(OFF_MISC + 64 + 128 <= 232448, "shared memory per block");
+};
+
+// barrier indices
+enum {
+    B_WFULL = 0,       // [4]
+    B_WEMPTY = 4,      // [4]
+    B_LAG = 8,         // [2]
+    B_XREADY = 10,     // [2]
+    B_CONV = 12,       // [2]
+    B_ZREADY = 14,     // [2]
+    B_RS = 16,         // [2]
+    B_HREADY = 18,     // [2]
+    B_HEAD = 20,
+    B_WG = 21,         // [2]
+    B_PAIR = 23,
+    B_FIN = 24
+};
+
+struct TcParams {
+    const uint8_t *wimg;       // [n_models] weight images
+    uint64_t wimg_stride;
+    const uint8_t *pblob;      // [n_models] parameter blocks
+    uint64_t pblob_stride;
+    const float *sH, *sL;
+    int64_t nw;
+    int W, stride;
+    const int32_t *slides;     // device, n_slides (NULL: zero lag)
+    int n_slides;
+    int n_models;
+    float *out;
+    int logits;
+    uint8_t *ring;             // per-CTA lag history
+    uint64_t ring_cta_bytes;
+    const uint8_t *zeros;      // >= 2 KiB of zeros
+    int L, lps;
+    uint64_t ring_rows;        // lag-history rows per branch (sum of dilations)
+    int *err;                  // error word: wait site of the first timeout
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t tanh_h2(uint32_t x) {
+    uint32_t y;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(y) : "r"(x));
+    return y;
+}
+__device__ __forceinline__ uint32_t hadd2(uint32_t a, uint32_t b) {
+    uint32_t y;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(y) : "r"(a), "r"(b));
+    return y;
+}
+__device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t y;
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(y) : "r"(a), "r"(b), "r"(c));
+    return y;
+}
+__device__ __forceinline__ uint32_t hmul2(uint32_t a, uint32_t b) {
+    uint32_t y;
+    asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(y) : "r"(a), "r"(b));
+    return y;
+}
+__device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+// job j -> (slide ordinal, model, window)
+struct Job {
+    int si, m;
+    int64_t w, wl;
+};
+__device__ __forceinline__ Job decode_job(const TcParams &p, int64_t j) {
+    Job q;
+    q.w = j % p.nw;
+    const int64_t r = j / p.nw;
+    q.m = (int)(r % p.n_models);
+    q.si = (int)(r / p.n_models);
+    int64_t k = p.slides ? (int64_t)p.slides[q.si] : 0;
+    int64_t wl = (q.w + k) % p.nw;
+    if (wl < 0) wl += p.nw;
+    q.wl = wl;
+    return q;
+}
+
+template <int R, int S, int HC>
+__global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
+    using Sh = TcShape<R, S, HC>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Sh::OFF_BAR);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Sh::OFF_MISC);
+    int *abort_flag = reinterpret_cast<int *>(smem + Sh::OFF_MISC + 8);
+    float *part = reinterpret_cast<float *>(smem + Sh::OFF_PART);
+    const uint32_t s_base = smem_u32(smem);
+    const uint32_t s_stage = s_base + Sh::OFF_STAGE;
+    const uint32_t s_z = s_base + Sh::OFF_Z;
+    const uint32_t s_ent = s_base + Sh::OFF_ENT;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NT = p.W / kTile;
+    const int L = p.L, lps = p.lps;
+    const int64_t n_jobs = (int64_t)(p.n_slides > 0 ? p.n_slides : 1) * p.n_models * p.nw;
+    const int items_per_tile = 4 * L + 2 * Sh::NH;
+
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) {
+            mbar_init(&bar[B_WFULL + i], 1);
+            mbar_init(&bar[B_WEMPTY + i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar[B_LAG + b], 1);
+            mbar_init(&bar[B_XREADY + b], 4);
+            mbar_init(&bar[B_CONV + b], 1);
+            mbar_init(&bar[B_ZREADY + b], 4);
+            mbar_init(&bar[B_RS + b], 1);
+            mbar_init(&bar[B_HREADY + b], 4);
+            mbar_init(&bar[B_WG + b], 4);
+        }
+        mbar_init(&bar[B_HEAD], 1);
+        mbar_init(&bar[B_PAIR], 8);
+        mbar_init(&bar[B_FIN], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, Sh::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ weight producer
+        if (lane == 0) {
+            uint32_t item = 0;
+            for (int64_t j = blockIdx.x; j < n_jobs; j += gridDim.x) {
+                const Job q = decode_job(p, j);
+                const uint8_t *wm = p.wimg + (uint64_t)q.m * p.wimg_stride;
+                for (int tt = 0; tt < NT; ++tt) {
+                    for (int i = 0; i < items_per_tile; ++i, ++item) {
+                        const int e = item & 3;
+                        const uint32_t u = item >> 2;
+                        if (!mbar_wait(&bar[B_WEMPTY + e], (u & 1) ^ 1, abort_flag, p.err, 1, kWaitNs)) goto prod_out;
+                        uint64_t off;
+                        uint32_t bytes;
+                        if (i < 4 * L) {
+                            const int l = i >> 2, k = i & 3;
+                            off = (uint64_t)l * Sh::LAYER_IMG;
+                            if (k < 2) {
+                                off += (uint64_t)k * Sh::CONV_BYTES;
+                                bytes = Sh::CONV_BYTES;
+                            } else {
+                                off += 2ull * Sh::CONV_BYTES + (uint64_t)(k - 2) * Sh::RS_BYTES;
+                                bytes = Sh::RS_BYTES;
+                            }
+                        } else {
+                            off = (uint64_t)L * Sh::LAYER_IMG + (uint64_t)(i - 4 * L) * Sh::HEAD_BYTES;
+                            bytes = Sh::HEAD_BYTES;
+                        }
+                        mbar_arrive_expect_tx(&bar[B_WFULL + e], bytes);
+                        bulk_g2s(smem + Sh::OFF_ENT + e * Sh::ENT_BYTES, wm + off, bytes, &bar[B_WFULL + e]);
+                    }
+                }
+            }
+        prod_out:
+            // never leave with copies in flight: the last copy of every entry must have landed
+            for (int k = 0; k < 4 && k < (int)item; ++k) {
+                const uint32_t it = item - 1 - k;
+                mbar_wait(&bar[B_WFULL + (it & 3)], (it >> 2) & 1, abort_flag, p.err, 2, kWaitNs);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t ID_CONV = idesc_f16(128, Sh::N1, 1);
+            constexpr uint32_t ID_RES = idesc_f16(128, R, 0);
+            constexpr uint32_t ID_SKIP = idesc_f16(128, S, 0);
+            constexpr uint32_t ID_HEAD = idesc_f16(128, Sh::HP, 0);
+            uint32_t item = 0, ph_x[2] = {0, 0}, ph_lag[2] = {0, 0}, ph_z[2] = {0, 0}, ph_h[2] = {0, 0};
+            bool ok = true;
+            for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
+                for (int tt = 0; tt < NT && ok; ++tt) {
+                    for (int l = 0; l < L && ok; ++l) {
+                        const int d = 1 << (l % lps);
+                        const int n = d < kTile ? d : kTile;
+                        for (int b = 0; b < 2 && ok; ++b) {
+                            const int e = item & 3;
+                            ok = mbar_wait(&bar[B_XREADY + b], ph_x[b] & 1, abort_flag, p.err, 10, kWaitNs) &&
+                                 mbar_wait(&bar[B_LAG + b], ph_lag[b] & 1, abort_flag, p.err, 11, kWaitNs) &&
+                                 mbar_wait(&bar[B_WFULL + e], (item >> 2) & 1, abort_flag, p.err, 12, kWaitNs);
+                            if (!ok) break;
+                            ++ph_x[b];
+                            ++ph_lag[b];
+                            tc_fence_after();
+                            const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
+                            const uint32_t we = s_ent + e * Sh::ENT_BYTES;
+                            const uint32_t dcol = tmem + b * Sh::TMEM_BSTRIDE;
+#pragma unroll
+                            for (int ks = 0; ks < Sh::RC; ++ks) {       // K = 2R in steps of 16
+                                uint64_t ad;
+                                if (ks < Sh::RC / 2)
+                                    ad = sdesc(st + 2 * ks * Sh::STAGE_LBO + (kTile - n) * 16, Sh::STAGE_LBO, 128);
+                                else
+                                    ad = sdesc(st + (2 * ks - Sh::RC) * Sh::STAGE_LBO + kTile * 16, Sh::STAGE_LBO, 128);
+                                const uint64_t bd = sdesc(we + 2 * ks * (Sh::N1 * 16), Sh::N1 * 16, 128);
+                                mma_f16(dcol, ad, bd, ID_CONV, ks > 0 ? 1u : 0u);
+                            }
+                            mma_commit(&bar[B_CONV + b]);
+                            mma_commit(&bar[B_WEMPTY + e]);
+                            ++item;
+                        }
+                        for (int b = 0; b < 2 && ok; ++b) {
+                            const int e = item & 3;
+                            ok = mbar_wait(&bar[B_ZREADY + b], ph_z[b] & 1, abort_flag, p.err, 13, kWaitNs) &&
+                                 mbar_wait(&bar[B_WFULL + e], (item >> 2) & 1, abort_flag, p.err, 14, kWaitNs);
+                            if (!ok) break;
+                            ++ph_z[b];
+                            tc_fence_after();
+                            const uint32_t zb = s_z + b * Sh::Z_BYTES;
+                            const uint32_t we = s_ent + e * Sh::ENT_BYTES;
+                            const uint32_t dcol = tmem + b * Sh::TMEM_BSTRIDE;
+#pragma unroll
+                            for (int ks = 0; ks < Sh::RC / 2; ++ks) {
+                                const uint64_t ad = sdesc(zb + 2 * ks * Sh::Z_LBO, Sh::Z_LBO, 128);
+                                const uint64_t bd = sdesc(we + 2 * ks * (R * 16), R * 16, 128);
+                                mma_f16(dcol, ad, bd, ID_RES, ks > 0 ? 1u : 0u);
+                            }
+#pragma unroll
+                            for (int ks = 0; ks < Sh::RC / 2; ++ks) {
+                                const uint64_t ad = sdesc(zb + 2 * ks * Sh::Z_LBO, Sh::Z_LBO, 128);
+                                const uint64_t bd = sdesc(we + Sh::RES_BYTES + 2 * ks * (S * 16), S * 16, 128);
+                                mma_f16(dcol + 2 * R, ad, bd, ID_SKIP, (l > 0 || ks > 0) ? 1u : 0u);
+                            }
+                            mma_commit(&bar[B_RS + b]);
+                            mma_commit(&bar[B_WEMPTY + e]);
+                            ++item;
+                        }
+                    }
+                    if (!ok) break;
+                    // head: u[piece nh] = sum over kh of h_kh . W_h1[nh, kh]^T
+                    ok = mbar_wait(&bar[B_HREADY + 0], ph_h[0] & 1, abort_flag, p.err, 15, kWaitNs) &&
+                         mbar_wait(&bar[B_HREADY + 1], ph_h[1] & 1, abort_flag, p.err, 16, kWaitNs);
+                    if (!ok) break;
+                    ++ph_h[0];
+                    ++ph_h[1];
+                    for (int nh = 0; nh < Sh::NH && ok; ++nh) {
+                        for (int kh = 0; kh < 2; ++kh) {
+                            const int e = item & 3;
+                            ok = mbar_wait(&bar[B_WFULL + e], (item >> 2) & 1, abort_flag, p.err, 17, kWaitNs);
+                            if (!ok) break;
+                            tc_fence_after();
+                            const uint32_t ha = s_stage + kh * Sh::STAGE_BYTES;
+                            const uint32_t we = s_ent + e * Sh::ENT_BYTES;
+#pragma unroll
+                            for (int ks = 0; ks < Sh::SC / 2; ++ks) {
+                                const uint64_t ad = sdesc(ha + 2 * ks * (kTile * 16), kTile * 16, 128);
+                                const uint64_t bd = sdesc(we + 2 * ks * (Sh::HP * 16), Sh::HP * 16, 128);
+                                mma_f16(tmem + nh * Sh::TMEM_BSTRIDE, ad, bd, ID_HEAD, (kh > 0 || ks > 0) ? 1u : 0u);
+                            }
+                            mma_commit(&bar[B_WEMPTY + e]);
+                            ++item;
+                        }
+                    }
+                    if (ok) mma_commit(&bar[B_HEAD]);
+                }
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            mma_commit(&bar[B_FIN]);
+            mbar_wait(&bar[B_FIN], 0, abort_flag, p.err, 18, kWaitNs);
+        }
+    } else if (warp >= 4) {
+        // ------------------------------------------------------------ epilogue (thread = row)
+        const int b = (warp - 4) >> 2;                 // 0: Hanford branch, 1: Livingston branch
+        const int q = warp & 3;                        // TMEM lane quarter of this warp
+        const int r = q * 32 + lane;                   // row within the tile
+        const bool leader = (r == 0);
+        const uint32_t t_lane = (uint32_t)(q * 32) << 16;
+        const uint32_t t_conv = tmem + t_lane + b * Sh::TMEM_BSTRIDE;
+        const uint32_t t_skip = t_conv + 2 * R;
+        const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
+        const uint32_t zb = s_z + b * Sh::Z_BYTES;
+        uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * (2 * R);
+        uint32_t ph_conv = 0, ph_rs = 0, ph_head = 0, ph_wg = 0, ph_pair = 0, lag_issued = 0, tiles = 0;
+        bool ok = true;
+        float x[R];
+        const uint32_t half2_half = 0x38003800u;     // (0.5, 0.5) in FP16x2
+
+        // lagged rows of layer l for the tile at t0 -> staging rows [128 - n, 128)
+        auto issue_lag = [&](int l, int t0) {
+            const int d = 1 << (l % lps);
+            const int n = d < kTile ? d : kTile;
+            const uint32_t bytes = (uint32_t)n * 16;
+            mbar_arrive_expect_tx(&bar[B_LAG + b], bytes * Sh::RC);
+            const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
+            const uint8_t *src = ring_b + roff * (2 * R) + (uint64_t)(t0 & (d - 1)) * 16;
+            uint8_t *dst0 = smem + Sh::OFF_STAGE + b * Sh::STAGE_BYTES + (kTile - n) * 16;
+#pragma unroll
+            for (int c = 0; c < Sh::RC; ++c)
+                bulk_g2s(dst0 + c * Sh::STAGE_LBO, (t0 < d) ? p.zeros : src + (uint64_t)c * d * 16, bytes,
+                         &bar[B_LAG + b]);
+            ++lag_issued;
+        };
+        auto warp_wait = [&](int idx, uint32_t parity, int site) -> bool {
+            bool w = mbar_wait(&bar[idx], parity, abort_flag, p.err, site, kWaitNs);
+            return __all_sync(0xffffffffu, w);
+        };
+        auto warp_arrive = [&](int idx) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[idx]);
+        };
+        auto store_x = [&]() {
+#pragma unroll
+            for (int c = 0; c < Sh::RC; ++c) {
+                uint4 v;
+                v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
+                v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
+                v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
+                v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+                sts128(st + c * Sh::STAGE_LBO + (kTile + r) * 16, v);
+            }
+        };
+
+        if (leader && (int64_t)blockIdx.x < n_jobs) issue_lag(0, 0);
+        for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
+            const Job jb = decode_job(p, j);
+            const uint8_t *pm = p.pblob + (uint64_t)jb.m * p.pblob_stride;
+            const uint8_t *pbr = pm + b * Sh::pb_bytes(L);
+            const float4 *w_in4 = reinterpret_cast<const float4 *>(pbr);
+            const float4 *b_in4 = w_in4 + R / 4;
+            const float4 *bsk4 = b_in4 + R / 4;
+            const uint8_t *play = pbr + 8 * R + 4 * S;
+            const float *phd = reinterpret_cast<const float *>(pm + 2 * Sh::pb_bytes(L));
+            const float *b1 = phd, *w2 = phd + HC;
+            const float b2 = __ldg(phd + 2 * HC);
+            const float *sv = b ? p.sL + jb.wl * (int64_t)p.stride : p.sH + jb.w * (int64_t)p.stride;
+            float *outp = p.out + (((int64_t)jb.si * p.n_models + jb.m) * p.nw + jb.w) * (int64_t)p.W;
+            for (int tt = 0; tt < NT && ok; ++tt, ++tiles) {
+                const int t0 = tt * kTile;
+                // input 1x1 convolution x_0 = w_in s + b_in (FP32), BF16 copy for the MMA
+                {
+                    const float sval = __ldg(sv + t0 + r);
+#pragma unroll
+                    for (int c4 = 0; c4 < R / 4; ++c4) {
+                        const float4 wi = __ldg(w_in4 + c4), bi = __ldg(b_in4 + c4);
+                        x[4 * c4 + 0] = fmaf(wi.x, sval, bi.x);
+                        x[4 * c4 + 1] = fmaf(wi.y, sval, bi.y);
+                        x[4 * c4 + 2] = fmaf(wi.z, sval, bi.z);
+                        x[4 * c4 + 3] = fmaf(wi.w, sval, bi.w);
+                    }
+                    store_x();
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    warp_arrive(B_XREADY + b);
+                }
+                for (int l = 0; l < L; ++l) {
+                    const int d = 1 << (l % lps);
+                    const int n = d < kTile ? d : kTile;
+                    if (!warp_wait(B_CONV + b, ph_conv & 1, 30)) { ok = false; break; }
+                    ++ph_conv;
+                    tc_fence_after();
+                    if (leader && l + 1 < L) issue_lag(l + 1, t0);
+                    // lag history of layer l for the following tiles: rows t0+r, r >= 128 - n
+                    if (tt + 1 < NT && r >= kTile - n) {
+                        const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
+                        uint8_t *dst = ring_b + roff * (2 * R) + (uint64_t)((t0 + r) & (d - 1)) * 16;
+#pragma unroll
+                        for (int c = 0; c < Sh::RC; ++c) {
+                            const uint4 v = lds128(st + c * Sh::STAGE_LBO + (kTile + r) * 16);
+                            *reinterpret_cast<uint4 *>(dst + (uint64_t)c * d * 16) = v;
+                        }
+                        fence_proxy_async_global();
+                    }
+                    // gate: z = tanh(f + b_f) * (0.5 tanh(g/2 + b_g/2) + 0.5), FP16x2
+                    const uint4 *bc4 = reinterpret_cast<const uint4 *>(play + (uint64_t)l * Sh::PL_BYTES);
+#pragma unroll
+                    for (int cc = 0; cc < R / 16; ++cc) {
+                        uint32_t fr[16], gr[16];
+                        tmem_ld16(t_conv + 16 * cc, fr);
+                        tmem_ld16(t_conv + R + 16 * cc, gr);
+                        const uint4 bf0 = __ldg(bc4 + 2 * cc), bf1 = __ldg(bc4 + 2 * cc + 1);
+                        const uint4 bg0 = __ldg(bc4 + R / 8 + 2 * cc), bg1 = __ldg(bc4 + R / 8 + 2 * cc + 1);
+                        tmem_ld_wait();
+                        const uint32_t bfw[8] = {bf0.x, bf0.y, bf0.z, bf0.w, bf1.x, bf1.y, bf1.z, bf1.w};
+                        const uint32_t bgw[8] = {bg0.x, bg0.y, bg0.z, bg0.w, bg1.x, bg1.y, bg1.z, bg1.w};
+                        uint32_t zz[8];
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const uint32_t hf = hadd2(pack_h2(__uint_as_float(fr[2 * jj]), __uint_as_float(fr[2 * jj + 1])), bfw[jj]);
+                            const uint32_t hg = hadd2(pack_h2(__uint_as_float(gr[2 * jj]), __uint_as_float(gr[2 * jj + 1])), bgw[jj]);
+                            const uint32_t sg = hfma2(tanh_h2(hg), half2_half, half2_half);
+                            zz[jj] = hmul2(tanh_h2(hf), sg);
+                        }
+                        sts128(zb + (2 * cc) * Sh::Z_LBO + r * 16, make_uint4(zz[0], zz[1], zz[2], zz[3]));
+                        sts128(zb + (2 * cc + 1) * Sh::Z_LBO + r * 16, make_uint4(zz[4], zz[5], zz[6], zz[7]));
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    warp_arrive(B_ZREADY + b);
+                    if (!warp_wait(B_RS + b, ph_rs & 1, 31)) { ok = false; break; }
+                    ++ph_rs;
+                    tc_fence_after();
+                    if (l + 1 < L) {
+                        // residual: x_{l+1} = x_l + (W_res z) + b_res  (FP32)
+                        const float4 *br4 = reinterpret_cast<const float4 *>(play + (uint64_t)l * Sh::PL_BYTES + 4 * R);
+#pragma unroll
+                        for (int cc = 0; cc < R / 16; ++cc) {
+                            uint32_t rr[16];
+                            tmem_ld16(t_conv + 16 * cc, rr);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int k4 = 0; k4 < 4; ++k4) {
+                                const float4 bb = __ldg(br4 + 4 * cc + k4);
+                                x[16 * cc + 4 * k4 + 0] += __uint_as_float(rr[4 * k4 + 0]) + bb.x;
+                                x[16 * cc + 4 * k4 + 1] += __uint_as_float(rr[4 * k4 + 1]) + bb.y;
+                                x[16 * cc + 4 * k4 + 2] += __uint_as_float(rr[4 * k4 + 2]) + bb.z;
+                                x[16 * cc + 4 * k4 + 3] += __uint_as_float(rr[4 * k4 + 3]) + bb.w;
+                            }
+                        }
+                        store_x();
+                        fence_proxy_async_smem();
+                        tc_fence_before();
+                        warp_arrive(B_XREADY + b);
+                    }
+                }
+                if (!ok) break;
+                // every row's history copy has read the staging buffer before it becomes the head operand
+                warp_arrive(B_WG + b);
+                if (!warp_wait(B_WG + b, ph_wg & 1, 32)) { ok = false; break; }
+                ++ph_wg;
+                // head operand h = ReLU(skip + sum of skip biases), FP16, rows-128 layout in this branch's staging buffer
+#pragma unroll
+                for (int cc = 0; cc < S / 16; ++cc) {
+                    uint32_t sr[16];
+                    tmem_ld16(t_skip + 16 * cc, sr);
+                    tmem_ld_wait();
+                    float h[16];
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const float4 bs = __ldg(bsk4 + 4 * cc + k4);
+                        h[4 * k4 + 0] = fmaxf(__uint_as_float(sr[4 * k4 + 0]) + bs.x, 0.f);
+                        h[4 * k4 + 1] = fmaxf(__uint_as_float(sr[4 * k4 + 1]) + bs.y, 0.f);
+                        h[4 * k4 + 2] = fmaxf(__uint_as_float(sr[4 * k4 + 2]) + bs.z, 0.f);
+                        h[4 * k4 + 3] = fmaxf(__uint_as_float(sr[4 * k4 + 3]) + bs.w, 0.f);
+                    }
+                    sts128(st + (2 * cc) * (kTile * 16) + r * 16,
+                           make_uint4(pack_h2(h[0], h[1]), pack_h2(h[2], h[3]), pack_h2(h[4], h[5]), pack_h2(h[6], h[7])));
+                    sts128(st + (2 * cc + 1) * (kTile * 16) + r * 16,
+                           make_uint4(pack_h2(h[8], h[9]), pack_h2(h[10], h[11]), pack_h2(h[12], h[13]),
+                                      pack_h2(h[14], h[15])));
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                warp_arrive(B_HREADY + b);
+                if (!warp_wait(B_HEAD, ph_head & 1, 33)) { ok = false; break; }
+                ++ph_head;
+                tc_fence_after();
+                // the staging buffer is free again: bring in the next tile's layer-0 history
+                if (leader) {
+                    if (tt + 1 < NT) issue_lag(0, t0 + kTile);
+                    else if (j + (int64_t)gridDim.x < n_jobs) issue_lag(0, 0);
+                }
+                float acc = 0.f;
+                if (b < Sh::NH) {
+                    const uint32_t t_u = tmem + t_lane + b * Sh::TMEM_BSTRIDE;
+#pragma unroll
+                    for (int cc = 0; cc < Sh::HP / 16; ++cc) {
+                        uint32_t ur[16];
+                        tmem_ld16(t_u + 16 * cc, ur);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) {
+                            const int ch = b * Sh::HP + 16 * cc + jj;
+                            const float u = __uint_as_float(ur[jj]) + __ldg(b1 + ch);
+                            acc = fmaf(__ldg(w2 + ch), fmaxf(u, 0.f), acc);
+                        }
+                    }
+                }
+                float *pp = part + (tiles & 1) * 2 * kTile;
+                pp[b * kTile + r] = acc;
+                tc_fence_before();
+                warp_arrive(B_PAIR);
+                if (!warp_wait(B_PAIR, ph_pair & 1, 34)) { ok = false; break; }
+                ++ph_pair;
+                if (b == 0) {
+                    const float lg = (pp[r] + pp[kTile + r]) + b2;
+                    outp[t0 + r] = p.logits ? lg : 1.f / (1.f + expf(-lg));
+                }
+            }
+        }
+        // never leave with history copies in flight
+        if (leader && lag_issued > 0)
+            mbar_wait(&bar[B_LAG + b], (lag_issued - 1) & 1, abort_flag, p.err, 35, kWaitNs);
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, Sh::TMEM_COLS);
+    }
+}
+
+}  // namespace
+}  // namespace gwe
+
+// ============================================================================ host side
+namespace gwe {
+namespace {
+
+struct TcState {
+    int variant = -1;            // 0: (R, S, Hc) = (32, 32, 32); 1: (64, 128, 256)
+    DevBuf img, pblob, ring, zeros, err, slides;
+    uint64_t img_stride = 0, pblob_stride = 0;
+    int sms = 0;
+};
+
+int tc_variant(const Dims &d) {
+    if (d.k != 2) return -1;
+    if (d.R == 32 && d.S == 32 && d.Hc == 32) return 0;
+    if (d.R == 64 && d.S == 128 && d.Hc == 256) return 1;
+    return -1;
+}
+
+inline uint16_t to_bf16(float f) {
+    __nv_bfloat16 h = __float2bfloat16_rn(f);
+    uint16_t u;
+    std::memcpy(&u, &h, 2);
+    return u;
+}
+inline uint16_t to_f16(float f) {
+    __half h = __float2half_rn(f);
+    uint16_t u;
+    std::memcpy(&u, &h, 2);
+    return u;
+}
+
+// element (n, k) of a K-major operand with `rows` rows in the chunk-column layout
+inline size_t chunk_off(int rows, int n, int k) { return (size_t)(k / 8) * rows * 16 + (size_t)n * 16 + (k % 8) * 2; }
+inline void put16(std::vector<uint8_t> &v, size_t off, uint16_t x) { std::memcpy(v.data() + off, &x, 2); }
+
+template <int R, int S, int HC>
+void build_images(const Dims &d, const float *hb, std::vector<uint8_t> &img, std::vector<uint8_t> &pbl,
+                  uint64_t &img_stride, uint64_t &pb_stride) {
+    using Sh = TcShape<R, S, HC>;
+    const int L = d.L;
+    img_stride = (Sh::img_bytes(L) + 255) & ~uint64_t(255);
+    pb_stride = ((uint64_t)Sh::pm_bytes(L) + 255) & ~uint64_t(255);
+    img.assign(img_stride * d.n_models, 0);
+    pbl.assign(pb_stride * d.n_models, 0);
+    for (int mi = 0; mi < d.n_models; ++mi) {
+        const float *src = hb + (int64_t)mi * d.P;
+        uint8_t *im0 = img.data() + img_stride * mi;
+        std::vector<uint8_t> tmp;
+        for (int l = 0; l < L; ++l) {
+            for (int b = 0; b < 2; ++b) {
+                // conv item: rows n = output channel (g half pre-halved), k < R lag tap, k >= R current tap
+                tmp.assign(Sh::CONV_BYTES, 0);
+                const float *wc = src + off_wconv(d, b, l);
+                for (int o = 0; o < 2 * R; ++o)
+                    for (int k = 0; k < 2 * R; ++k) {
+                        const int tap = k < R ? 0 : 1, i = k % R;
+                        float v = wc[((int64_t)o * 2 + tap) * R + i];
+                        if (o >= R) v *= 0.5f;
+                        put16(tmp, chunk_off(2 * R, o, k), to_bf16(v));
+                    }
+                std::memcpy(im0 + (uint64_t)l * Sh::LAYER_IMG + (uint64_t)b * Sh::CONV_BYTES, tmp.data(), tmp.size());
+                // rs item: W_res [R x R] then W_skip [S x R], FP16
+                tmp.assign(Sh::RS_BYTES, 0);
+                const float *wr = src + off_wres(d, b, l), *ws = src + off_wskip(d, b, l);
+                for (int o = 0; o < R; ++o)
+                    for (int k = 0; k < R; ++k) put16(tmp, chunk_off(R, o, k), to_f16(wr[(int64_t)o * R + k]));
+                for (int o = 0; o < S; ++o)
+                    for (int k = 0; k < R; ++k)
+                        put16(tmp, Sh::RES_BYTES + chunk_off(S, o, k), to_f16(ws[(int64_t)o * R + k]));
+                std::memcpy(im0 + (uint64_t)l * Sh::LAYER_IMG + 2ull * Sh::CONV_BYTES + (uint64_t)b * Sh::RS_BYTES,
+                            tmp.data(), tmp.size());
+            }
+        }
+        // head pieces (nh, kh): rows = u channels nh*HP.., k = skip channel of branch kh
+        const float *w1 = src + off_wh1(d);
+        for (int nh = 0; nh < Sh::NH; ++nh)
+            for (int kh = 0; kh < 2; ++kh) {
+                tmp.assign(Sh::HEAD_BYTES, 0);
+                for (int n = 0; n < Sh::HP; ++n)
+                    for (int k = 0; k < S; ++k)
+                        put16(tmp, chunk_off(Sh::HP, n, k), to_f16(w1[(int64_t)(nh * Sh::HP + n) * 2 * S + kh * S + k]));
+                std::memcpy(im0 + (uint64_t)L * Sh::LAYER_IMG + (uint64_t)(nh * 2 + kh) * Sh::HEAD_BYTES, tmp.data(),
+                            tmp.size());
+            }
+        // parameter block
+        uint8_t *pm = pbl.data() + pb_stride * mi;
+        for (int b = 0; b < 2; ++b) {
+            uint8_t *pb = pm + (uint64_t)b * Sh::pb_bytes(L);
+            float *w_in = reinterpret_cast<float *>(pb), *b_in = w_in + R, *bsk = b_in + R;
+            const float *bb = src + off_branch(d, b);
+            for (int c = 0; c < R; ++c) {
+                w_in[c] = bb[c];
+                b_in[c] = bb[R + c];
+            }
+            for (int c = 0; c < S; ++c) {
+                double acc = 0.0;
+                for (int l = 0; l < L; ++l) acc += src[off_bskip(d, b, l) + c];
+                bsk[c] = (float)acc;
+            }
+            for (int l = 0; l < L; ++l) {
+                uint8_t *pl = pb + 8 * R + 4 * S + (uint64_t)l * Sh::PL_BYTES;
+                const float *bc = src + off_bconv(d, b, l);
+                for (int o = 0; o < 2 * R; ++o) {
+                    const uint16_t h = to_f16(o < R ? bc[o] : 0.5f * bc[o]);
+                    std::memcpy(pl + 2 * o, &h, 2);
+                }
+                float *br = reinterpret_cast<float *>(pl + 4 * R);
+                for (int c = 0; c < R; ++c) br[c] = src[off_bres(d, b, l) + c];
+            }
+        }
+        float *ph = reinterpret_cast<float *>(pm + 2ull * Sh::pb_bytes(L));
+        for (int j = 0; j < HC; ++j) {
+            ph[j] = src[off_bh1(d) + j];
+            ph[HC + j] = src[off_wh2(d) + j];
+        }
+        ph[2 * HC] = src[off_bh2(d)];
+    }
+}
+
+template <int R, int S, int HC>
+cudaError_t set_tc_attr() {
+    return cudaFuncSetAttribute(k_branch_tc<R, S, HC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TcShape<R, S, HC>::SMEM);
+}
+
+template <int R, int S, int HC>
+gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL, int64_t nw, int W, int stride,
+                     const int32_t *slides_host, int n_slides, float *out, bool logits, cudaStream_t st) {
+    using Sh = TcShape<R, S, HC>;
+    const Dims &d = m->dims;
+    const int ns = n_slides > 0 ? n_slides : 1;
+    const int64_t n_jobs = (int64_t)ns * d.n_models * nw;
+    if (n_jobs <= 0) return GWE_OK;
+    uint64_t ring_rows = 0;
+    for (int l = 0; l < d.L; ++l) ring_rows += (uint64_t)1 << (l % d.lps);
+    const uint64_t ring_cta = (2 * ring_rows * 2 * R + 255) & ~uint64_t(255);
+    const int grid = (int)std::min<int64_t>(s.sms, n_jobs);
+    GWE_CUDA_TRY(s.ring.ensure(ring_cta * grid));
+    const int32_t *dsl = nullptr;
+    if (n_slides > 0) {
+        GWE_CUDA_TRY(s.slides.ensure(sizeof(int32_t) * n_slides));
+        GWE_CUDA_TRY(cudaMemcpyAsync(s.slides.ptr, slides_host, sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
+        dsl = s.slides.as<int32_t>();
+    }
+    TcParams p;
+    p.wimg = s.img.as<uint8_t>();
+    p.wimg_stride = s.img_stride;
+    p.pblob = s.pblob.as<uint8_t>();
+    p.pblob_stride = s.pblob_stride;
+    p.sH = sH;
+    p.sL = sL;
+    p.nw = nw;
+    p.W = W;
+    p.stride = stride;
+    p.slides = dsl;
+    p.n_slides = n_slides;
+    p.n_models = d.n_models;
+    p.out = out;
+    p.logits = logits ? 1 : 0;
+    p.ring = s.ring.as<uint8_t>();
+    p.ring_cta_bytes = ring_cta;
+    p.zeros = s.zeros.as<uint8_t>();
+    p.L = d.L;
+    p.lps = d.lps;
+    p.ring_rows = ring_rows;
+    p.err = s.err.as<int>();
+    {
+        ProfScope prof("k_branch_tc", st);
+        k_branch_tc<R, S, HC><<<grid, kThreads, Sh::SMEM, st>>>(p);
+        note_launch();
+    }
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
+}  // namespace
+
+bool bf16_supported(const Dims &d) { return tc_variant(d) >= 0 && d.lps <= 10; }
+
+gwe_status bf16_prepare(gwe_model *m, const float *hb) {
+    const Dims &d = m->dims;
+    if (!bf16_supported(d)) {
+        set_error("tensor-core path supports (R, S, Hc) = (32, 32, 32) or (64, 128, 256), kernel 2, "
+                  "layers_per_stack <= 10");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+    if (!s) {
+        s = new TcState();
+        m->bf16 = s;
+    }
+    s->variant = tc_variant(d);
+    std::vector<uint8_t> img, pbl;
+    if (s->variant == 0)
+        build_images<32, 32, 32>(d, hb, img, pbl, s->img_stride, s->pblob_stride);
+    else
+        build_images<64, 128, 256>(d, hb, img, pbl, s->img_stride, s->pblob_stride);
+    GWE_CUDA_TRY(s->img.ensure(img.size()));
+    GWE_CUDA_TRY(cudaMemcpy(s->img.ptr, img.data(), img.size(), cudaMemcpyHostToDevice));
+    GWE_CUDA_TRY(s->pblob.ensure(pbl.size()));
+    GWE_CUDA_TRY(cudaMemcpy(s->pblob.ptr, pbl.data(), pbl.size(), cudaMemcpyHostToDevice));
+    GWE_CUDA_TRY(s->zeros.ensure(4096));
+    GWE_CUDA_TRY(cudaMemset(s->zeros.ptr, 0, 4096));
+    GWE_CUDA_TRY(s->err.ensure(256));
+    GWE_CUDA_TRY(cudaMemset(s->err.ptr, 0, 256));
+    GWE_CUDA_TRY(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, m->device));
+    if (s->variant == 0) {
+        GWE_CUDA_TRY((set_tc_attr<32, 32, 32>()));
+    } else {
+        GWE_CUDA_TRY((set_tc_attr<64, 128, 256>()));
+    }
+    return GWE_OK;
+}
+
+void bf16_release(gwe_model *m) {
+    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+    if (!s) return;
+    s->img.release();
+    s->pblob.release();
+    s->ring.release();
+    s->zeros.release();
+    s->err.release();
+    s->slides.release();
+    delete s;
+    m->bf16 = nullptr;
+}
+
+gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int W, int stride,
+                        int64_t nw, const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st) {
+    (void)n_samples;
+    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+    if (!s || s->variant < 0) {
+        set_error("tensor-core path not prepared");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    if (W % kTile != 0) {
+        set_error("tensor-core path needs window to be a multiple of 128");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    if (s->variant == 0) return launch_tc<32, 32, 32>(m, *s, sH, sL, nw, W, stride, slides, n_slides, out, logits, st);
+    return launch_tc<64, 128, 256>(m, *s, sH, sL, nw, W, stride, slides, n_slides, out, logits, st);
+}
+
+gwe_status bf16_check(gwe_model *m, cudaStream_t st) {
+    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+    if (!s) return GWE_OK;
+    GWE_CUDA_TRY(cudaStreamSynchronize(st));
+    int e = 0;
+    GWE_CUDA_TRY(cudaMemcpy(&e, s->err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        cudaMemset(s->err.ptr, 0, sizeof(int));
+        set_error("a device-side wait of the tensor-core kernel timed out (site " + std::to_string(e) + ")");
+        return GWE_ERR_TIMEOUT;
+    }
+    return GWE_OK;
+}
+
+}  // namespace gwe

@@ -119,7 +119,8 @@ gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
                         int stride, int64_t n_windows, const int32_t *slides, int n_slides, float *out,
                         bool logits, cudaStream_t st);
 
-// bf16_path.cu
+// branch_tc.cu (tensor-core path: GWE_BF16)
+gwe_status bf16_check(gwe_model *m, cudaStream_t st);
 gwe_status bf16_prepare(gwe_model *m, const float *host_blob);
 void bf16_release(gwe_model *m);
 gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
