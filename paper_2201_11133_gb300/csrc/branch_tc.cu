@@ -52,7 +52,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 384;
+constexpr int kThreads = 640;
 constexpr int kTile = 128;
 constexpr int kNEnt = 4;
 constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s per wait
@@ -71,6 +71,8 @@ struct TcShape {
     static constexpr int SC = S / 8;
     static constexpr int NH = HC <= 128 ? 1 : 2;  // head output pieces
     static constexpr int HP = HC / NH;
+    static constexpr int HQ = S / 2;              // K width of one head weight piece
+    static constexpr int NHP = 4 * NH;            // head weight pieces: (nh, K quarter)
     static constexpr uint32_t STAGE_ROWS = 256;
     static constexpr uint32_t STAGE_LBO = STAGE_ROWS * 16;
     static constexpr uint32_t STAGE_BYTES = STAGE_LBO * RC;
@@ -80,32 +82,37 @@ struct TcShape {
     static constexpr uint32_t RES_BYTES = R * R * 2;
     static constexpr uint32_t SKIP_BYTES = S * R * 2;
     static constexpr uint32_t RS_BYTES = RES_BYTES + SKIP_BYTES;
-    static constexpr uint32_t HEAD_BYTES = HP * S * 2;
-    static constexpr uint32_t ENT_BYTES = cmax(CONV_BYTES, cmax(RS_BYTES, HEAD_BYTES));
+    static constexpr uint32_t HEADP_BYTES = HP * HQ * 2;
+    static constexpr uint32_t BIAS_BYTES = 4 * R;   // b_conv as FP16 [2R] or b_res as FP32 [R]
+    static constexpr uint32_t ECONV = cmax(CONV_BYTES, HEADP_BYTES);
+    static constexpr uint32_t ERS = cmax(RS_BYTES, HEADP_BYTES);
     static constexpr uint32_t TMEM_BR = 2 * R + S;
     static constexpr uint32_t TMEM_COLS = pow2ceil(2 * TMEM_BR);
     static constexpr uint32_t TMEM_BSTRIDE = TMEM_COLS / 2;
     // shared memory map
     static constexpr uint32_t OFF_STAGE = 0;
     static constexpr uint32_t OFF_Z = 2 * STAGE_BYTES;
-    static constexpr uint32_t OFF_ENT = OFF_Z + 2 * Z_BYTES;
-    static constexpr uint32_t OFF_PART = OFF_ENT + kNEnt * ENT_BYTES;
-    static constexpr uint32_t OFF_BAR = OFF_PART + 2 * 2 * kTile * 4;
-    static constexpr uint32_t N_BAR = 32;
+    static constexpr uint32_t OFF_ENT = OFF_Z + 2 * Z_BYTES;           // [branch]{conv entry, rs entry}
+    static constexpr uint32_t ENT_BR = ECONV + ERS;
+    static constexpr uint32_t OFF_BIAS = OFF_ENT + 2 * ENT_BR;         // [branch]{b_conv[2 slots], b_res[2 slots]}
+    static constexpr uint32_t BIAS_BR = 4 * BIAS_BYTES;
+    static constexpr uint32_t OFF_PART = OFF_BIAS + 2 * BIAS_BR;
+    static constexpr uint32_t OFF_BAR = OFF_PART + 4 * kTile * 4;
+    static constexpr uint32_t N_BAR = 40;
     static constexpr uint32_t OFF_MISC = OFF_BAR + N_BAR * 8;
     static constexpr uint32_t SMEM = OFF_MISC + 64 + 128;    // + alignment slack
-    // per-branch float parameter block (bytes): w_in[R], b_in[R], bskip_sum[S], then per layer
+    // per-branch parameter block (bytes): w_in[R], b_in[R], bskip_sum[S] (FP32), then per layer
     // b_conv as FP16 [2R] (g half pre-halved) and b_res FP32 [R]
-    static constexpr uint32_t PL_BYTES = 4 * R + 4 * R;
+    static constexpr uint32_t PL_BYTES = 2 * BIAS_BYTES;
     static __host__ __device__ constexpr uint32_t pb_bytes(int L) { return 8 * R + 4 * S + L * PL_BYTES; }
     static __host__ __device__ constexpr uint32_t ph_bytes() { return ((8 * HC + 4) + 15) & ~15u; }
     static __host__ __device__ constexpr uint32_t pm_bytes(int L) { return 2 * pb_bytes(L) + ph_bytes(); }
-    // per-model weight image: per layer [conv H][conv L][rs H][rs L], then head pieces (nh, kh)
+    // per-model weight image: per layer [conv H][conv L][rs H][rs L], then the head pieces
     static constexpr uint32_t LAYER_IMG = 2 * CONV_BYTES + 2 * RS_BYTES;
     static __host__ __device__ constexpr uint64_t img_bytes(int L) {
-        return (uint64_t)L * LAYER_IMG + 2ull * NH * HEAD_BYTES;
+        return (uint64_t)L * LAYER_IMG + (uint64_t)NHP * HEADP_BYTES;
     }
-    static_assert(R % 16 == 0 && S % 16 == 0 && HP % 16 == 0, "channel counts must be multiples of 16");
+    static_assert(R % 16 == 0 && S % 32 == 0 && HP % 16 == 0, "channel counts");
     static_assert(N1 <= 256 && S <= 256 && HP <= 256, "MMA N limit");
     static_assert(HP <= 2 * R, "head piece must fit the conv TMEM columns");
     static_assert(256 * S <= STAGE_BYTES, "head operand must fit one staging buffer");
@@ -115,8 +122,8 @@ struct TcShape {
 
 // barrier indices
 enum {
-    B_WFULL = 0,       // [4]
-    B_WEMPTY = 4,      // [4]
+    B_WFULL = 0,       // [2 branches][2 entries: conv, rs]
+    B_WEMPTY = 4,      // [2][2]
     B_LAG = 8,         // [2]
     B_XREADY = 10,     // [2]
     B_CONV = 12,       // [2]
@@ -126,7 +133,9 @@ enum {
     B_HEAD = 20,
     B_WG = 21,         // [2]
     B_PAIR = 23,
-    B_FIN = 24
+    B_FIN = 24,        // [2]
+    B_BIAS = 26,       // [2 branches][4 slots: b_conv x2, b_res x2]
+    B_GO = 34          // branch 1 may start its tile (branch 0's first gate is done)
 };
 
 struct TcParams {
@@ -210,6 +219,9 @@ __device__ __forceinline__ Job decode_job(const TcParams &p, int64_t j) {
 template <int R, int S, int HC>
 __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
     using Sh = TcShape<R, S, HC>;
+    constexpr int RH = R / 2;          // channels per epilogue thread (half of a row)
+    constexpr int SH = S / 2;
+    constexpr int HPH = Sh::HP / 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Sh::OFF_BAR);
@@ -220,30 +232,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
     const uint32_t s_stage = s_base + Sh::OFF_STAGE;
     const uint32_t s_z = s_base + Sh::OFF_Z;
     const uint32_t s_ent = s_base + Sh::OFF_ENT;
+    const uint32_t s_bias = s_base + Sh::OFF_BIAS;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NT = p.W / kTile;
     const int L = p.L, lps = p.lps;
     const int64_t n_jobs = (int64_t)(p.n_slides > 0 ? p.n_slides : 1) * p.n_models * p.nw;
-    const int items_per_tile = 4 * L + 2 * Sh::NH;
 
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) {
-            mbar_init(&bar[B_WFULL + i], 1);
-            mbar_init(&bar[B_WEMPTY + i], 1);
-        }
         for (int b = 0; b < 2; ++b) {
+            for (int e = 0; e < 2; ++e) {
+                mbar_init(&bar[B_WFULL + 2 * b + e], 1);
+                mbar_init(&bar[B_WEMPTY + 2 * b + e], 1);
+            }
             mbar_init(&bar[B_LAG + b], 1);
-            mbar_init(&bar[B_XREADY + b], 4);
+            mbar_init(&bar[B_XREADY + b], 8);
             mbar_init(&bar[B_CONV + b], 1);
-            mbar_init(&bar[B_ZREADY + b], 4);
+            mbar_init(&bar[B_ZREADY + b], 8);
             mbar_init(&bar[B_RS + b], 1);
-            mbar_init(&bar[B_HREADY + b], 4);
-            mbar_init(&bar[B_WG + b], 4);
+            mbar_init(&bar[B_HREADY + b], 8);
+            mbar_init(&bar[B_WG + b], 8);
+            mbar_init(&bar[B_FIN + b], 1);
+            for (int k = 0; k < 4; ++k) mbar_init(&bar[B_BIAS + 4 * b + k], 1);
         }
         mbar_init(&bar[B_HEAD], 1);
-        mbar_init(&bar[B_PAIR], 8);
-        mbar_init(&bar[B_FIN], 1);
+        mbar_init(&bar[B_PAIR], 16);
+        mbar_init(&bar[B_GO], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -253,177 +267,217 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0) {
-        // ------------------------------------------------------------ weight producer
-        if (lane == 0) {
-            uint32_t item = 0;
-            for (int64_t j = blockIdx.x; j < n_jobs; j += gridDim.x) {
-                const Job q = decode_job(p, j);
-                const uint8_t *wm = p.wimg + (uint64_t)q.m * p.wimg_stride;
-                for (int tt = 0; tt < NT; ++tt) {
-                    for (int i = 0; i < items_per_tile; ++i, ++item) {
-                        const int e = item & 3;
-                        const uint32_t u = item >> 2;
-                        if (!mbar_wait(&bar[B_WEMPTY + e], (u & 1) ^ 1, abort_flag, p.err, 1, kWaitNs)) goto prod_out;
-                        uint64_t off;
-                        uint32_t bytes;
-                        if (i < 4 * L) {
-                            const int l = i >> 2, k = i & 3;
-                            off = (uint64_t)l * Sh::LAYER_IMG;
-                            if (k < 2) {
-                                off += (uint64_t)k * Sh::CONV_BYTES;
-                                bytes = Sh::CONV_BYTES;
+    if (warp < 4) {
+        const int b = warp >> 1;               // branch served by this warp
+        if ((warp & 1) == 0) {
+            // -------------------------------------------------------- producer of branch b
+            // Per tile and layer: that layer's weights (+ biases) into the branch's conv and rs
+            // entries, and the lagged rows of the layer into the staging buffer; branch 0 also
+            // streams the head weight pieces through its two entries.
+            if (lane == 0) {
+                uint32_t it[2] = {0, 0};       // items issued per entry
+                uint32_t lag_issued = 0, ph_h = 0, g = 0;
+                bool ok = true, first = true;
+                uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * (2 * R);
+                auto take = [&](int e, int site) -> bool {
+                    return mbar_wait(&bar[B_WEMPTY + 2 * b + e], ((it[e] & 1) ^ 1), abort_flag, p.err, site, kWaitNs);
+                };
+                auto issue_lag = [&](int l, int t0) {
+                    const int d = 1 << (l % lps);
+                    const int n = d < kTile ? d : kTile;
+                    const uint32_t bytes = (uint32_t)n * 16;
+                    mbar_arrive_expect_tx(&bar[B_LAG + b], bytes * Sh::RC);
+                    const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
+                    const uint8_t *src = ring_b + roff * (2 * R) + (uint64_t)(t0 & (d - 1)) * 16;
+                    uint8_t *dst0 = smem + Sh::OFF_STAGE + b * Sh::STAGE_BYTES + (kTile - n) * 16;
+#pragma unroll
+                    for (int c = 0; c < Sh::RC; ++c)
+                        bulk_g2s(dst0 + c * Sh::STAGE_LBO, (t0 < d) ? p.zeros : src + (uint64_t)c * d * 16, bytes,
+                                 &bar[B_LAG + b]);
+                    ++lag_issued;
+                };
+                for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
+                    const Job q = decode_job(p, j);
+                    const uint8_t *wm = p.wimg + (uint64_t)q.m * p.wimg_stride;
+                    const uint8_t *play = p.pblob + (uint64_t)q.m * p.pblob_stride + b * Sh::pb_bytes(L) + 8 * R + 4 * S;
+                    for (int tt = 0; tt < NT && ok; ++tt) {
+                        for (int l = 0; l < L; ++l, ++g) {
+                            // conv entry: free once the previous conv (or head piece) MMA completed
+                            if (!(ok = take(0, 1))) break;
+                            mbar_arrive_expect_tx(&bar[B_WFULL + 2 * b + 0], Sh::CONV_BYTES);
+                            bulk_g2s(smem + Sh::OFF_ENT + b * Sh::ENT_BR,
+                                     wm + (uint64_t)l * Sh::LAYER_IMG + (uint64_t)b * Sh::CONV_BYTES, Sh::CONV_BYTES,
+                                     &bar[B_WFULL + 2 * b + 0]);
+                            // b_conv of this layer into slot g & 1 (its previous reader, the gate two
+                            // layers back, finished before the conv that just freed the entry)
+                            mbar_arrive_expect_tx(&bar[B_BIAS + 4 * b + (g & 1)], Sh::BIAS_BYTES);
+                            bulk_g2s(smem + Sh::OFF_BIAS + b * Sh::BIAS_BR + (g & 1) * Sh::BIAS_BYTES,
+                                     play + (uint64_t)l * Sh::PL_BYTES, Sh::BIAS_BYTES, &bar[B_BIAS + 4 * b + (g & 1)]);
+                            ++it[0];
+                            // lagged rows: the staging buffer is free once the previous conv completed
+                            // (layer 0: once the previous tile's head has read it)
+                            if (l > 0 || first) {
+                                issue_lag(l, tt * kTile);
                             } else {
-                                off += 2ull * Sh::CONV_BYTES + (uint64_t)(k - 2) * Sh::RS_BYTES;
-                                bytes = Sh::RS_BYTES;
+                                ok = mbar_wait(&bar[B_HREADY + b], ph_h & 1, abort_flag, p.err, 3, kWaitNs) &&
+                                     mbar_wait(&bar[B_HEAD], ph_h & 1, abort_flag, p.err, 4, kWaitNs);
+                                if (!ok) break;
+                                ++ph_h;
+                                issue_lag(0, tt * kTile);
                             }
-                        } else {
-                            off = (uint64_t)L * Sh::LAYER_IMG + (uint64_t)(i - 4 * L) * Sh::HEAD_BYTES;
-                            bytes = Sh::HEAD_BYTES;
+                            first = false;
+                            // rs entry
+                            if (!(ok = take(1, 5))) break;
+                            mbar_arrive_expect_tx(&bar[B_WFULL + 2 * b + 1], Sh::RS_BYTES);
+                            bulk_g2s(smem + Sh::OFF_ENT + b * Sh::ENT_BR + Sh::ECONV,
+                                     wm + (uint64_t)l * Sh::LAYER_IMG + 2ull * Sh::CONV_BYTES + (uint64_t)b * Sh::RS_BYTES,
+                                     Sh::RS_BYTES, &bar[B_WFULL + 2 * b + 1]);
+                            mbar_arrive_expect_tx(&bar[B_BIAS + 4 * b + 2 + (g & 1)], Sh::BIAS_BYTES);
+                            bulk_g2s(smem + Sh::OFF_BIAS + b * Sh::BIAS_BR + (2 + (g & 1)) * Sh::BIAS_BYTES,
+                                     play + (uint64_t)l * Sh::PL_BYTES + Sh::BIAS_BYTES, Sh::BIAS_BYTES,
+                                     &bar[B_BIAS + 4 * b + 2 + (g & 1)]);
+                            ++it[1];
                         }
-                        mbar_arrive_expect_tx(&bar[B_WFULL + e], bytes);
-                        bulk_g2s(smem + Sh::OFF_ENT + e * Sh::ENT_BYTES, wm + off, bytes, &bar[B_WFULL + e]);
+                        if (!ok || b != 0) continue;
+                        for (int pc = 0; pc < Sh::NHP; ++pc) {
+                            const int e = pc & 1;
+                            if (!(ok = take(e, 6))) break;
+                            mbar_arrive_expect_tx(&bar[B_WFULL + e], Sh::HEADP_BYTES);
+                            bulk_g2s(smem + Sh::OFF_ENT + e * Sh::ECONV,
+                                     wm + (uint64_t)L * Sh::LAYER_IMG + (uint64_t)pc * Sh::HEADP_BYTES, Sh::HEADP_BYTES,
+                                     &bar[B_WFULL + e]);
+                            ++it[e];
+                        }
                     }
                 }
+                // never leave with copies in flight
+                for (int e = 0; e < 2; ++e)
+                    if (it[e] > 0)
+                        mbar_wait(&bar[B_WFULL + 2 * b + e], (it[e] - 1) & 1, abort_flag, p.err, 7, kWaitNs);
+                if (lag_issued > 0)
+                    mbar_wait(&bar[B_LAG + b], (lag_issued - 1) & 1, abort_flag, p.err, 8, kWaitNs);
+                for (uint32_t k = 0; k < 2 && k < g; ++k) {       // last b_conv / b_res of both slots
+                    const uint32_t gg = g - 1 - k;
+                    mbar_wait(&bar[B_BIAS + 4 * b + (gg & 1)], (gg >> 1) & 1, abort_flag, p.err, 9, kWaitNs);
+                    mbar_wait(&bar[B_BIAS + 4 * b + 2 + (gg & 1)], (gg >> 1) & 1, abort_flag, p.err, 9, kWaitNs);
+                }
             }
-        prod_out:
-            // never leave with copies in flight: the last copy of every entry must have landed
-            for (int k = 0; k < 4 && k < (int)item; ++k) {
-                const uint32_t it = item - 1 - k;
-                mbar_wait(&bar[B_WFULL + (it & 3)], (it >> 2) & 1, abort_flag, p.err, 2, kWaitNs);
-            }
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t ID_CONV = idesc_f16(128, Sh::N1, 1);
-            constexpr uint32_t ID_RES = idesc_f16(128, R, 0);
-            constexpr uint32_t ID_SKIP = idesc_f16(128, S, 0);
-            constexpr uint32_t ID_HEAD = idesc_f16(128, Sh::HP, 0);
-            uint32_t item = 0, ph_x[2] = {0, 0}, ph_lag[2] = {0, 0}, ph_z[2] = {0, 0}, ph_h[2] = {0, 0};
-            bool ok = true;
-            for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
-                for (int tt = 0; tt < NT && ok; ++tt) {
-                    for (int l = 0; l < L && ok; ++l) {
-                        const int d = 1 << (l % lps);
-                        const int n = d < kTile ? d : kTile;
-                        for (int b = 0; b < 2 && ok; ++b) {
-                            const int e = item & 3;
-                            ok = mbar_wait(&bar[B_XREADY + b], ph_x[b] & 1, abort_flag, p.err, 10, kWaitNs) &&
-                                 mbar_wait(&bar[B_LAG + b], ph_lag[b] & 1, abort_flag, p.err, 11, kWaitNs) &&
-                                 mbar_wait(&bar[B_WFULL + e], (item >> 2) & 1, abort_flag, p.err, 12, kWaitNs);
+        } else {
+            // -------------------------------------------------------- MMA issuer of branch b (+ head on branch 0)
+            if (lane == 0) {
+                constexpr uint32_t ID_CONV = idesc_f16(128, Sh::N1, 1);
+                constexpr uint32_t ID_RES = idesc_f16(128, R, 0);
+                constexpr uint32_t ID_SKIP = idesc_f16(128, S, 0);
+                constexpr uint32_t ID_HEAD = idesc_f16(128, Sh::HP, 0);
+                uint32_t it[2] = {0, 0}, ph_x = 0, ph_lag = 0, ph_z = 0, ph_h = 0, ph_go = 0;
+                bool ok = true;
+                const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
+                const uint32_t zb = s_z + b * Sh::Z_BYTES;
+                const uint32_t dcol = tmem + b * Sh::TMEM_BSTRIDE;
+                const uint32_t e_conv = s_ent + b * Sh::ENT_BR, e_rs = e_conv + Sh::ECONV;
+                for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
+                    for (int tt = 0; tt < NT && ok; ++tt) {
+                        // Ping-pong: branch 1 starts a tile once branch 0's first gate is done, so
+                        // that one branch's MMAs overlap the other's gate for the rest of the tile.
+                        if (b == 1) {
+                            if (!(ok = mbar_wait(&bar[B_GO], ph_go & 1, abort_flag, p.err, 19, kWaitNs))) break;
+                            ++ph_go;
+                        }
+                        for (int l = 0; l < L; ++l) {
+                            const int d = 1 << (l % lps);
+                            const int n = d < kTile ? d : kTile;
+                            ok = mbar_wait(&bar[B_XREADY + b], ph_x & 1, abort_flag, p.err, 10, kWaitNs) &&
+                                 mbar_wait(&bar[B_LAG + b], ph_lag & 1, abort_flag, p.err, 11, kWaitNs) &&
+                                 mbar_wait(&bar[B_WFULL + 2 * b], it[0] & 1, abort_flag, p.err, 12, kWaitNs);
                             if (!ok) break;
-                            ++ph_x[b];
-                            ++ph_lag[b];
+                            ++ph_x;
+                            ++ph_lag;
                             tc_fence_after();
-                            const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
-                            const uint32_t we = s_ent + e * Sh::ENT_BYTES;
-                            const uint32_t dcol = tmem + b * Sh::TMEM_BSTRIDE;
 #pragma unroll
-                            for (int ks = 0; ks < Sh::RC; ++ks) {       // K = 2R in steps of 16
+                            for (int ks = 0; ks < Sh::RC; ++ks) {   // K = 2R in steps of 16
                                 uint64_t ad;
                                 if (ks < Sh::RC / 2)
                                     ad = sdesc(st + 2 * ks * Sh::STAGE_LBO + (kTile - n) * 16, Sh::STAGE_LBO, 128);
                                 else
                                     ad = sdesc(st + (2 * ks - Sh::RC) * Sh::STAGE_LBO + kTile * 16, Sh::STAGE_LBO, 128);
-                                const uint64_t bd = sdesc(we + 2 * ks * (Sh::N1 * 16), Sh::N1 * 16, 128);
+                                const uint64_t bd = sdesc(e_conv + 2 * ks * (Sh::N1 * 16), Sh::N1 * 16, 128);
                                 mma_f16(dcol, ad, bd, ID_CONV, ks > 0 ? 1u : 0u);
                             }
                             mma_commit(&bar[B_CONV + b]);
-                            mma_commit(&bar[B_WEMPTY + e]);
-                            ++item;
-                        }
-                        for (int b = 0; b < 2 && ok; ++b) {
-                            const int e = item & 3;
-                            ok = mbar_wait(&bar[B_ZREADY + b], ph_z[b] & 1, abort_flag, p.err, 13, kWaitNs) &&
-                                 mbar_wait(&bar[B_WFULL + e], (item >> 2) & 1, abort_flag, p.err, 14, kWaitNs);
+                            mma_commit(&bar[B_WEMPTY + 2 * b]);
+                            ++it[0];
+                            ok = mbar_wait(&bar[B_ZREADY + b], ph_z & 1, abort_flag, p.err, 13, kWaitNs) &&
+                                 mbar_wait(&bar[B_WFULL + 2 * b + 1], it[1] & 1, abort_flag, p.err, 14, kWaitNs);
                             if (!ok) break;
-                            ++ph_z[b];
+                            ++ph_z;
+                            if (b == 0 && l == 0) mbar_arrive(&bar[B_GO]);
                             tc_fence_after();
-                            const uint32_t zb = s_z + b * Sh::Z_BYTES;
-                            const uint32_t we = s_ent + e * Sh::ENT_BYTES;
-                            const uint32_t dcol = tmem + b * Sh::TMEM_BSTRIDE;
 #pragma unroll
                             for (int ks = 0; ks < Sh::RC / 2; ++ks) {
                                 const uint64_t ad = sdesc(zb + 2 * ks * Sh::Z_LBO, Sh::Z_LBO, 128);
-                                const uint64_t bd = sdesc(we + 2 * ks * (R * 16), R * 16, 128);
+                                const uint64_t bd = sdesc(e_rs + 2 * ks * (R * 16), R * 16, 128);
                                 mma_f16(dcol, ad, bd, ID_RES, ks > 0 ? 1u : 0u);
                             }
 #pragma unroll
                             for (int ks = 0; ks < Sh::RC / 2; ++ks) {
                                 const uint64_t ad = sdesc(zb + 2 * ks * Sh::Z_LBO, Sh::Z_LBO, 128);
-                                const uint64_t bd = sdesc(we + Sh::RES_BYTES + 2 * ks * (S * 16), S * 16, 128);
+                                const uint64_t bd = sdesc(e_rs + Sh::RES_BYTES + 2 * ks * (S * 16), S * 16, 128);
                                 mma_f16(dcol + 2 * R, ad, bd, ID_SKIP, (l > 0 || ks > 0) ? 1u : 0u);
                             }
                             mma_commit(&bar[B_RS + b]);
-                            mma_commit(&bar[B_WEMPTY + e]);
-                            ++item;
+                            mma_commit(&bar[B_WEMPTY + 2 * b + 1]);
+                            ++it[1];
                         }
-                    }
-                    if (!ok) break;
-                    // head: u[piece nh] = sum over kh of h_kh . W_h1[nh, kh]^T
-                    ok = mbar_wait(&bar[B_HREADY + 0], ph_h[0] & 1, abort_flag, p.err, 15, kWaitNs) &&
-                         mbar_wait(&bar[B_HREADY + 1], ph_h[1] & 1, abort_flag, p.err, 16, kWaitNs);
-                    if (!ok) break;
-                    ++ph_h[0];
-                    ++ph_h[1];
-                    for (int nh = 0; nh < Sh::NH && ok; ++nh) {
-                        for (int kh = 0; kh < 2; ++kh) {
-                            const int e = item & 3;
-                            ok = mbar_wait(&bar[B_WFULL + e], (item >> 2) & 1, abort_flag, p.err, 17, kWaitNs);
+                        if (!ok || b != 0) continue;
+                        // head (branch 0's MMA warp): u[nh] = sum over K quarters of h . W_h1[nh, quarter]^T
+                        ok = mbar_wait(&bar[B_HREADY + 0], ph_h & 1, abort_flag, p.err, 15, kWaitNs) &&
+                             mbar_wait(&bar[B_HREADY + 1], ph_h & 1, abort_flag, p.err, 16, kWaitNs);
+                        if (!ok) break;
+                        ++ph_h;
+                        for (int pc = 0; pc < Sh::NHP && ok; ++pc) {
+                            const int e = pc & 1, nh = pc >> 2, kq = pc & 3;
+                            ok = mbar_wait(&bar[B_WFULL + e], it[e] & 1, abort_flag, p.err, 17, kWaitNs);
                             if (!ok) break;
                             tc_fence_after();
-                            const uint32_t ha = s_stage + kh * Sh::STAGE_BYTES;
-                            const uint32_t we = s_ent + e * Sh::ENT_BYTES;
+                            const uint32_t ha = s_stage + (kq >> 1) * Sh::STAGE_BYTES + (kq & 1) * (Sh::HQ / 8) * (kTile * 16);
+                            const uint32_t we = s_ent + e * Sh::ECONV;
 #pragma unroll
-                            for (int ks = 0; ks < Sh::SC / 2; ++ks) {
+                            for (int ks = 0; ks < Sh::HQ / 16; ++ks) {
                                 const uint64_t ad = sdesc(ha + 2 * ks * (kTile * 16), kTile * 16, 128);
                                 const uint64_t bd = sdesc(we + 2 * ks * (Sh::HP * 16), Sh::HP * 16, 128);
-                                mma_f16(tmem + nh * Sh::TMEM_BSTRIDE, ad, bd, ID_HEAD, (kh > 0 || ks > 0) ? 1u : 0u);
+                                mma_f16(tmem + nh * Sh::TMEM_BSTRIDE, ad, bd, ID_HEAD, (kq > 0 || ks > 0) ? 1u : 0u);
                             }
                             mma_commit(&bar[B_WEMPTY + e]);
-                            ++item;
+                            ++it[e];
                         }
+                        if (ok) mma_commit(&bar[B_HEAD]);
                     }
-                    if (ok) mma_commit(&bar[B_HEAD]);
                 }
+                // all MMAs issued by this thread complete before TMEM is released
+                mma_commit(&bar[B_FIN + b]);
+                mbar_wait(&bar[B_FIN + b], 0, abort_flag, p.err, 18, kWaitNs);
             }
-            // all MMAs issued by this thread complete before TMEM is released
-            mma_commit(&bar[B_FIN]);
-            mbar_wait(&bar[B_FIN], 0, abort_flag, p.err, 18, kWaitNs);
         }
-    } else if (warp >= 4) {
-        // ------------------------------------------------------------ epilogue (thread = row)
-        const int b = (warp - 4) >> 2;                 // 0: Hanford branch, 1: Livingston branch
+    } else {
+        // ------------------------------------------------------------ epilogue (thread = row, half the channels)
+        const int eg = warp - 4;
+        const int b = eg >> 3;                         // 0: Hanford branch, 1: Livingston branch
+        const int hf = (eg >> 2) & 1;                  // channel half
         const int q = warp & 3;                        // TMEM lane quarter of this warp
         const int r = q * 32 + lane;                   // row within the tile
-        const bool leader = (r == 0);
         const uint32_t t_lane = (uint32_t)(q * 32) << 16;
         const uint32_t t_conv = tmem + t_lane + b * Sh::TMEM_BSTRIDE;
         const uint32_t t_skip = t_conv + 2 * R;
         const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
         const uint32_t zb = s_z + b * Sh::Z_BYTES;
+        const uint32_t sb = s_bias + b * Sh::BIAS_BR;
+        const int c0 = hf * RH;                        // first channel of this thread
         uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * (2 * R);
-        uint32_t ph_conv = 0, ph_rs = 0, ph_head = 0, ph_wg = 0, ph_pair = 0, lag_issued = 0, tiles = 0;
+        uint32_t ph_conv = 0, ph_rs = 0, ph_head = 0, ph_wg = 0, ph_pair = 0, tiles = 0;
         bool ok = true;
-        float x[R];
+        float x[RH];
         const uint32_t half2_half = 0x38003800u;     // (0.5, 0.5) in FP16x2
 
-        // lagged rows of layer l for the tile at t0 -> staging rows [128 - n, 128)
-        auto issue_lag = [&](int l, int t0) {
-            const int d = 1 << (l % lps);
-            const int n = d < kTile ? d : kTile;
-            const uint32_t bytes = (uint32_t)n * 16;
-            mbar_arrive_expect_tx(&bar[B_LAG + b], bytes * Sh::RC);
-            const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
-            const uint8_t *src = ring_b + roff * (2 * R) + (uint64_t)(t0 & (d - 1)) * 16;
-            uint8_t *dst0 = smem + Sh::OFF_STAGE + b * Sh::STAGE_BYTES + (kTile - n) * 16;
-#pragma unroll
-            for (int c = 0; c < Sh::RC; ++c)
-                bulk_g2s(dst0 + c * Sh::STAGE_LBO, (t0 < d) ? p.zeros : src + (uint64_t)c * d * 16, bytes,
-                         &bar[B_LAG + b]);
-            ++lag_issued;
-        };
         auto warp_wait = [&](int idx, uint32_t parity, int site) -> bool {
             bool w = mbar_wait(&bar[idx], parity, abort_flag, p.err, site, kWaitNs);
             return __all_sync(0xffffffffu, w);
@@ -434,25 +488,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
         };
         auto store_x = [&]() {
 #pragma unroll
-            for (int c = 0; c < Sh::RC; ++c) {
+            for (int c = 0; c < RH / 8; ++c) {
                 uint4 v;
                 v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
                 v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
                 v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
                 v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
-                sts128(st + c * Sh::STAGE_LBO + (kTile + r) * 16, v);
+                sts128(st + (hf * (RH / 8) + c) * Sh::STAGE_LBO + (kTile + r) * 16, v);
             }
         };
+        // z for 16 channels starting at ch from the f / g accumulator columns
+        auto gate16 = [&](const uint32_t (&fr)[16], const uint32_t (&gr)[16], int ch, uint32_t bslot) {
+            const uint4 bf0 = lds128(bslot + ch * 2), bf1 = lds128(bslot + ch * 2 + 16);
+            const uint4 bg0 = lds128(bslot + (R + ch) * 2), bg1 = lds128(bslot + (R + ch) * 2 + 16);
+            const uint32_t bfw[8] = {bf0.x, bf0.y, bf0.z, bf0.w, bf1.x, bf1.y, bf1.z, bf1.w};
+            const uint32_t bgw[8] = {bg0.x, bg0.y, bg0.z, bg0.w, bg1.x, bg1.y, bg1.z, bg1.w};
+            uint32_t zz[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const uint32_t hfv = hadd2(pack_h2(__uint_as_float(fr[2 * jj]), __uint_as_float(fr[2 * jj + 1])), bfw[jj]);
+                const uint32_t hgv = hadd2(pack_h2(__uint_as_float(gr[2 * jj]), __uint_as_float(gr[2 * jj + 1])), bgw[jj]);
+                const uint32_t sg = hfma2(tanh_h2(hgv), half2_half, half2_half);
+                zz[jj] = hmul2(tanh_h2(hfv), sg);
+            }
+            sts128(zb + (ch / 8) * Sh::Z_LBO + r * 16, make_uint4(zz[0], zz[1], zz[2], zz[3]));
+            sts128(zb + (ch / 8 + 1) * Sh::Z_LBO + r * 16, make_uint4(zz[4], zz[5], zz[6], zz[7]));
+        };
 
-        if (leader && (int64_t)blockIdx.x < n_jobs) issue_lag(0, 0);
         for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
             const Job jb = decode_job(p, j);
             const uint8_t *pm = p.pblob + (uint64_t)jb.m * p.pblob_stride;
             const uint8_t *pbr = pm + b * Sh::pb_bytes(L);
-            const float4 *w_in4 = reinterpret_cast<const float4 *>(pbr);
-            const float4 *b_in4 = w_in4 + R / 4;
-            const float4 *bsk4 = b_in4 + R / 4;
-            const uint8_t *play = pbr + 8 * R + 4 * S;
+            const float4 *w_in4 = reinterpret_cast<const float4 *>(pbr) + c0 / 4;
+            const float4 *b_in4 = reinterpret_cast<const float4 *>(pbr) + R / 4 + c0 / 4;
+            const float4 *bsk4 = reinterpret_cast<const float4 *>(pbr) + R / 2 + hf * (SH / 4);
             const float *phd = reinterpret_cast<const float *>(pm + 2 * Sh::pb_bytes(L));
             const float *b1 = phd, *w2 = phd + HC;
             const float b2 = __ldg(phd + 2 * HC);
@@ -464,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 {
                     const float sval = __ldg(sv + t0 + r);
 #pragma unroll
-                    for (int c4 = 0; c4 < R / 4; ++c4) {
+                    for (int c4 = 0; c4 < RH / 4; ++c4) {
                         const float4 wi = __ldg(w_in4 + c4), bi = __ldg(b_in4 + c4);
                         x[4 * c4 + 0] = fmaf(wi.x, sval, bi.x);
                         x[4 * c4 + 1] = fmaf(wi.y, sval, bi.y);
@@ -479,66 +548,63 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 for (int l = 0; l < L; ++l) {
                     const int d = 1 << (l % lps);
                     const int n = d < kTile ? d : kTile;
-                    if (!warp_wait(B_CONV + b, ph_conv & 1, 30)) { ok = false; break; }
+                    const uint32_t g = tiles * (uint32_t)L + l;   // layer ordinal: bias slot g & 1, use (g >> 1)
+                    if (!warp_wait(B_CONV + b, ph_conv & 1, 30) ||
+                        !warp_wait(B_BIAS + 4 * b + (g & 1), (g >> 1) & 1, 36)) { ok = false; break; }
                     ++ph_conv;
                     tc_fence_after();
-                    if (leader && l + 1 < L) issue_lag(l + 1, t0);
                     // lag history of layer l for the following tiles: rows t0+r, r >= 128 - n
                     if (tt + 1 < NT && r >= kTile - n) {
                         const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
                         uint8_t *dst = ring_b + roff * (2 * R) + (uint64_t)((t0 + r) & (d - 1)) * 16;
 #pragma unroll
-                        for (int c = 0; c < Sh::RC; ++c) {
+                        for (int c = hf * (Sh::RC / 2); c < (hf + 1) * (Sh::RC / 2); ++c) {
                             const uint4 v = lds128(st + c * Sh::STAGE_LBO + (kTile + r) * 16);
                             *reinterpret_cast<uint4 *>(dst + (uint64_t)c * d * 16) = v;
                         }
-                        fence_proxy_async_global();
                     }
                     // gate: z = tanh(f + b_f) * (0.5 tanh(g/2 + b_g/2) + 0.5), FP16x2
-                    const uint4 *bc4 = reinterpret_cast<const uint4 *>(play + (uint64_t)l * Sh::PL_BYTES);
-#pragma unroll
-                    for (int cc = 0; cc < R / 16; ++cc) {
-                        uint32_t fr[16], gr[16];
-                        tmem_ld16(t_conv + 16 * cc, fr);
-                        tmem_ld16(t_conv + R + 16 * cc, gr);
-                        const uint4 bf0 = __ldg(bc4 + 2 * cc), bf1 = __ldg(bc4 + 2 * cc + 1);
-                        const uint4 bg0 = __ldg(bc4 + R / 8 + 2 * cc), bg1 = __ldg(bc4 + R / 8 + 2 * cc + 1);
+                    {
+                        const uint32_t bslot = sb + (g & 1) * Sh::BIAS_BYTES;
+                        uint32_t fa[16], ga[16];
+                        tmem_ld16(t_conv + c0, fa);
+                        tmem_ld16(t_conv + R + c0, ga);
                         tmem_ld_wait();
-                        const uint32_t bfw[8] = {bf0.x, bf0.y, bf0.z, bf0.w, bf1.x, bf1.y, bf1.z, bf1.w};
-                        const uint32_t bgw[8] = {bg0.x, bg0.y, bg0.z, bg0.w, bg1.x, bg1.y, bg1.z, bg1.w};
-                        uint32_t zz[8];
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) {
-                            const uint32_t hf = hadd2(pack_h2(__uint_as_float(fr[2 * jj]), __uint_as_float(fr[2 * jj + 1])), bfw[jj]);
-                            const uint32_t hg = hadd2(pack_h2(__uint_as_float(gr[2 * jj]), __uint_as_float(gr[2 * jj + 1])), bgw[jj]);
-                            const uint32_t sg = hfma2(tanh_h2(hg), half2_half, half2_half);
-                            zz[jj] = hmul2(tanh_h2(hf), sg);
+                        if constexpr (RH == 32) {
+                            uint32_t fb[16], gbv[16];
+                            tmem_ld16(t_conv + c0 + 16, fb);
+                            tmem_ld16(t_conv + R + c0 + 16, gbv);
+                            gate16(fa, ga, c0, bslot);
+                            tmem_ld_wait();
+                            gate16(fb, gbv, c0 + 16, bslot);
+                        } else {
+                            gate16(fa, ga, c0, bslot);
                         }
-                        sts128(zb + (2 * cc) * Sh::Z_LBO + r * 16, make_uint4(zz[0], zz[1], zz[2], zz[3]));
-                        sts128(zb + (2 * cc + 1) * Sh::Z_LBO + r * 16, make_uint4(zz[4], zz[5], zz[6], zz[7]));
                     }
                     fence_proxy_async_smem();
                     tc_fence_before();
                     warp_arrive(B_ZREADY + b);
-                    if (!warp_wait(B_RS + b, ph_rs & 1, 31)) { ok = false; break; }
+                    if (!warp_wait(B_RS + b, ph_rs & 1, 31) ||
+                        !warp_wait(B_BIAS + 4 * b + 2 + (g & 1), (g >> 1) & 1, 37)) { ok = false; break; }
                     ++ph_rs;
                     tc_fence_after();
                     if (l + 1 < L) {
                         // residual: x_{l+1} = x_l + (W_res z) + b_res  (FP32)
-                        const float4 *br4 = reinterpret_cast<const float4 *>(play + (uint64_t)l * Sh::PL_BYTES + 4 * R);
+                        const uint32_t bres = sb + (2 + (g & 1)) * Sh::BIAS_BYTES + c0 * 4;
+                        uint32_t rr[RH];
+                        if constexpr (RH == 32) {
+                            tmem_ld32(t_conv + c0, rr);
+                        } else {
+                            tmem_ld16(t_conv + c0, rr);
+                        }
+                        tmem_ld_wait();
 #pragma unroll
-                        for (int cc = 0; cc < R / 16; ++cc) {
-                            uint32_t rr[16];
-                            tmem_ld16(t_conv + 16 * cc, rr);
-                            tmem_ld_wait();
-#pragma unroll
-                            for (int k4 = 0; k4 < 4; ++k4) {
-                                const float4 bb = __ldg(br4 + 4 * cc + k4);
-                                x[16 * cc + 4 * k4 + 0] += __uint_as_float(rr[4 * k4 + 0]) + bb.x;
-                                x[16 * cc + 4 * k4 + 1] += __uint_as_float(rr[4 * k4 + 1]) + bb.y;
-                                x[16 * cc + 4 * k4 + 2] += __uint_as_float(rr[4 * k4 + 2]) + bb.z;
-                                x[16 * cc + 4 * k4 + 3] += __uint_as_float(rr[4 * k4 + 3]) + bb.w;
-                            }
+                        for (int k4 = 0; k4 < RH / 4; ++k4) {
+                            const uint4 bb = lds128(bres + 16 * k4);
+                            x[4 * k4 + 0] += __uint_as_float(rr[4 * k4 + 0]) + __uint_as_float(bb.x);
+                            x[4 * k4 + 1] += __uint_as_float(rr[4 * k4 + 1]) + __uint_as_float(bb.y);
+                            x[4 * k4 + 2] += __uint_as_float(rr[4 * k4 + 2]) + __uint_as_float(bb.z);
+                            x[4 * k4 + 3] += __uint_as_float(rr[4 * k4 + 3]) + __uint_as_float(bb.w);
                         }
                         store_x();
                         fence_proxy_async_smem();
@@ -547,15 +613,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     }
                 }
                 if (!ok) break;
+                // history rows written with ordinary stores are read by bulk copies of later tiles
+                fence_proxy_async_global();
                 // every row's history copy has read the staging buffer before it becomes the head operand
                 warp_arrive(B_WG + b);
                 if (!warp_wait(B_WG + b, ph_wg & 1, 32)) { ok = false; break; }
                 ++ph_wg;
                 // head operand h = ReLU(skip + sum of skip biases), FP16, rows-128 layout in this branch's staging buffer
 #pragma unroll
-                for (int cc = 0; cc < S / 16; ++cc) {
+                for (int cc = 0; cc < SH / 16; ++cc) {
+                    const int ch = hf * SH + 16 * cc;
                     uint32_t sr[16];
-                    tmem_ld16(t_skip + 16 * cc, sr);
+                    tmem_ld16(t_skip + ch, sr);
                     tmem_ld_wait();
                     float h[16];
 #pragma unroll
@@ -566,9 +635,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         h[4 * k4 + 2] = fmaxf(__uint_as_float(sr[4 * k4 + 2]) + bs.z, 0.f);
                         h[4 * k4 + 3] = fmaxf(__uint_as_float(sr[4 * k4 + 3]) + bs.w, 0.f);
                     }
-                    sts128(st + (2 * cc) * (kTile * 16) + r * 16,
+                    sts128(st + (ch / 8) * (kTile * 16) + r * 16,
                            make_uint4(pack_h2(h[0], h[1]), pack_h2(h[2], h[3]), pack_h2(h[4], h[5]), pack_h2(h[6], h[7])));
-                    sts128(st + (2 * cc + 1) * (kTile * 16) + r * 16,
+                    sts128(st + (ch / 8 + 1) * (kTile * 16) + r * 16,
                            make_uint4(pack_h2(h[8], h[9]), pack_h2(h[10], h[11]), pack_h2(h[12], h[13]),
                                       pack_h2(h[14], h[15])));
                 }
@@ -578,42 +647,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 if (!warp_wait(B_HEAD, ph_head & 1, 33)) { ok = false; break; }
                 ++ph_head;
                 tc_fence_after();
-                // the staging buffer is free again: bring in the next tile's layer-0 history
-                if (leader) {
-                    if (tt + 1 < NT) issue_lag(0, t0 + kTile);
-                    else if (j + (int64_t)gridDim.x < n_jobs) issue_lag(0, 0);
-                }
                 float acc = 0.f;
                 if (b < Sh::NH) {
-                    const uint32_t t_u = tmem + t_lane + b * Sh::TMEM_BSTRIDE;
+                    const uint32_t t_u = tmem + t_lane + b * Sh::TMEM_BSTRIDE + hf * HPH;
 #pragma unroll
-                    for (int cc = 0; cc < Sh::HP / 16; ++cc) {
+                    for (int cc = 0; cc < HPH / 16; ++cc) {
                         uint32_t ur[16];
                         tmem_ld16(t_u + 16 * cc, ur);
                         tmem_ld_wait();
 #pragma unroll
                         for (int jj = 0; jj < 16; ++jj) {
-                            const int ch = b * Sh::HP + 16 * cc + jj;
+                            const int ch = b * Sh::HP + hf * HPH + 16 * cc + jj;
                             const float u = __uint_as_float(ur[jj]) + __ldg(b1 + ch);
                             acc = fmaf(__ldg(w2 + ch), fmaxf(u, 0.f), acc);
                         }
                     }
                 }
-                float *pp = part + (tiles & 1) * 2 * kTile;
-                pp[b * kTile + r] = acc;
+                // single buffer: no warp can write the next tile's partials before this tile's
+                // are read, since the next head needs this reader's rows of the next tile first
+                float *pp = part;
+                pp[(2 * b + hf) * kTile + r] = acc;
                 tc_fence_before();
                 warp_arrive(B_PAIR);
                 if (!warp_wait(B_PAIR, ph_pair & 1, 34)) { ok = false; break; }
                 ++ph_pair;
-                if (b == 0) {
-                    const float lg = (pp[r] + pp[kTile + r]) + b2;
+                if (b == 0 && hf == 0) {
+                    const float lg = ((pp[r] + pp[kTile + r]) + (pp[2 * kTile + r] + pp[3 * kTile + r])) + b2;
                     outp[t0 + r] = p.logits ? lg : 1.f / (1.f + expf(-lg));
                 }
             }
         }
-        // never leave with history copies in flight
-        if (leader && lag_issued > 0)
-            mbar_wait(&bar[B_LAG + b], (lag_issued - 1) & 1, abort_flag, p.err, 35, kWaitNs);
     }
     __syncwarp();
     tc_fence_before();
@@ -700,17 +763,17 @@ void build_images(const Dims &d, const float *hb, std::vector<uint8_t> &img, std
                             tmp.data(), tmp.size());
             }
         }
-        // head pieces (nh, kh): rows = u channels nh*HP.., k = skip channel of branch kh
+        // head pieces pc = (nh, kq): rows = u channels nh*HP + n; K = h channels kq*HQ .. of [h_H ; h_L]
         const float *w1 = src + off_wh1(d);
-        for (int nh = 0; nh < Sh::NH; ++nh)
-            for (int kh = 0; kh < 2; ++kh) {
-                tmp.assign(Sh::HEAD_BYTES, 0);
-                for (int n = 0; n < Sh::HP; ++n)
-                    for (int k = 0; k < S; ++k)
-                        put16(tmp, chunk_off(Sh::HP, n, k), to_f16(w1[(int64_t)(nh * Sh::HP + n) * 2 * S + kh * S + k]));
-                std::memcpy(im0 + (uint64_t)L * Sh::LAYER_IMG + (uint64_t)(nh * 2 + kh) * Sh::HEAD_BYTES, tmp.data(),
-                            tmp.size());
-            }
+        for (int pc = 0; pc < Sh::NHP; ++pc) {
+            const int nh = pc >> 2, kq = pc & 3;
+            tmp.assign(Sh::HEADP_BYTES, 0);
+            for (int n = 0; n < Sh::HP; ++n)
+                for (int k = 0; k < Sh::HQ; ++k)
+                    put16(tmp, chunk_off(Sh::HP, n, k),
+                          to_f16(w1[(int64_t)(nh * Sh::HP + n) * 2 * S + kq * Sh::HQ + k]));
+            std::memcpy(im0 + (uint64_t)L * Sh::LAYER_IMG + (uint64_t)pc * Sh::HEADP_BYTES, tmp.data(), tmp.size());
+        }
         // parameter block
         uint8_t *pm = pbl.data() + pb_stride * mi;
         for (int b = 0; b < 2; ++b) {
