@@ -114,9 +114,9 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel: str, src_file: str):
+def traffic_for(kernel: str, src_files):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when
-    the kernel source changed since the counters were taken."""
+    the kernel sources changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -125,7 +125,10 @@ def traffic_for(kernel: str, src_file: str):
     e = d.get(kernel)
     if not e:
         return None
-    sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in src_files:
+        h.update(open(f, "rb").read())
+    sha = h.hexdigest()[:16]
     if e.get("src_sha") != sha:
         return None
     return e.get("bytes_per_launch")
@@ -330,15 +333,15 @@ def main():
             flops_step = cfg["n_models"] * nw * WINDOW * 2 * workload.n_layers(cfg) * per_layer
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
             peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            bound, unit, src = "alu", "TFLOP/s", "fp32_path.cu"
+            bound, unit, src = "alu", "TFLOP/s", ["fp32_path.cu"]
         else:
             flops_step = cfg["n_models"] * nw * WINDOW * fps
             peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == 2 else 1.0)
-            bound, unit, src = "tensor", "TFLOP/s", "branch_tc.cu"
+            bound, unit, src = "tensor", "TFLOP/s", ["branch_tc.cu", "tc_ptx.cuh"]
         flops_launch = flops_step * args.steps / kn
         achieved = flops_launch / (kms / kn / 1000.0) / 1e12
-        src_path = os.path.join(ROOT, "paper_2201_11133_gb300", "csrc", src)
-        traffic = traffic_for(kname, src_path) if os.path.exists(src_path) else None
+        src_paths = [os.path.join(ROOT, "paper_2201_11133_gb300", "csrc", f) for f in src]
+        traffic = traffic_for(kname, src_paths) if all(os.path.exists(f) for f in src_paths) else None
         roof = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "peak_source": f"of {peak_kind}",
                 "traffic": traffic, "launches": kn, "kernel_ms_per_step": kms / args.steps,

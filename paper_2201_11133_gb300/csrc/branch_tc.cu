@@ -76,8 +76,6 @@ struct TcShape {
     static constexpr uint32_t STAGE_ROWS = 256;
     static constexpr uint32_t STAGE_LBO = STAGE_ROWS * 16;
     static constexpr uint32_t STAGE_BYTES = STAGE_LBO * RC;
-    static constexpr uint32_t Z_LBO = kTile * 16;
-    static constexpr uint32_t Z_BYTES = Z_LBO * RC;
     static constexpr uint32_t CONV_BYTES = N1 * 2 * R * 2;
     static constexpr uint32_t RES_BYTES = R * R * 2;
     static constexpr uint32_t SKIP_BYTES = S * R * 2;
@@ -91,8 +89,7 @@ struct TcShape {
     static constexpr uint32_t TMEM_BSTRIDE = TMEM_COLS / 2;
     // shared memory map
     static constexpr uint32_t OFF_STAGE = 0;
-    static constexpr uint32_t OFF_Z = 2 * STAGE_BYTES;
-    static constexpr uint32_t OFF_ENT = OFF_Z + 2 * Z_BYTES;           // [branch]{conv entry, rs entry}
+    static constexpr uint32_t OFF_ENT = 2 * STAGE_BYTES;               // [branch]{conv entry, rs entry}
     static constexpr uint32_t ENT_BR = ECONV + ERS;
     static constexpr uint32_t OFF_BIAS = OFF_ENT + 2 * ENT_BR;         // [branch]{b_conv[2 slots], b_res[2 slots]}
     static constexpr uint32_t BIAS_BR = 4 * BIAS_BYTES;
@@ -222,6 +219,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
     constexpr int RH = R / 2;          // channels per epilogue thread (half of a row)
     constexpr int SH = S / 2;
     constexpr int HPH = Sh::HP / 2;
+    // TMEM column of the gate output z for K step ks (16 channels): the epilogue half that owns
+    // channels [hf*RH, hf*RH + RH) packs them, two per column, at the start of its f columns
+    auto zcol = [](int ks) -> uint32_t { return (uint32_t)((ks / (RH / 16)) * RH + 8 * (ks % (RH / 16))); };
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Sh::OFF_BAR);
@@ -230,7 +230,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
     float *part = reinterpret_cast<float *>(smem + Sh::OFF_PART);
     const uint32_t s_base = smem_u32(smem);
     const uint32_t s_stage = s_base + Sh::OFF_STAGE;
-    const uint32_t s_z = s_base + Sh::OFF_Z;
     const uint32_t s_ent = s_base + Sh::OFF_ENT;
     const uint32_t s_bias = s_base + Sh::OFF_BIAS;
 
@@ -372,9 +371,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 uint32_t it[2] = {0, 0}, ph_x = 0, ph_lag = 0, ph_z = 0, ph_h = 0, ph_go = 0;
                 bool ok = true;
                 const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
-                const uint32_t zb = s_z + b * Sh::Z_BYTES;
                 const uint32_t dcol = tmem + b * Sh::TMEM_BSTRIDE;
                 const uint32_t e_conv = s_ent + b * Sh::ENT_BR, e_rs = e_conv + Sh::ECONV;
+                // descriptors of K step 0; a K step of 16 advances two chunk columns (descriptor
+                // addresses count 16-byte units, and these sums never carry out of the address field)
+                const uint64_t a_lag0 = sdesc(st, Sh::STAGE_LBO, 128);
+                const uint64_t a_cur0 = sdesc(st + kTile * 16, Sh::STAGE_LBO, 128);
+                const uint64_t b_conv0 = sdesc(e_conv, Sh::N1 * 16, 128);
+                const uint64_t b_res0 = sdesc(e_rs, R * 16, 128);
+                const uint64_t b_skip0 = sdesc(e_rs + Sh::RES_BYTES, S * 16, 128);
+                constexpr uint64_t A_STEP = 2 * Sh::STAGE_LBO / 16;
                 for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
                     for (int tt = 0; tt < NT && ok; ++tt) {
                         // Ping-pong: branch 1 starts a tile once branch 0's first gate is done, so
@@ -393,16 +399,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             ++ph_x;
                             ++ph_lag;
                             tc_fence_after();
+                            // K = 2R in steps of 16: the lagged rows (staging rows 128 - n ..), then the current ones
+                            const uint64_t a_lag = a_lag0 + (uint64_t)(kTile - n);
+                            mma_f16(dcol, a_lag, b_conv0, ID_CONV, 0u);
 #pragma unroll
-                            for (int ks = 0; ks < Sh::RC; ++ks) {   // K = 2R in steps of 16
-                                uint64_t ad;
-                                if (ks < Sh::RC / 2)
-                                    ad = sdesc(st + 2 * ks * Sh::STAGE_LBO + (kTile - n) * 16, Sh::STAGE_LBO, 128);
-                                else
-                                    ad = sdesc(st + (2 * ks - Sh::RC) * Sh::STAGE_LBO + kTile * 16, Sh::STAGE_LBO, 128);
-                                const uint64_t bd = sdesc(e_conv + 2 * ks * (Sh::N1 * 16), Sh::N1 * 16, 128);
-                                mma_f16(dcol, ad, bd, ID_CONV, ks > 0 ? 1u : 0u);
-                            }
+                            for (int ks = 1; ks < Sh::RC / 2; ++ks)
+                                mma_f16(dcol, a_lag + ks * A_STEP, b_conv0 + ks * (2 * Sh::N1), ID_CONV, 1u);
+#pragma unroll
+                            for (int ks = Sh::RC / 2; ks < Sh::RC; ++ks)
+                                mma_f16(dcol, a_cur0 + (ks - Sh::RC / 2) * A_STEP, b_conv0 + ks * (2 * Sh::N1), ID_CONV, 1u);
                             mma_commit(&bar[B_CONV + b]);
                             mma_commit(&bar[B_WEMPTY + 2 * b]);
                             ++it[0];
@@ -412,18 +417,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             ++ph_z;
                             if (b == 0 && l == 0) mbar_arrive(&bar[B_GO]);
                             tc_fence_after();
+                            // z (FP16, two per column) sits in the f columns: channels [16ks, 16ks+16)
+                            // at column zcol(ks); r goes to the g columns, s accumulates after them
 #pragma unroll
-                            for (int ks = 0; ks < Sh::RC / 2; ++ks) {
-                                const uint64_t ad = sdesc(zb + 2 * ks * Sh::Z_LBO, Sh::Z_LBO, 128);
-                                const uint64_t bd = sdesc(e_rs + 2 * ks * (R * 16), R * 16, 128);
-                                mma_f16(dcol, ad, bd, ID_RES, ks > 0 ? 1u : 0u);
-                            }
+                            for (int ks = 0; ks < Sh::RC / 2; ++ks)
+                                mma_f16_ta(dcol + R, dcol + zcol(ks), b_res0 + ks * (2 * R), ID_RES, ks > 0 ? 1u : 0u);
+                            mma_f16_ta(dcol + 2 * R, dcol + zcol(0), b_skip0, ID_SKIP, l > 0 ? 1u : 0u);
 #pragma unroll
-                            for (int ks = 0; ks < Sh::RC / 2; ++ks) {
-                                const uint64_t ad = sdesc(zb + 2 * ks * Sh::Z_LBO, Sh::Z_LBO, 128);
-                                const uint64_t bd = sdesc(e_rs + Sh::RES_BYTES + 2 * ks * (S * 16), S * 16, 128);
-                                mma_f16(dcol + 2 * R, ad, bd, ID_SKIP, (l > 0 || ks > 0) ? 1u : 0u);
-                            }
+                            for (int ks = 1; ks < Sh::RC / 2; ++ks)
+                                mma_f16_ta(dcol + 2 * R, dcol + zcol(ks), b_skip0 + ks * (2 * S), ID_SKIP, 1u);
                             mma_commit(&bar[B_RS + b]);
                             mma_commit(&bar[B_WEMPTY + 2 * b + 1]);
                             ++it[1];
@@ -469,7 +471,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
         const uint32_t t_conv = tmem + t_lane + b * Sh::TMEM_BSTRIDE;
         const uint32_t t_skip = t_conv + 2 * R;
         const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
-        const uint32_t zb = s_z + b * Sh::Z_BYTES;
         const uint32_t sb = s_bias + b * Sh::BIAS_BR;
         const int c0 = hf * RH;                        // first channel of this thread
         uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * (2 * R);
@@ -498,12 +499,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             }
         };
         // z for 16 channels starting at ch from the f / g accumulator columns
-        auto gate16 = [&](const uint32_t (&fr)[16], const uint32_t (&gr)[16], int ch, uint32_t bslot) {
+        auto gate16 = [&](const uint32_t (&fr)[16], const uint32_t (&gr)[16], int ch, uint32_t bslot, uint32_t (&zz)[8]) {
             const uint4 bf0 = lds128(bslot + ch * 2), bf1 = lds128(bslot + ch * 2 + 16);
             const uint4 bg0 = lds128(bslot + (R + ch) * 2), bg1 = lds128(bslot + (R + ch) * 2 + 16);
             const uint32_t bfw[8] = {bf0.x, bf0.y, bf0.z, bf0.w, bf1.x, bf1.y, bf1.z, bf1.w};
             const uint32_t bgw[8] = {bg0.x, bg0.y, bg0.z, bg0.w, bg1.x, bg1.y, bg1.z, bg1.w};
-            uint32_t zz[8];
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
                 const uint32_t hfv = hadd2(pack_h2(__uint_as_float(fr[2 * jj]), __uint_as_float(fr[2 * jj + 1])), bfw[jj]);
@@ -511,8 +511,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 const uint32_t sg = hfma2(tanh_h2(hgv), half2_half, half2_half);
                 zz[jj] = hmul2(tanh_h2(hfv), sg);
             }
-            sts128(zb + (ch / 8) * Sh::Z_LBO + r * 16, make_uint4(zz[0], zz[1], zz[2], zz[3]));
-            sts128(zb + (ch / 8 + 1) * Sh::Z_LBO + r * 16, make_uint4(zz[4], zz[5], zz[6], zz[7]));
         };
 
         for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
@@ -558,9 +556,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
                         uint8_t *dst = ring_b + roff * (2 * R) + (uint64_t)((t0 + r) & (d - 1)) * 16;
 #pragma unroll
-                        for (int c = hf * (Sh::RC / 2); c < (hf + 1) * (Sh::RC / 2); ++c) {
-                            const uint4 v = lds128(st + c * Sh::STAGE_LBO + (kTile + r) * 16);
-                            *reinterpret_cast<uint4 *>(dst + (uint64_t)c * d * 16) = v;
+                        for (int c = 0; c < RH / 8; ++c) {
+                            uint4 v;
+                            v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
+                            v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
+                            v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
+                            v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+                            *reinterpret_cast<uint4 *>(dst + (uint64_t)(hf * (RH / 8) + c) * d * 16) = v;
                         }
                     }
                     // gate: z = tanh(f + b_f) * (0.5 tanh(g/2 + b_g/2) + 0.5), FP16x2
@@ -570,18 +572,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         tmem_ld16(t_conv + c0, fa);
                         tmem_ld16(t_conv + R + c0, ga);
                         tmem_ld_wait();
+                        uint32_t z0[8];
                         if constexpr (RH == 32) {
-                            uint32_t fb[16], gbv[16];
+                            uint32_t fb[16], gbv[16], z1[8];
                             tmem_ld16(t_conv + c0 + 16, fb);
                             tmem_ld16(t_conv + R + c0 + 16, gbv);
-                            gate16(fa, ga, c0, bslot);
+                            gate16(fa, ga, c0, bslot, z0);
                             tmem_ld_wait();
-                            gate16(fb, gbv, c0 + 16, bslot);
+                            gate16(fb, gbv, c0 + 16, bslot, z1);
+                            tmem_st8(t_conv + c0 + 8, z1);
                         } else {
-                            gate16(fa, ga, c0, bslot);
+                            gate16(fa, ga, c0, bslot, z0);
                         }
+                        tmem_st8(t_conv + c0, z0);
+                        tmem_st_wait();
                     }
-                    fence_proxy_async_smem();
                     tc_fence_before();
                     warp_arrive(B_ZREADY + b);
                     if (!warp_wait(B_RS + b, ph_rs & 1, 31) ||
@@ -593,9 +598,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         const uint32_t bres = sb + (2 + (g & 1)) * Sh::BIAS_BYTES + c0 * 4;
                         uint32_t rr[RH];
                         if constexpr (RH == 32) {
-                            tmem_ld32(t_conv + c0, rr);
+                            tmem_ld32(t_conv + R + c0, rr);
                         } else {
-                            tmem_ld16(t_conv + c0, rr);
+                            tmem_ld16(t_conv + R + c0, rr);
                         }
                         tmem_ld_wait();
 #pragma unroll
