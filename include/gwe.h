@@ -175,6 +175,40 @@ gwe_status gwe_backward(gwe_model *model, int model_index, const float *x_H, con
  */
 gwe_status gwe_sync(gwe_model *model, void *stream);
 
+/*
+ * Allocation-free ensemble forward (the paper has no counterpart: this is an
+ * interface for callers, not a step of the method).  It computes exactly what
+ * gwe_forward computes for zero lag on the tensor-core path, but it never
+ * allocates device memory: its scratch (the per-CTA history of lagged rows,
+ * a block of zero rows and an error word) sits in one fixed 24 MiB array
+ * compiled into the library, instead of buffers the handle grows on demand.
+ * It serves callers that must not call cudaMalloc while they stream: for
+ * example a low-latency trigger pipeline sharing the GPU with other work, for
+ * which cudaMalloc's implicit device-wide synchronisation would stall the
+ * other work, or a process whose device memory is fully reserved up front by
+ * a framework's pool.  The handle itself is still created (and allocated)
+ * once, beforehand, with gwe_model_create.
+ *   model       handle created with precision GWE_BF16.
+ *   strain_H/L  device, FP32, n_samples each; out_prob device, FP32
+ *               [n_models][n_windows][window] (caller-owned, as for gwe_forward).
+ *   status      device pointer to one int owned by the caller, or NULL.  It is
+ *               set to 0 on the stream, then to a nonzero wait-site code if a
+ *               bounded device-side wait of the kernel gave up (the outputs are
+ *               then invalid).  With NULL the code is written into the array.
+ * Limits: window must be a multiple of 128; the number of CTAs is reduced so
+ * that their lag rings fit the array (the 30-layer, R = 64 configuration
+ * needs 768 KiB per CTA, so at most 32 CTAs run and the call is slower than
+ * gwe_forward); a configuration whose single-CTA ring exceeds the array is
+ * rejected with GWE_ERR_ARG.
+ * The first call on each device looks up the array's device address for that
+ * device (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * clears its error word and zero rows on the stream; calls whose executions
+ * overlap on the GPU (for example on two streams) race on it, so serialise them.
+ */
+gwe_status gwe_forward_static(gwe_model *model, const float *strain_H, const float *strain_L, int64_t n_samples,
+                              int window, int stride, float *out_prob, int *status, void *stream);
+
 /* Flags of gwe_triggers. */
 #define GWE_TRIG_PER_MODEL 1   /* also return every model's kept peaks (model >= 0) */
 

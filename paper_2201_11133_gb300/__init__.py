@@ -21,7 +21,7 @@ __all__ = [
     "GWE_FP32", "GWE_BF16", "GWE_FP8", "GweError", "load", "build",
     "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_destroy",
     "gwe_forward", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
-    "gwe_version", "gwe_sync", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
+    "gwe_version", "gwe_sync", "gwe_forward_static", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
 
 GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
@@ -83,6 +83,7 @@ def load():
             "gwe_triggers": (I, [P, I, I, I64, I, I, F, D, I64, I, P, I64, P, P]),
             "gwe_whiten": (I, [P, I64, D, I, I, P, P]),
             "gwe_sync": (I, [P, P]),
+            "gwe_forward_static": (I, [P, P, P, I64, I, I, P, P, P]),
             "gwe_profile_enable": (I, [I]),
             "gwe_profile_read": (I, [I, P, I, P, P]),
             "gwe_last_error": (ctypes.c_char_p, []),
@@ -206,6 +207,14 @@ def gwe_triggers(prob, n_models: int, n_slides: int, n_windows: int, window: int
                           ctypes.byref(n_out), _stream(stream))
     _check(st, "gwe_triggers")
     return out[:n_out.value].copy()
+
+
+def gwe_forward_static(model: int, strain_H, strain_L, n_samples: int, window: int, stride: int, out_prob,
+                       status=None, stream=None) -> None:
+    """Zero-lag forward that allocates no device memory (scratch in a fixed array of the library)."""
+    _check(load().gwe_forward_static(model, _dptr(strain_H), _dptr(strain_L), int(n_samples), int(window),
+                                     int(stride), _dptr(out_prob), _dptr(status), _stream(stream)),
+           "gwe_forward_static")
 
 
 def gwe_sync(model: int, stream=None) -> None:

@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -953,3 +954,129 @@ gwe_status bf16_check(gwe_model *m, cudaStream_t st) {
 }
 
 }  // namespace gwe
+
+// ============================================================================ allocation-free forward
+// A variant of the tensor-core forward for callers that must not allocate device memory while
+// they stream: its lag-history ring, zero rows and error word live in one fixed file-scope device
+// array instead of buffers the handle grows on demand.  The array is part of the library image,
+// so every GPU that loads the library holds it until the process exits.
+namespace gwe {
+namespace {
+
+constexpr size_t kStaticScratchBytes = 24u << 20;     // 24 MiB
+constexpr size_t kStaticErrOff = 0;                   // one int (wait site of a timeout)
+constexpr size_t kStaticZeroOff = 256;                // 4 KiB of zero rows
+constexpr size_t kStaticRingOff = 256 + 4096;         // per-CTA lag rings
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+uint8_t *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the array for the current device, looked up once per device (the
+// array's name in host code is only a stand-in for it).
+gwe_status static_scratch(uint8_t **out) {
+    int dev = 0;
+    GWE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("gwe_forward_static: device ordinal out of range");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error(std::string("gwe_forward_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+            return GWE_ERR_CUDA;
+        }
+        g_static_ptr[dev] = reinterpret_cast<uint8_t *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return GWE_OK;
+}
+
+template <int R, int S, int HC>
+gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const float *sH, const float *sL, int64_t nw,
+                            int W, int stride, float *out, int *status, cudaStream_t st) {
+    using Sh = TcShape<R, S, HC>;
+    const Dims &d = m->dims;
+    const int64_t n_jobs = (int64_t)d.n_models * nw;
+    uint64_t ring_rows = 0;
+    for (int l = 0; l < d.L; ++l) ring_rows += (uint64_t)1 << (l % d.lps);
+    const uint64_t ring_cta = (2 * ring_rows * 2 * R + 255) & ~uint64_t(255);
+    const uint64_t cap = kStaticScratchBytes - kStaticRingOff;
+    if (ring_cta > cap) {
+        set_error("gwe_forward_static: one CTA's lag ring (" + std::to_string(ring_cta) +
+                  " bytes) exceeds the fixed scratch (" + std::to_string(cap) + " bytes)");
+        return GWE_ERR_ARG;
+    }
+    const int grid = (int)std::min<int64_t>(std::min<int64_t>(s.sms, n_jobs), (int64_t)(cap / ring_cta));
+    int *err = status ? status : reinterpret_cast<int *>(scratch + kStaticErrOff);
+    // the error word and the zero rows must start at zero; the ring needs no clearing (rows before
+    // a window's start are read from the zero rows)
+    GWE_CUDA_TRY(cudaMemsetAsync(scratch, 0, kStaticRingOff, st));
+    if (status) GWE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+    TcParams p;
+    p.wimg = s.img.as<uint8_t>();
+    p.wimg_stride = s.img_stride;
+    p.pblob = s.pblob.as<uint8_t>();
+    p.pblob_stride = s.pblob_stride;
+    p.sH = sH;
+    p.sL = sL;
+    p.nw = nw;
+    p.W = W;
+    p.stride = stride;
+    p.slides = nullptr;
+    p.n_slides = 0;
+    p.n_models = d.n_models;
+    p.out = out;
+    p.logits = 0;
+    p.ring = scratch + kStaticRingOff;
+    p.ring_cta_bytes = ring_cta;
+    p.zeros = scratch + kStaticZeroOff;
+    p.L = d.L;
+    p.lps = d.lps;
+    p.ring_rows = ring_rows;
+    p.err = err;
+    k_branch_tc<R, S, HC><<<grid, kThreads, Sh::SMEM, st>>>(p);
+    note_launch();
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
+}  // namespace
+}  // namespace gwe
+
+using namespace gwe;
+
+extern "C" gwe_status gwe_forward_static(gwe_model *m, const float *strain_H, const float *strain_L, int64_t n,
+                                         int window, int stride, float *out_prob, int *status, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    GWE_ARG_CHECK(strain_H != nullptr && strain_L != nullptr && out_prob != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(window > 0 && stride > 0 && stride <= window, "bad window/stride");
+    GWE_ARG_CHECK(n >= window, "n_samples < window");
+    if (m->precision != GWE_BF16) {
+        set_error("gwe_forward_static: the handle must use the tensor-core precision (GWE_BF16)");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+    if (!s || s->variant < 0) {
+        set_error("gwe_forward_static: tensor-core path not prepared");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    if (window % kTile != 0) {
+        set_error("gwe_forward_static: window must be a multiple of 128");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    const int64_t nw = (n - window) / stride + 1;
+    uint8_t *scratch = nullptr;
+    gwe_status st = static_scratch(&scratch);
+    if (st != GWE_OK) return st;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (s->variant == 0)
+        return launch_tc_static<32, 32, 32>(m, *s, scratch, strain_H, strain_L, nw, window, stride, out_prob, status, cs);
+    return launch_tc_static<64, 128, 256>(m, *s, scratch, strain_H, strain_L, nw, window, stride, out_prob, status, cs);
+}
