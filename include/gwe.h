@@ -159,9 +159,14 @@ gwe_status gwe_forward_logits(gwe_model *model, const float *x_H, const float *x
  *   grad_weights device FP32 [gwe_param_count], overwritten with dLoss/dweights
  *                (summed over the batch), blob layout.
  *   grad_H, grad_L device FP32 [batch][window] dLoss/dstrain, or NULL.
- * Activations are recomputed from the inputs, stack by stack.  Uses the FP32
- * weights unless the handle's precision is GWE_BF16 (BF16 operands, FP32
- * accumulation and FP32 master gradients).
+ * The forward keeps only each stack's input and the final skip sums; the
+ * backward recomputes one stack at a time from its input (per-stack
+ * recomputation) and walks it backwards.  FP32 arithmetic on the FP32 weights
+ * (for every handle precision); weight gradients are reduced with atomic
+ * additions, so their summation order is not fixed.  Windows are processed in
+ * chunks of 16; the workspace (about 0.3 GB per chunk for the 30-layer R = 64
+ * model) is owned by the handle.  GWE_ERR_UNSUPPORTED for channel counts the
+ * FP32 kernels do not cover.
  */
 gwe_status gwe_backward(gwe_model *model, int model_index, const float *x_H, const float *x_L, int batch,
                         int window, const float *dlogit, float *grad_weights, float *grad_H, float *grad_L,

@@ -21,7 +21,7 @@ __all__ = [
     "GWE_FP32", "GWE_BF16", "GWE_FP8", "GweError", "load", "build",
     "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_destroy",
     "gwe_forward", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
-    "gwe_version", "gwe_sync", "gwe_forward_static", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
+    "gwe_version", "gwe_sync", "gwe_forward_static", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
 
 GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
@@ -287,3 +287,48 @@ class Model:
             out = torch.empty((int(self.cfg["n_models"]), B, W), dtype=torch.float32, device=x_H.device)
         gwe_forward_logits(self.handle, x_H, x_L, B, W, out, stream)
         return out
+
+
+def _autograd_function():
+    import torch
+
+    class GweLogits(torch.autograd.Function):
+        """Logits of a one-member handle as a differentiable function of its FP32 weight blob
+        and of the two detector windows; the backward pass runs gwe_backward."""
+
+        @staticmethod
+        def forward(ctx, weights, x_H, x_L, model):
+            if int(model.cfg["n_models"]) != 1:
+                raise ValueError("GweLogits needs a one-member handle")
+            gwe_model_set_weights(model.handle, weights.detach().float().cpu().numpy())
+            out = model.logits(x_H.contiguous(), x_L.contiguous())[0]
+            ctx.save_for_backward(x_H, x_L)
+            ctx.model = model
+            ctx.wdevice = weights.device
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            x_H, x_L = ctx.saved_tensors
+            model = ctx.model
+            B, W = int(x_H.shape[0]), int(x_H.shape[1])
+            dev = x_H.device
+            gw = torch.empty(gwe_param_count(model.cfg), dtype=torch.float32, device=dev)
+            gH = torch.empty((B, W), dtype=torch.float32, device=dev) if ctx.needs_input_grad[1] else None
+            gL = torch.empty((B, W), dtype=torch.float32, device=dev) if ctx.needs_input_grad[2] else None
+            gwe_backward(model.handle, 0, x_H.contiguous(), x_L.contiguous(), B, W,
+                         grad_out.contiguous().float(), gw, gH, gL)
+            return gw.to(ctx.wdevice), gH, gL, None
+
+    return GweLogits
+
+
+_GWE_LOGITS = None
+
+
+def gwe_logits_autograd(model, weights, x_H, x_L):
+    """Differentiable logits [batch, window] of a one-member handle (weights: FP32 blob [P])."""
+    global _GWE_LOGITS
+    if _GWE_LOGITS is None:
+        _GWE_LOGITS = _autograd_function()
+    return _GWE_LOGITS.apply(weights, x_H, x_L, model)

@@ -149,6 +149,7 @@ gwe_status gwe_model_set_weights(gwe_model *m, const float *hb) {
 void gwe_model_destroy(gwe_model *m) {
     if (!m) return;
     bf16_release(m);
+    fp32_backward_release(m);
     m->w32.release();
     m->f32.buf.release();
     m->ws.x0.release();
@@ -193,11 +194,12 @@ gwe_status gwe_forward_logits(gwe_model *m, const float *xH, const float *xL, in
 gwe_status gwe_backward(gwe_model *m, int model_index, const float *xH, const float *xL, int batch, int window,
                         const float *dlogit, float *grad_w, float *grad_H, float *grad_L, void *stream) {
     clear_error();
-    (void)model_index; (void)xH; (void)xL; (void)batch; (void)window; (void)dlogit; (void)grad_w;
-    (void)grad_H; (void)grad_L; (void)stream;
     GWE_ARG_CHECK(m != nullptr, "model is NULL");
-    set_error("gwe_backward: not built yet");
-    return GWE_ERR_UNSUPPORTED;
+    GWE_ARG_CHECK(model_index >= 0 && model_index < m->dims.n_models, "model_index out of range");
+    GWE_ARG_CHECK(xH != nullptr && xL != nullptr && dlogit != nullptr && grad_w != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(batch > 0 && window > 0, "batch and window must be positive");
+    GWE_ARG_CHECK((int64_t)batch * window < ((int64_t)1 << 31), "batch * window too large");
+    return fp32_backward(m, model_index, xH, xL, batch, window, dlogit, grad_w, grad_H, grad_L, as_stream(stream));
 }
 
 gwe_status gwe_triggers(const float *prob, int n_models, int n_slides, int64_t n_windows, int window, int stride,

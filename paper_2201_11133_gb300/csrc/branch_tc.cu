@@ -55,7 +55,6 @@ using namespace tc;
 
 constexpr int kThreads = 640;
 constexpr int kTile = 128;
-constexpr int kNEnt = 4;
 constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s per wait
 
 constexpr uint32_t pow2ceil(uint32_t x) {
@@ -69,7 +68,6 @@ template <int R, int S, int HC>
 struct TcShape {
     static constexpr int N1 = 2 * R;              // conv outputs: f then g
     static constexpr int RC = R / 8;              // 16-byte chunks of an R-wide row
-    static constexpr int SC = S / 8;
     static constexpr int NH = HC <= 128 ? 1 : 2;  // head output pieces
     static constexpr int HP = HC / NH;
     static constexpr int HQ = S / 2;              // K width of one head weight piece

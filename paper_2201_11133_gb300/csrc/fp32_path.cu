@@ -22,6 +22,7 @@ namespace gwe {
 namespace {
 
 constexpr int kTM = 64;        // time rows per block
+constexpr int LF_FROM_STRAIN = 1, LF_SKIP_INIT = 2, LF_NO_SKIP = 4;
 constexpr int kThreads = 256;  // 16 x 16 thread grid: 4 rows x (N/16) columns per thread
 
 template <int R, int S>
@@ -40,7 +41,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_fp32_layer(const float *__restrict__ xin, float *__restrict__ xout, float *__restrict__ skip,
              const float *__restrict__ wl_base, int64_t branch_stride, const float *__restrict__ win,
              const float *__restrict__ sH, const float *__restrict__ sL, int64_t w0, int stride, int W,
-             int C, int d, int first) {
+             int C, int d, int flags, float *__restrict__ a_out) {
+    // flags: LF_FROM_STRAIN x_l is the input projection of the strain (else read xin);
+    //        LF_SKIP_INIT skip = q (else skip += q); LF_NO_SKIP skip is not written.
+    // a_out (optional): the pre-activations a = conv + b_conv, [rows][2R].
+    const int first = flags & LF_FROM_STRAIN;
     using Sh = LayerShape<R, S>;
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
@@ -114,6 +119,15 @@ k_fp32_layer(const float *__restrict__ xin, float *__restrict__ xout, float *__r
             for (int i = 0; i < 4; ++i) acc[i][j] = fmaf(a[i], wv, acc[i][j]);
         }
     }
+    if (a_out) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int t = t0 + ty + 16 * i;
+            if (t >= W) continue;
+#pragma unroll
+            for (int j = 0; j < Sh::J1; ++j) a_out[(xrow0 + t) * (2 * R) + tx + 16 * j] = acc[i][j];
+        }
+    }
     // gate: column ch (< R) is the tanh input, column ch + R its sigmoid gate
 #pragma unroll
     for (int j = 0; j < Sh::J1 / 2; ++j) {
@@ -156,9 +170,9 @@ k_fp32_layer(const float *__restrict__ xin, float *__restrict__ xout, float *__r
             const int col = tx + 16 * j;
             if (col < R) {
                 xout[(xrow0 + t) * R + col] = xc[r * Sh::LD + col] + acc2[i][j];
-            } else {
+            } else if (!(flags & LF_NO_SKIP)) {
                 float *sp = skip + (xrow0 + t) * S + (col - R);
-                *sp = first ? acc2[i][j] : (*sp + acc2[i][j]);
+                *sp = (flags & LF_SKIP_INIT) ? acc2[i][j] : (*sp + acc2[i][j]);
             }
         }
     }
@@ -254,13 +268,13 @@ __global__ void k_fp32_combine(const float *__restrict__ PH, const float *__rest
 
 template <int R, int S>
 void launch_layer(const float *xin, float *xout, float *skip, const float *wl, int64_t bstride, const float *win,
-                  const float *sH, const float *sL, int64_t w0, int stride, int W, int C, int d, int first,
-                  cudaStream_t st) {
+                  const float *sH, const float *sL, int64_t w0, int stride, int W, int C, int d, int flags,
+                  cudaStream_t st, float *a_out = nullptr) {
     using Sh = LayerShape<R, S>;
     dim3 grid((W + kTM - 1) / kTM, 2 * C);
     ProfScope prof("k_fp32_layer", st);
     k_fp32_layer<R, S><<<grid, kThreads, Sh::SMEM, st>>>(xin, xout, skip, wl, bstride, win, sH, sL, w0, stride, W,
-                                                         C, d, first);
+                                                         C, d, flags, a_out);
     note_launch();
 }
 
@@ -398,12 +412,13 @@ gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
                 const int dl = 1 << (l % d.lps);
                 const float *wl = layers + (int64_t)l * f.layer_stride;
                 const int64_t bstride = (int64_t)L * f.layer_stride;
+                const int flags = l == 0 ? (LF_FROM_STRAIN | LF_SKIP_INIT) : 0;
                 if (v == kSmall)
                     launch_layer<32, 32>(xin, xout, m->ws.skip.as<float>(), wl, bstride, wm, sH, sL, w0, stride, W, C,
-                                         dl, l == 0, st);
+                                         dl, flags, st);
                 else
                     launch_layer<64, 128>(xin, xout, m->ws.skip.as<float>(), wl, bstride, wm, sH, sL, w0, stride, W,
-                                          C, dl, l == 0, st);
+                                          C, dl, flags, st);
                 std::swap(xin, xout);
             }
             float *proj = m->ws.proj.as<float>();
@@ -425,6 +440,477 @@ gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
             }
             GWE_CUDA_TRY(cudaGetLastError());
         }
+    }
+    return GWE_OK;
+}
+
+// ============================================================================ backward (FP32)
+// Reverse-mode pass of one model over a batch of explicit windows (paper paragraph "AI ensemble
+// construction": per-time-step labels, binary cross-entropy on the logits), in FP32 with
+// per-stack recomputation: the forward keeps only each stack's input and the final skip sums;
+// the backward re-runs one stack at a time (saving x_l and a_l of its layers) and walks it
+// backwards.  Per layer (dilation d), rows t of one window, with dskip the gradient of the skip
+// sum (the same for every layer of the branch):
+//   dz    = W_res^T dx_{l+1} + W_skip^T dskip
+//   da_f  = dz s (1 - tanh(f)^2),  da_g = dz tanh(f) s (1 - s),  s = sigmoid(g)
+//   dx_l  = dx_{l+1} + W1^T da(t) + W0^T da(t + d)      (zero beyond the window end)
+//   dW0  += da(t) x_l(t - d)^T, dW1 += da(t) x_l(t)^T, dW_res += dx_{l+1} z^T, dW_skip += dskip z^T
+// and the biases take the column sums.  Weight gradients are reduced over rows in blocks that
+// each own a slice of rows, then added atomically (summation order is not fixed).
+namespace {
+
+constexpr int BT = 64;   // rows and columns per block tile
+constexpr int BK = 32;   // K slice staged in shared memory
+
+struct BSrc {
+    const float *A;      // A[row][k] of branch 0; branch b adds b * a_boff
+    int lda;
+    int shift;           // use row t + shift of the same window (zero outside [0, W))
+    int relu;            // apply ReLU to A on load
+    const float *Wt;     // Wt[k][n] of branch 0; branch b adds b * w_boff
+    int ldw;
+    int K;
+};
+
+struct BRows {
+    BSrc s[2];
+    int nsrc;
+    int N;               // output columns
+    int W, C;            // window length; windows per branch (grid.y = nbranch * C)
+    int64_t a_boff, w_boff, y_boff;   // per-branch offsets (elements)
+    float *Y;            // output [row][ldy] of branch 0
+    int ldy;
+    // epilogue operands
+    const float *aux0;   // EP_DZ: a [row][2R]; EP_ADD: residual [row][N]; EP_HEAD_U: b1; EP_HEAD_DH: skip (both branches)
+    const float *aux1;   // EP_HEAD_U: w2
+    const float *aux2;   // EP_HEAD_U: dlogit [row]
+    float *out1;         // EP_DZ: z [row][R]; EP_HEAD_U: ReLU(u) [row][N]; EP_HEAD_DH: dskip (both branches)
+    int64_t aux_boff;    // per-branch offset of aux0 / out1 rows (EP_DZ) or branch block size (EP_HEAD_DH)
+};
+
+enum { EP_DZ = 0, EP_ADD = 1, EP_HEAD_U = 2, EP_HEAD_DH = 3 };
+
+__device__ __forceinline__ float sigm_f(float x) { return 1.f / (1.f + expf(-x)); }
+
+template <int EP>
+__global__ void __launch_bounds__(256) k_bwd_rows(const BRows p) {
+    __shared__ float As[BK][BT + 1];
+    __shared__ float Ws[BK][BT];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int bw = blockIdx.y, b = bw / p.C;
+    const int t0 = blockIdx.x * BT, n0 = blockIdx.z * BT;
+    const int64_t row0 = (int64_t)(bw - b * p.C) * p.W;   // first row of this window within its branch
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int si = 0; si < p.nsrc; ++si) {
+        const BSrc &sc = p.s[si];
+        const float *A = sc.A + b * p.a_boff;
+        const float *Wt = sc.Wt + b * p.w_boff;
+        for (int k0 = 0; k0 < sc.K; k0 += BK) {
+            for (int i = tid; i < BT * BK; i += 256) {
+                const int r = i / BK, k = i - r * BK, t = t0 + r + sc.shift;
+                float v = 0.f;
+                if (t >= 0 && t < p.W && k0 + k < sc.K) v = A[(row0 + t) * sc.lda + k0 + k];
+                if (sc.relu) v = fmaxf(v, 0.f);
+                As[k][r] = v;
+            }
+            for (int i = tid; i < BK * BT; i += 256) {
+                const int k = i / BT, n = i - k * BT;
+                Ws[k][n] = (k0 + k < sc.K && n0 + n < p.N) ? Wt[(int64_t)(k0 + k) * sc.ldw + n0 + n] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int k = 0; k < BK; ++k) {
+                float a[4], w[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w[j] = Ws[k][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int t = t0 + ty + 16 * i;
+        if (t >= p.W) continue;
+        const int64_t row = row0 + t;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n >= p.N) continue;
+            const float v = acc[i][j];
+            if (EP == EP_DZ) {
+                // n is a residual channel c (N = R); a holds [f | g] per row
+                const int R = p.N;
+                const float *a = p.aux0 + b * p.aux_boff * 2 + row * 2 * R;
+                const float f = a[n], g = a[R + n];
+                const float th = tanhf(f), sg = sigm_f(g);
+                float *da = p.Y + b * p.y_boff + row * p.ldy;
+                da[n] = v * sg * (1.f - th * th);
+                da[R + n] = v * th * sg * (1.f - sg);
+                p.out1[b * p.aux_boff + row * R + n] = th * sg;
+            } else if (EP == EP_ADD) {
+                p.Y[b * p.y_boff + row * p.ldy + n] = v + p.aux0[b * p.y_boff + row * p.ldy + n];
+            } else if (EP == EP_HEAD_U) {
+                const float u = v + p.aux0[n];
+                const float dl = p.aux2[row];
+                p.Y[row * p.ldy + n] = (u > 0.f) ? dl * p.aux1[n] : 0.f;
+                p.out1[row * p.ldy + n] = fmaxf(u, 0.f);
+            } else {   // EP_HEAD_DH: n < 2S -> branch n / S, skip channel n % S
+                const int S = p.N / 2;
+                const int bb = n / S, ch = n - bb * S;
+                const int64_t idx = bb * p.aux_boff + row * S + ch;
+                p.out1[idx] = (p.aux0[idx] > 0.f) ? v : 0.f;
+            }
+        }
+    }
+}
+
+// dW[n][k] += sum_r G(r)[n] X(r)[k] (X optional) and db[n] += sum_r G(r)[n] (db optional), over
+// the rows of each branch; X(r) is row t + shift of the same window (zero outside [0, W)).
+struct BWg {
+    const float *G; int ldg; int N; int64_t g_boff;
+    const float *X; int ldx; int K; int shift; int xrelu; int64_t x_boff;
+    float *dW; int ldw; int64_t w_boff;
+    float *db; int64_t db_boff;
+    int W, C, splits;
+};
+
+__global__ void __launch_bounds__(256) k_wgrad(const BWg p) {
+    __shared__ float Gs[BK][BT];
+    __shared__ float Xs[BK][BT];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int b = blockIdx.z / p.splits, sp = blockIdx.z - b * p.splits;
+    const int k0 = blockIdx.x * BT, n0 = blockIdx.y * BT;
+    const int64_t rows = (int64_t)p.C * p.W;
+    const int64_t chunk = (rows + p.splits - 1) / p.splits;
+    const int64_t r_begin = sp * chunk, r_end = min(rows, r_begin + chunk);
+    const float *G = p.G + b * p.g_boff;
+    const float *X = p.X ? p.X + b * p.x_boff : nullptr;
+    const bool do_bias = p.db && blockIdx.x == 0;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    float bacc = 0.f;
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += BK) {
+        for (int i = tid; i < BK * BT; i += 256) {
+            const int r = i / BT, c = i - r * BT;
+            const int64_t row = r0 + r;
+            float gv = 0.f, xv = 0.f;
+            if (row < r_end) {
+                if (n0 + c < p.N) gv = G[row * p.ldg + n0 + c];
+                if (X && k0 + c < p.K) {
+                    const int64_t w = row / p.W;
+                    const int t = (int)(row - w * p.W) + p.shift;
+                    if (t >= 0 && t < p.W) xv = X[(w * p.W + t) * p.ldx + k0 + c];
+                    if (p.xrelu) xv = fmaxf(xv, 0.f);
+                }
+            }
+            Gs[r][c] = gv;
+            Xs[r][c] = xv;
+        }
+        __syncthreads();
+        if (X) {
+#pragma unroll 8
+            for (int r = 0; r < BK; ++r) {
+                float g[4], x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) g[i] = Gs[r][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) x[j] = Xs[r][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(g[i], x[j], acc[i][j]);
+            }
+        }
+        if (do_bias && tid < BT)
+            for (int r = 0; r < BK; ++r) bacc += Gs[r][tid];
+        __syncthreads();
+    }
+    if (X) {
+        float *dW = p.dW + b * p.w_boff;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int n = n0 + ty + 16 * i;
+            if (n >= p.N) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = k0 + tx + 16 * j;
+                if (k < p.K) atomicAdd(dW + (int64_t)n * p.ldw + k, acc[i][j]);
+            }
+        }
+    }
+    if (do_bias && tid < BT && n0 + tid < p.N) atomicAdd(p.db + b * p.db_boff + n0 + tid, bacc);
+}
+
+// x_0 = w_in s + b_in for both branches; rows of branch b follow branch b-1
+__global__ void k_input_proj(const float *__restrict__ sH, const float *__restrict__ sL,
+                             const float *__restrict__ blob, int64_t Pb, int R, int64_t rows, float *__restrict__ x0) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * rows * R) return;
+    const int64_t row = i / R;
+    const int c = (int)(i - row * R);
+    const int b = row >= rows;
+    const float s = b ? sL[row - rows] : sH[row];
+    const float *w = blob + b * Pb;
+    x0[i] = fmaf(w[c], s, w[R + c]);
+}
+
+// ds[t] = sum_c w_in[c] dx_0[t][c]
+__global__ void k_dstrain(const float *__restrict__ dx0, const float *__restrict__ w_in, int R, int64_t rows,
+                          float *__restrict__ ds) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    float acc = 0.f;
+    for (int c = lane; c < R; c += 32) acc = fmaf(w_in[c], dx0[row * R + c], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) ds[row] = acc;
+}
+
+template <int EP>
+void launch_rows(const BRows &p, int nbranch, cudaStream_t st) {
+    dim3 grid((p.W + BT - 1) / BT, nbranch * p.C, (p.N + BT - 1) / BT);
+    k_bwd_rows<EP><<<grid, 256, 0, st>>>(p);
+    note_launch();
+}
+
+void launch_wgrad(const BWg &p, int nbranch, cudaStream_t st) {
+    const int kt = p.X ? (p.K + BT - 1) / BT : 1;
+    dim3 grid(kt, (p.N + BT - 1) / BT, p.splits * nbranch);
+    ProfScope prof("k_wgrad", st);
+    k_wgrad<<<grid, 256, 0, st>>>(p);
+    note_launch();
+}
+
+BWg wg(const float *G, int ldg, int N, int64_t g_boff, const float *X, int ldx, int K, int shift, int64_t x_boff,
+       float *dW, int ldw, int64_t w_boff, float *db, int64_t db_boff, int W, int C) {
+    BWg p;
+    p.G = G; p.ldg = ldg; p.N = N; p.g_boff = g_boff;
+    p.X = X; p.ldx = ldx; p.K = K; p.shift = shift; p.xrelu = 0; p.x_boff = x_boff;
+    p.dW = dW; p.ldw = ldw; p.w_boff = w_boff;
+    p.db = db; p.db_boff = db_boff;
+    p.W = W; p.C = C;
+    const int64_t rows = (int64_t)C * W;
+    p.splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, rows / 2048));
+    return p;
+}
+
+BSrc src(const float *A, int lda, int shift, int relu, const float *Wt, int ldw, int K) {
+    BSrc s;
+    s.A = A; s.lda = lda; s.shift = shift; s.relu = relu; s.Wt = Wt; s.ldw = ldw; s.K = K;
+    return s;
+}
+
+}  // namespace
+
+namespace {
+
+struct BwdWs {
+    DevBuf xsave, xrec, arec, skip, dskip, dxa, dxb, da, z, ru, du, dummy;
+};
+
+}  // namespace
+
+void fp32_backward_release(gwe_model *m) {
+    BwdWs *w = reinterpret_cast<BwdWs *>(m->bwd);
+    if (!w) return;
+    DevBuf *all[] = {&w->xsave, &w->xrec, &w->arec, &w->skip, &w->dskip, &w->dxa, &w->dxb, &w->da, &w->z, &w->ru,
+                     &w->du, &w->dummy};
+    for (DevBuf *b : all) b->release();
+    delete w;
+    m->bwd = nullptr;
+}
+
+gwe_status fp32_backward(gwe_model *m, int mi, const float *xH, const float *xL, int batch, int W,
+                         const float *dlogit, float *gw, float *gH, float *gL, cudaStream_t st) {
+    const Dims &d = m->dims;
+    const Variant v = variant_of(d);
+    if (v == kNone) {
+        set_error("backward: unsupported configuration");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    const int R = d.R, S = d.S, Hc = d.Hc, L = d.L, lps = d.lps, stacks = d.stacks;
+    BwdWs *w = reinterpret_cast<BwdWs *>(m->bwd);
+    if (!w) {
+        w = new BwdWs();
+        m->bwd = w;
+    }
+    const int C = std::min(batch, 16);                       // windows per chunk
+    const size_t rows = (size_t)C * W, rows2 = 2 * rows;      // per branch, both branches
+    GWE_CUDA_TRY(w->xsave.ensure(sizeof(float) * stacks * rows2 * R));
+    GWE_CUDA_TRY(w->xrec.ensure(sizeof(float) * (lps + 1) * rows2 * R));
+    GWE_CUDA_TRY(w->arec.ensure(sizeof(float) * lps * rows2 * 2 * R));
+    GWE_CUDA_TRY(w->skip.ensure(sizeof(float) * rows2 * S));
+    GWE_CUDA_TRY(w->dskip.ensure(sizeof(float) * rows2 * S));
+    GWE_CUDA_TRY(w->dxa.ensure(sizeof(float) * rows2 * R));
+    GWE_CUDA_TRY(w->dxb.ensure(sizeof(float) * rows2 * R));
+    GWE_CUDA_TRY(w->da.ensure(sizeof(float) * rows2 * 2 * R));
+    GWE_CUDA_TRY(w->z.ensure(sizeof(float) * rows2 * R));
+    GWE_CUDA_TRY(w->ru.ensure(sizeof(float) * rows * Hc));
+    GWE_CUDA_TRY(w->du.ensure(sizeof(float) * rows * Hc));
+    GWE_CUDA_TRY(w->dummy.ensure(sizeof(float) * 64));
+    GWE_CUDA_TRY(cudaMemsetAsync(gw, 0, sizeof(float) * d.P, st));
+
+    const float *blob = m->w32.as<float>() + (int64_t)mi * d.P;          // FP32 weights, blob layout
+    const Fp32Weights &f = m->f32;
+    const float *wm = f.buf.as<float>() + (int64_t)mi * f.model_stride;   // FP32 kernel layout
+    const float *layers = wm + ((4 * R + 3) & ~3);
+    const float *head = wm + f.head_off;
+    const int64_t bstride = (int64_t)L * f.layer_stride;
+    float *xsave = w->xsave.as<float>(), *xrec = w->xrec.as<float>(), *arec = w->arec.as<float>();
+    float *skip = w->skip.as<float>(), *dskip = w->dskip.as<float>();
+    float *da = w->da.as<float>(), *z = w->z.as<float>(), *ru = w->ru.as<float>(), *du = w->du.as<float>();
+    const int64_t Pb = d.Pb;
+
+    for (int c0 = 0; c0 < batch; c0 += C) {
+        const int Cc = std::min(C, batch - c0);
+        const int64_t rb = (int64_t)Cc * W;      // rows per branch in this chunk
+        const float *sH = xH + (int64_t)c0 * W, *sL = xL + (int64_t)c0 * W;
+        // ---- forward, keeping each stack's input and the final skip sums
+        {
+            float *xa = xrec, *xb = xrec + rows2 * R;
+            const int64_t n = 2 * rb * R;
+            k_input_proj<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sH, sL, blob, Pb, R, rb, xa);
+            note_launch();
+            for (int l = 0; l < L; ++l) {
+                if (l % lps == 0)
+                    GWE_CUDA_TRY(cudaMemcpyAsync(xsave + (size_t)(l / lps) * rows2 * R, xa, sizeof(float) * 2 * rb * R,
+                                                 cudaMemcpyDeviceToDevice, st));
+                const float *wl = layers + (int64_t)l * f.layer_stride;
+                const int flags = (l == 0) ? LF_SKIP_INIT : 0;
+                if (v == kSmall)
+                    launch_layer<32, 32>(xa, xb, skip, wl, bstride, wm, sH, sL, 0, W, W, Cc, 1 << (l % lps), flags, st);
+                else
+                    launch_layer<64, 128>(xa, xb, skip, wl, bstride, wm, sH, sL, 0, W, W, Cc, 1 << (l % lps), flags, st);
+                std::swap(xa, xb);
+            }
+        }
+        // ---- head: u = W1 [ReLU(s_H); ReLU(s_L)] + b1, du = dlogit w2 [u > 0]; dskip
+        {
+            BRows p{};
+            p.nsrc = 2;
+            p.s[0] = src(skip, S, 0, 1, head, Hc, S);                          // W1t rows of branch H
+            p.s[1] = src(skip + rb * S, S, 0, 1, head + (int64_t)S * Hc, Hc, S); // branch L
+            p.N = Hc; p.W = W; p.C = Cc;
+            p.Y = du; p.ldy = Hc;
+            p.aux0 = blob + off_bh1(d); p.aux1 = blob + off_wh2(d); p.aux2 = dlogit + (int64_t)c0 * W;
+            p.out1 = ru;
+            launch_rows<EP_HEAD_U>(p, 1, st);
+            BRows q{};
+            q.nsrc = 1;
+            q.s[0] = src(du, Hc, 0, 0, blob + off_wh1(d), 2 * S, Hc);
+            q.N = 2 * S; q.W = W; q.C = Cc;
+            q.aux0 = skip; q.out1 = dskip; q.aux_boff = rb * S;
+            launch_rows<EP_HEAD_DH>(q, 1, st);
+            // dW1[:, branch half] = sum_r du[r] ReLU(s_branch[r])^T, db1 = sum_r du[r]
+            float *g1 = gw + off_wh1(d);
+            BWg p1 = wg(du, Hc, Hc, 0, skip, S, S, 0, 0, g1, 2 * S, 0, gw + off_bh1(d), 0, W, Cc);
+            p1.xrelu = 1;
+            launch_wgrad(p1, 1, st);
+            BWg p2 = wg(du, Hc, Hc, 0, skip + rb * S, S, S, 0, 0, g1 + S, 2 * S, 0, nullptr, 0, W, Cc);
+            p2.xrelu = 1;
+            launch_wgrad(p2, 1, st);
+            // dw2[j] = sum_r ReLU(u)[r][j] dlogit[r]; db2 = sum_r dlogit[r]
+            launch_wgrad(wg(ru, Hc, Hc, 0, dlogit + (int64_t)c0 * W, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, Cc),
+                         1, st);
+            launch_wgrad(wg(dlogit + (int64_t)c0 * W, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W,
+                            Cc), 1, st);
+        }
+        // ---- branches, stack by stack in reverse, recomputing each stack from its input
+        float *dx_hi = w->dxa.as<float>(), *dx_lo = w->dxb.as<float>();   // dL/dx_{l+1}, dL/dx_l
+        GWE_CUDA_TRY(cudaMemsetAsync(dx_hi, 0, sizeof(float) * 2 * rb * R, st));
+        const int64_t xb_off = rb * R;               // branch offsets in [branch][rows][C] arrays
+        for (int k = stacks - 1; k >= 0; --k) {
+            GWE_CUDA_TRY(cudaMemcpyAsync(xrec, xsave + (size_t)k * rows2 * R, sizeof(float) * 2 * rb * R,
+                                         cudaMemcpyDeviceToDevice, st));
+            for (int j = 0; j < lps; ++j) {
+                const int l = k * lps + j;
+                const float *wl = layers + (int64_t)l * f.layer_stride;
+                float *xin = xrec + (size_t)j * rows2 * R, *xout = xrec + (size_t)(j + 1) * rows2 * R;
+                float *aout = arec + (size_t)j * rows2 * 2 * R;
+                if (v == kSmall)
+                    launch_layer<32, 32>(xin, xout, w->dummy.as<float>(), wl, bstride, wm, sH, sL, 0, W, W, Cc, 1 << j,
+                                         LF_NO_SKIP, st, aout);
+                else
+                    launch_layer<64, 128>(xin, xout, w->dummy.as<float>(), wl, bstride, wm, sH, sL, 0, W, W, Cc, 1 << j,
+                                          LF_NO_SKIP, st, aout);
+            }
+            for (int j = lps - 1; j >= 0; --j) {
+                const int l = k * lps + j, dl = 1 << j;
+                const float *xl = xrec + (size_t)j * rows2 * R;
+                const float *al = arec + (size_t)j * rows2 * 2 * R;
+                // dz and the gate backward -> da, z
+                BRows p{};
+                p.nsrc = 2;
+                p.s[0] = src(dx_hi, R, 0, 0, blob + off_wres(d, 0, l), R, R);
+                p.s[1] = src(dskip, S, 0, 0, blob + off_wskip(d, 0, l), R, S);
+                p.N = R; p.W = W; p.C = Cc;
+                p.a_boff = 0; p.w_boff = Pb; p.y_boff = rb * 2 * R;
+                p.Y = da; p.ldy = 2 * R;
+                p.aux0 = al; p.out1 = z; p.aux_boff = rb * R;
+                // per-branch A offsets differ between the two sources; run one branch per launch
+                for (int b = 0; b < 2; ++b) {
+                    BRows pb = p;
+                    pb.s[0].A = dx_hi + b * xb_off;
+                    pb.s[1].A = dskip + b * rb * S;
+                    pb.s[0].Wt = blob + off_wres(d, b, l);
+                    pb.s[1].Wt = blob + off_wskip(d, b, l);
+                    pb.w_boff = 0;
+                    pb.Y = da + b * rb * 2 * R; pb.y_boff = 0;
+                    pb.aux0 = al + b * rb * 2 * R; pb.out1 = z + b * rb * R; pb.aux_boff = 0;
+                    launch_rows<EP_DZ>(pb, 1, st);
+                }
+                // weight gradients of this layer (both branches: offsets per branch)
+                launch_wgrad(wg(dx_hi, R, R, xb_off, z, R, R, 0, rb * R, gw + off_wres(d, 0, l), R, Pb,
+                                gw + off_bres(d, 0, l), Pb, W, Cc), 2, st);
+                launch_wgrad(wg(dskip, S, S, rb * S, z, R, R, 0, rb * R, gw + off_wskip(d, 0, l), R, Pb,
+                                gw + off_bskip(d, 0, l), Pb, W, Cc), 2, st);
+                launch_wgrad(wg(da, 2 * R, 2 * R, rb * 2 * R, xl, R, R, -dl, rb * R, gw + off_wconv(d, 0, l), 2 * R, Pb,
+                                gw + off_bconv(d, 0, l), Pb, W, Cc), 2, st);
+                launch_wgrad(wg(da, 2 * R, 2 * R, rb * 2 * R, xl, R, R, 0, rb * R, gw + off_wconv(d, 0, l) + R, 2 * R, Pb,
+                                nullptr, 0, W, Cc), 2, st);
+                // dx_l = dx_{l+1} + W1^T da(t) + W0^T da(t + d)
+                BRows q{};
+                q.nsrc = 2;
+                q.s[0] = src(da, 2 * R, 0, 0, blob + off_wconv(d, 0, l) + R, 2 * R, 2 * R);
+                q.s[1] = src(da, 2 * R, dl, 0, blob + off_wconv(d, 0, l), 2 * R, 2 * R);
+                q.N = R; q.W = W; q.C = Cc;
+                q.a_boff = rb * 2 * R; q.w_boff = Pb; q.y_boff = rb * R;
+                q.Y = dx_lo; q.ldy = R; q.aux0 = dx_hi;
+                launch_rows<EP_ADD>(q, 2, st);
+                std::swap(dx_hi, dx_lo);
+            }
+        }
+        // ---- input projection: dw_in, db_in and dL/dstrain
+        {
+            launch_wgrad(wg(dx_hi, R, R, 0, sH, 1, 1, 0, 0, gw + off_branch(d, 0), 1, 0, gw + off_branch(d, 0) + R, 0,
+                            W, Cc), 1, st);
+            launch_wgrad(wg(dx_hi + xb_off, R, R, 0, sL, 1, 1, 0, 0, gw + off_branch(d, 1), 1, 0,
+                            gw + off_branch(d, 1) + R, 0, W, Cc), 1, st);
+            const unsigned nb = (unsigned)((rb + 7) / 8);
+            if (gH) {
+                k_dstrain<<<nb, 256, 0, st>>>(dx_hi, blob + off_branch(d, 0), R, rb, gH + (int64_t)c0 * W);
+                note_launch();
+            }
+            if (gL) {
+                k_dstrain<<<nb, 256, 0, st>>>(dx_hi + xb_off, blob + off_branch(d, 1), R, rb, gL + (int64_t)c0 * W);
+                note_launch();
+            }
+        }
+        GWE_CUDA_TRY(cudaGetLastError());
     }
     return GWE_OK;
 }

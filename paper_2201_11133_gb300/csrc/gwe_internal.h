@@ -106,7 +106,8 @@ struct gwe_model {
     int device = 0;
     gwe::DevBuf w32;              // FP32 blob [n_models][P] as given
     gwe::Fp32Weights f32;         // FP32 kernel layout
-    void *bf16 = nullptr;         // BF16 path state (opaque, bf16_path.cu)
+    void *bf16 = nullptr;         // tensor-core path state (opaque, branch_tc.cu)
+    void *bwd = nullptr;          // backward workspace (opaque, fp32_path.cu)
     gwe::Workspace ws;
 };
 
@@ -118,6 +119,11 @@ gwe_status fp32_prepare(gwe_model *m, const float *host_blob);
 gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
                         int stride, int64_t n_windows, const int32_t *slides, int n_slides, float *out,
                         bool logits, cudaStream_t st);
+
+// Backward pass of one ensemble member (FP32, per-stack recomputation); grad_w is overwritten.
+gwe_status fp32_backward(gwe_model *m, int model_index, const float *xH, const float *xL, int batch, int W,
+                         const float *dlogit, float *grad_w, float *grad_H, float *grad_L, cudaStream_t st);
+void fp32_backward_release(gwe_model *m);
 
 // branch_tc.cu (tensor-core path: GWE_BF16)
 gwe_status bf16_check(gwe_model *m, cudaStream_t st);
