@@ -242,19 +242,25 @@ gwe_status gwe_triggers(const float *prob, int n_models, int n_slides, int64_t n
                         gwe_trigger *out, int64_t cap, int64_t *n_out, void *stream);
 
 /*
- * Whitening front end (paper section "Data curation": the strain is whitened
- * with power spectral densities estimated from the data, then normalised to
- * unit standard deviation).  Welch PSD with a Hann window, segments of
- * seg_len samples at 50 % overlap, accumulated in FP64; the strain spectrum
- * is divided by sqrt(fs * PSD / 2) (PSD interpolated linearly onto the data's
- * frequency grid), zeroed below 15 Hz, transformed back and scaled to unit
- * standard deviation.
- *   strain   device FP32 [n] (one detector).
- *   n        samples; must be >= seg_len.
- *   fs       sample rate in Hz.
- *   seg_len  Welch segment length, a power of two (16384 = 4 s at 4096 Hz).
+ * Whitening front end (paper section "Materials and Methods", paragraph "Data
+ * preparation": the strain is whitened with power spectral densities
+ * estimated from the data, then normalised to unit standard deviation).
+ * Welch PSD: segments of seg_len samples at 50 % overlap, each minus its mean,
+ * periodic Hann window, one-sided density, averaged over segments; the segment
+ * transforms are FP32, the accumulation of |X|^2 and the PSD are FP64.  The
+ * strain spectrum (FP32 transform of all n samples) is divided by
+ * sqrt(fs * PSD / 2), the PSD interpolated linearly onto the data's frequency
+ * grid, zeroed below 15 Hz, transformed back and scaled to unit standard
+ * deviation (FP64 sums).  The FFTs are cuFFT calls; everything else is this
+ * library's kernels.
+ *   strain   device FP32 [n] (one detector; not modified).
+ *   n        samples; >= seg_len.
+ *   fs       sample rate in Hz (> 0).
+ *   seg_len  Welch segment length, a power of two >= 16 (16384 = 4 s at 4096 Hz).
  *   flags    0.
- *   out      device FP32 [n] whitened strain (may not alias strain).
+ *   out      device FP32 [n], whitened strain; must not alias strain.
+ * Asynchronous on `stream`; plans and work buffers are cached in the library
+ * (one whitening at a time per process).  GWE_ERR_ARG for invalid arguments.
  */
 gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream);
 

@@ -14,6 +14,8 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   find_peaks pinned (SciPy find_peaks as a library, rectangle/triangle closed forms)
   coincidence pinned (brute force over all tuples)
   stitch     pinned (explicit index map on a ramp)
+  whiten.welch_psd / whiten.whiten  pinned (scipy.signal.welch as a library, sinusoid
+      closed forms, statistics of whitened white and coloured noise)
 """
 from __future__ import annotations
 

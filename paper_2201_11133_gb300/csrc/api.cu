@@ -227,9 +227,13 @@ gwe_status gwe_sync(gwe_model *m, void *stream) {
 
 gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream) {
     clear_error();
-    (void)strain; (void)n; (void)fs; (void)seg_len; (void)flags; (void)out; (void)stream;
-    set_error("gwe_whiten: not built yet");
-    return GWE_ERR_UNSUPPORTED;
+    GWE_ARG_CHECK(strain != nullptr && out != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(out != strain, "out must not alias strain");
+    GWE_ARG_CHECK(fs > 0.0, "fs must be positive");
+    GWE_ARG_CHECK(seg_len >= 16 && (seg_len & (seg_len - 1)) == 0, "seg_len must be a power of two >= 16");
+    GWE_ARG_CHECK(n >= seg_len, "n_samples < seg_len");
+    GWE_ARG_CHECK(flags == 0, "flags must be 0");
+    return whiten_run(strain, n, fs, seg_len, out, as_stream(stream));
 }
 
 }  // extern "C"

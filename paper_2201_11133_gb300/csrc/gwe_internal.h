@@ -134,6 +134,9 @@ gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
                         bool logits, cudaStream_t st);
 bool bf16_supported(const Dims &d);
 
+// whiten.cu: Welch PSD (FP64 accumulation) and spectral whitening of one detector's strain
+gwe_status whiten_run(const float *x, int64_t n, double fs, int seg, float *out, cudaStream_t st);
+
 // triggers.cu
 gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,
                         int stride, float thr, double min_width, int64_t coinc, int flags, gwe_trigger *out,

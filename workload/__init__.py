@@ -254,3 +254,40 @@ def coloured_noise(n: int, seed: int = 1000, fs: int = FS) -> np.ndarray:
     spec = (rng.standard_normal(f.shape[0]) + 1j * rng.standard_normal(f.shape[0])) * amp / math.sqrt(2.0)
     spec[0] = 0.0
     return np.fft.irfft(spec, n) * 1e21
+
+
+def coloured_stream(n: int, seed: int = 1000, n_inj: int = 0, snr_range=(6.0, 20.0), mc_range=(5.0, 30.0),
+                    min_gap: int = 2 * FS, fs: int = FS):
+    """Two detector streams of n samples (float32) of coloured Gaussian noise with the analytic
+    spectrum (scaled by 1e21) and n_inj unwhitened leading-order chirps.
+
+    Each chirp is scaled so that, whitened with the true spectrum (division of its transform by
+    sqrt(fs S / 2), S the spectrum of the scaled noise), its norm is the detector SNR
+    (network SNR / sqrt(2)); mergers uniform, >= min_gap apart; Livingston delayed by U[-10, 10] ms
+    with an independent phase.  Stands in for unwhitened GWOSC strain with injections."""
+    xh = coloured_noise(n, seed=seed)
+    xl = coloured_noise(n, seed=seed + 1)
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    mergers = []
+    lo = 6 * fs
+    if n_inj > 0 and n > lo + 2 * fs:
+        slots = np.sort(rng.choice(np.arange(lo, n - fs, min_gap), size=n_inj, replace=False))
+        for tm in slots:
+            mc = rng.uniform(*mc_range)
+            snr = rng.uniform(*snr_range) / math.sqrt(2.0)
+            dt = int(round(rng.uniform(-0.010, 0.010) * fs))
+            ph = rng.uniform(0, 2 * math.pi)
+            for x, t_m, p0 in ((xh, int(tm), 0.0), (xl, int(tm) + dt, ph)):
+                n_before = min(t_m, 6 * fs)
+                h = newtonian_chirp(mc, n_before, fs=fs, phase0=p0)
+                pad = 8192
+                m = h.shape[0] + pad
+                hf = np.fft.rfft(np.concatenate([h, np.zeros(pad)]))
+                f = np.fft.rfftfreq(m, 1.0 / fs)
+                wf = hf / np.sqrt(fs * aligo_like_psd(f) * 1e42 / 2.0)
+                wf[f < 15.0] = 0.0
+                norm = math.sqrt(float(np.sum(np.fft.irfft(wf, m) ** 2)))
+                if norm > 0:
+                    x[t_m - n_before:t_m + 1] += h * (snr / norm)
+            mergers.append(int(tm))
+    return xh.astype(np.float32), xl.astype(np.float32), mergers
