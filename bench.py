@@ -227,6 +227,8 @@ def main():
     ap.add_argument("--cpu-windows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--slides", type=int, default=64,
+                    help="also time the time-slide background pass with this many Livingston offsets (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -342,6 +344,53 @@ def main():
         e2e = {"value": world * strain_s * e2e_steps / t_tot, "unit": UNIT,
                "h2d_bytes_per_step": int(hH.nbytes + hL.nbytes), "d2h_bytes_per_step": int(d2h)}
 
+    # time slides (the background estimate): offsets of 1..K seconds on the same hour, whitening +
+    # branch pass once + slide heads + triggers on all K x 4 series
+    slides_res = None
+    if args.slides > 0 and prec == 1:
+        k_sl = args.slides
+        offs = [2 * (i + 1) for i in range(k_sl)]          # 1 s = 2 windows at 0.5 s stride
+        out_sl = torch.empty((k_sl, cfg["n_models"], nw, WINDOW), dtype=torch.float32, device=dev)
+
+        def slide_step():
+            gwe.gwe_whiten(H, n, float(FS), WELCH_SEG, Hw, stream=stream)
+            gwe.gwe_whiten(L, n, float(FS), WELCH_SEG, Lw, stream=stream)
+            gwe.gwe_forward(model.handle, Hw, Lw, n, WINDOW, STRIDE, offs, out_sl, stream)
+            return gwe.gwe_triggers(out_sl, cfg["n_models"], k_sl, nw, WINDOW, STRIDE, thr, min_width, coinc,
+                                    flags=0, stream=stream)
+
+        slide_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        gwe.gwe_profile_enable(True)
+        st_ms = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            recs = slide_step()
+            e1.record(stream)
+            e1.synchronize()
+            st_ms.append(e0.elapsed_time(e1))
+        prof_sl = gwe.gwe_profile_read()
+        gwe.gwe_profile_enable(False)
+        t_sl = sum(st_ms) / len(st_ms)
+        if dist:
+            t = torch.tensor([t_sl], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_sl = float(t.item())
+        slides_res = {"offsets": k_sl, "ms_per_step": t_sl,
+                      "physical_strain_s_per_s": world * strain_s / (t_sl / 1000.0),
+                      "effective_strain_s_per_s": world * strain_s * k_sl / (t_sl / 1000.0),
+                      "ensemble_triggers": int(np.sum(recs["model"] == -1)) if len(recs) else 0,
+                      "kernels": {k: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2}
+                                  for k, v in prof_sl.items()},
+                      "note": "branch pass once per window (projections of the head's first conv kept in FP16), "
+                              "slide heads per offset, triggers on every (offset, model) series"}
+        del out_sl
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -399,6 +448,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "time_slides": slides_res,
         "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                     for k, v in prof.items()},
     }

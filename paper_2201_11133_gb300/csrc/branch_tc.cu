@@ -153,6 +153,12 @@ struct TcParams {
     int L, lps;
     uint64_t ring_rows;        // lag-history rows per branch (sum of dilations)
     int *err;                  // error word: wait site of the first timeout
+    int model0;                // jobs cover models model0 .. model0 + n_models - 1
+    // Projection mode (proj != NULL): instead of the head, store per branch the head's first
+    // convolution restricted to that branch, P_H = W_h1[:, H] ReLU(s_H) + b_h1 and
+    // P_L = W_h1[:, L] ReLU(s_L), FP16, laid out [branch][window][Hc/8][W][8] (relative to model
+    // model0's block); time slides then only evaluate ReLU(P_H + P_L') . w_h2 + b_h2.
+    uint16_t *proj;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -203,7 +209,7 @@ __device__ __forceinline__ Job decode_job(const TcParams &p, int64_t j) {
     Job q;
     q.w = j % p.nw;
     const int64_t r = j / p.nw;
-    q.m = (int)(r % p.n_models);
+    q.m = p.model0 + (int)(r % p.n_models);
     q.si = (int)(r / p.n_models);
     int64_t k = p.slides ? (int64_t)p.slides[q.si] : 0;
     int64_t wl = (q.w + k) % p.nw;
@@ -446,7 +452,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             for (int ks = 0; ks < Sh::HQ / 16; ++ks) {
                                 const uint64_t ad = sdesc(ha + 2 * ks * (kTile * 16), kTile * 16, 128);
                                 const uint64_t bd = sdesc(we + 2 * ks * (Sh::HP * 16), Sh::HP * 16, 128);
-                                mma_f16(tmem + nh * Sh::TMEM_BSTRIDE, ad, bd, ID_HEAD, (kq > 0 || ks > 0) ? 1u : 0u);
+                                if (p.proj)   // P_H pieces in branch 0's columns, P_L pieces in branch 1's
+                                    mma_f16(tmem + (kq >> 1) * Sh::TMEM_BSTRIDE + nh * Sh::HP, ad, bd, ID_HEAD,
+                                            ((kq & 1) || ks > 0) ? 1u : 0u);
+                                else
+                                    mma_f16(tmem + nh * Sh::TMEM_BSTRIDE, ad, bd, ID_HEAD, (kq > 0 || ks > 0) ? 1u : 0u);
                             }
                             mma_commit(&bar[B_WEMPTY + e]);
                             ++it[e];
@@ -651,6 +661,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 if (!warp_wait(B_HEAD, ph_head & 1, 33)) { ok = false; break; }
                 ++ph_head;
                 tc_fence_after();
+                if (p.proj) {
+                    // P_b (+ b_h1 for the Hanford branch), FP16, 16-byte chunks of 8 channels, rows contiguous
+                    uint16_t *pw = p.proj + ((uint64_t)b * p.nw + (uint64_t)jb.w) * (uint64_t)HC * p.W;
+                    const uint32_t t_p = tmem + t_lane + b * Sh::TMEM_BSTRIDE;
+                    constexpr int HH = HC / 2;       // channels per thread (half)
+#pragma unroll
+                    for (int cc = 0; cc < HH / 16; ++cc) {
+                        const int ch = hf * HH + 16 * cc;
+                        uint32_t ur[16];
+                        tmem_ld16(t_p + ch, ur);
+                        tmem_ld_wait();
+                        float u[16];
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj)
+                            u[jj] = __uint_as_float(ur[jj]) + (b == 0 ? __ldg(b1 + ch + jj) : 0.f);
+                        uint4 v0 = make_uint4(pack_h2(u[0], u[1]), pack_h2(u[2], u[3]), pack_h2(u[4], u[5]),
+                                              pack_h2(u[6], u[7]));
+                        uint4 v1 = make_uint4(pack_h2(u[8], u[9]), pack_h2(u[10], u[11]), pack_h2(u[12], u[13]),
+                                              pack_h2(u[14], u[15]));
+                        *reinterpret_cast<uint4 *>(pw + ((uint64_t)(ch / 8) * p.W + t0 + r) * 8) = v0;
+                        *reinterpret_cast<uint4 *>(pw + ((uint64_t)(ch / 8 + 1) * p.W + t0 + r) * 8) = v1;
+                    }
+                    tc_fence_before();
+                    continue;
+                }
                 float acc = 0.f;
                 if (b < Sh::NH) {
                     const uint32_t t_u = tmem + t_lane + b * Sh::TMEM_BSTRIDE + hf * HPH;
@@ -691,6 +726,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
     }
 }
 
+// Time slides on the branch projections: for each slide k, Hanford window w is paired with
+// Livingston window (w + k) mod n_w, and
+//   out[slide][w][t] = sigmoid(b_h2 + sum_j w_h2[j] ReLU(P_H[w][t][j] + P_L[w'][t][j]))
+// (the head's first convolution is linear in [s_H ; s_L], so the branch pass runs once per window
+// and a slide costs 3 Hc operations per sample).  FP16x2 ReLU-add and products with FP16 partial
+// sums over 16 channels, FP32 across partials, FP32 logit and sigmoid.
+// Grid: x = window (fast, so that concurrent blocks share the Livingston tiles in L2), y = 128-sample
+// tile; 128 threads, thread = sample; the block's Hanford tile is staged in shared memory.
+constexpr int kSlideT = 128;
+
+template <int HC>
+__global__ void __launch_bounds__(128) k_slide_head(const uint16_t *__restrict__ proj, int64_t nw, int W,
+                                                    const int32_t *__restrict__ koff, int n_slides,
+                                                    const float *__restrict__ w2, float b2, float *__restrict__ out,
+                                                    int64_t slide_stride, int logits) {
+    constexpr int NC = HC / 8;                    // 16-byte chunks per sample
+    extern __shared__ uint4 ph_s[];               // [NC][128]
+    __shared__ uint32_t w2h[HC / 2];
+    const int64_t w = blockIdx.x;
+    const int t0 = blockIdx.y * kSlideT, t = threadIdx.x;
+    const uint64_t bstride = (uint64_t)nw * HC * W;   // elements per branch block
+    const uint4 *pH = reinterpret_cast<const uint4 *>(proj + (uint64_t)w * HC * W);
+    for (int c = 0; c < NC; ++c) ph_s[c * kSlideT + t] = pH[(uint64_t)c * W + t0 + t];
+    for (int j = t; j < HC / 2; j += kSlideT) w2h[j] = pack_h2(w2[2 * j], w2[2 * j + 1]);
+    __syncthreads();
+    const uint32_t one2 = 0x3C003C00u;            // (1, 1) in FP16x2
+    for (int si = 0; si < n_slides; ++si) {
+        int64_t wl = w + koff[si];                // koff[si] = slide offset reduced to [0, n_w)
+        if (wl >= nw) wl -= nw;
+        const uint4 *pL = reinterpret_cast<const uint4 *>(proj + bstride + (uint64_t)wl * HC * W);
+        float acc = 0.f;
+#pragma unroll 4
+        for (int c = 0; c < NC; c += 2) {
+            uint32_t hacc = 0u;
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const uint4 a = ph_s[(c + cc) * kSlideT + t];
+                const uint4 l = __ldg(pL + (uint64_t)(c + cc) * W + t0 + t);
+                const uint32_t av[4] = {a.x, a.y, a.z, a.w}, lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t rl;
+                    asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(rl) : "r"(av[q]), "r"(one2), "r"(lv[q]));
+                    hacc = hfma2(rl, w2h[(c + cc) * 4 + q], hacc);
+                }
+            }
+            const __half2 hh = *reinterpret_cast<__half2 *>(&hacc);
+            const float2 f2 = __half22float2(hh);
+            acc += f2.x + f2.y;
+        }
+        const float lg = acc + b2;
+        out[(uint64_t)si * slide_stride + (uint64_t)w * W + t0 + t] = logits ? lg : 1.f / (1.f + expf(-lg));
+    }
+}
+
 }  // namespace
 }  // namespace gwe
 
@@ -700,9 +790,10 @@ namespace {
 
 struct TcState {
     int variant = -1;            // 0: (R, S, Hc) = (32, 32, 32); 1: (64, 128, 256)
-    DevBuf img, pblob, ring, zeros, err, slides;
+    DevBuf img, pblob, ring, zeros, err, slides, proj, koff;
     uint64_t img_stride = 0, pblob_stride = 0;
     int sms = 0;
+    std::vector<float> b2_host;   // b_h2 per model (slide heads take it by value)
 };
 
 int tc_variant(const Dims &d) {
@@ -815,8 +906,11 @@ void build_images(const Dims &d, const float *hb, std::vector<uint8_t> &img, std
 
 template <int R, int S, int HC>
 cudaError_t set_tc_attr() {
-    return cudaFuncSetAttribute(k_branch_tc<R, S, HC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TcShape<R, S, HC>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_branch_tc<R, S, HC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TcShape<R, S, HC>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_slide_head<HC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((HC / 8) * kSlideT * 16));
 }
 
 template <int R, int S, int HC>
@@ -824,19 +918,24 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
                      const int32_t *slides_host, int n_slides, float *out, bool logits, cudaStream_t st) {
     using Sh = TcShape<R, S, HC>;
     const Dims &d = m->dims;
-    const int ns = n_slides > 0 ? n_slides : 1;
-    const int64_t n_jobs = (int64_t)ns * d.n_models * nw;
-    if (n_jobs <= 0) return GWE_OK;
+    if (nw <= 0) return GWE_OK;
     uint64_t ring_rows = 0;
     for (int l = 0; l < d.L; ++l) ring_rows += (uint64_t)1 << (l % d.lps);
     const uint64_t ring_cta = (2 * ring_rows * 2 * R + 255) & ~uint64_t(255);
-    const int grid = (int)std::min<int64_t>(s.sms, n_jobs);
-    GWE_CUDA_TRY(s.ring.ensure(ring_cta * grid));
+    const int64_t max_jobs = (int64_t)d.n_models * nw;
+    const int grid_max = (int)std::min<int64_t>(s.sms, max_jobs);
+    GWE_CUDA_TRY(s.ring.ensure(ring_cta * grid_max));
     const int32_t *dsl = nullptr;
     if (n_slides > 0) {
-        GWE_CUDA_TRY(s.slides.ensure(sizeof(int32_t) * n_slides));
-        GWE_CUDA_TRY(cudaMemcpyAsync(s.slides.ptr, slides_host, sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
-        dsl = s.slides.as<int32_t>();
+        // offsets reduced to [0, n_w) on the host (pageable source: the copy is staged before return)
+        std::vector<int32_t> red(n_slides);
+        for (int i = 0; i < n_slides; ++i) {
+            int64_t k = (int64_t)slides_host[i] % nw;
+            red[i] = (int32_t)(k < 0 ? k + nw : k);
+        }
+        GWE_CUDA_TRY(s.koff.ensure(sizeof(int32_t) * n_slides));
+        GWE_CUDA_TRY(cudaMemcpyAsync(s.koff.ptr, red.data(), sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
+        dsl = s.koff.as<int32_t>();
     }
     TcParams p;
     p.wimg = s.img.as<uint8_t>();
@@ -848,8 +947,8 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     p.nw = nw;
     p.W = W;
     p.stride = stride;
-    p.slides = dsl;
-    p.n_slides = n_slides;
+    p.slides = nullptr;
+    p.n_slides = 0;
     p.n_models = d.n_models;
     p.out = out;
     p.logits = logits ? 1 : 0;
@@ -860,12 +959,41 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     p.lps = d.lps;
     p.ring_rows = ring_rows;
     p.err = s.err.as<int>();
-    {
+    p.model0 = 0;
+    p.proj = nullptr;
+    if (n_slides == 0) {
         ProfScope prof("k_branch_tc", st);
-        k_branch_tc<R, S, HC><<<grid, kThreads, Sh::SMEM, st>>>(p);
+        k_branch_tc<R, S, HC><<<grid_max, kThreads, Sh::SMEM, st>>>(p);
         note_launch();
+        GWE_CUDA_TRY(cudaGetLastError());
+        return GWE_OK;
     }
-    GWE_CUDA_TRY(cudaGetLastError());
+    // Time slides: per model, one branch pass storing the projections, then the slide heads.
+    const uint64_t proj_elems = 2ull * (uint64_t)nw * HC * W;
+    GWE_CUDA_TRY(s.proj.ensure(proj_elems * sizeof(uint16_t)));
+    const int grid = (int)std::min<int64_t>(s.sms, nw);
+    for (int mi = 0; mi < d.n_models; ++mi) {
+        TcParams q = p;
+        q.model0 = mi;
+        q.n_models = 1;
+        q.proj = s.proj.as<uint16_t>();
+        {
+            ProfScope prof("k_branch_tc", st);
+            k_branch_tc<R, S, HC><<<grid, kThreads, Sh::SMEM, st>>>(q);
+            note_launch();
+        }
+        const float *w2 = m->w32.as<float>() + (int64_t)mi * d.P + off_wh2(d);
+        const float b2 = s.b2_host[mi];
+        dim3 g2((unsigned)nw, (unsigned)(W / kSlideT));
+        {
+            ProfScope prof("k_slide_head", st);
+            k_slide_head<HC><<<g2, kSlideT, (HC / 8) * kSlideT * 16, st>>>(s.proj.as<uint16_t>(), nw, W, dsl, n_slides, w2, b2,
+                                                            out + (int64_t)mi * nw * W, (int64_t)d.n_models * nw * W,
+                                                            logits ? 1 : 0);
+            note_launch();
+        }
+        GWE_CUDA_TRY(cudaGetLastError());
+    }
     return GWE_OK;
 }
 
@@ -900,6 +1028,8 @@ gwe_status bf16_prepare(gwe_model *m, const float *hb) {
     GWE_CUDA_TRY(s->err.ensure(256));
     GWE_CUDA_TRY(cudaMemset(s->err.ptr, 0, 256));
     GWE_CUDA_TRY(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, m->device));
+    s->b2_host.resize(d.n_models);
+    for (int mi = 0; mi < d.n_models; ++mi) s->b2_host[mi] = hb[(int64_t)mi * d.P + off_bh2(d)];
     if (s->variant == 0) {
         GWE_CUDA_TRY((set_tc_attr<32, 32, 32>()));
     } else {
@@ -917,6 +1047,8 @@ void bf16_release(gwe_model *m) {
     s->zeros.release();
     s->err.release();
     s->slides.release();
+    s->proj.release();
+    s->koff.release();
     delete s;
     m->bf16 = nullptr;
 }
@@ -1038,6 +1170,8 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.lps = d.lps;
     p.ring_rows = ring_rows;
     p.err = err;
+    p.model0 = 0;
+    p.proj = nullptr;
     k_branch_tc<R, S, HC><<<grid, kThreads, Sh::SMEM, st>>>(p);
     note_launch();
     GWE_CUDA_TRY(cudaGetLastError());

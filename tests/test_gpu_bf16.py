@@ -66,3 +66,26 @@ def test_bf16_thirty_layer_ensemble():
     err = np.max(np.abs(out.cpu().numpy() - ref))
     print("bf16 30-layer max|dprob|", err)
     assert err <= TOL_BF16
+
+
+def test_bf16_ensemble_time_slides():
+    """64-slide style background: branches once per window, slide heads on the projections."""
+    import torch
+    dev = require_gpu()
+    cfg = workload.config("ensemble")
+    W, stride = 1024, 512
+    n = W + 5 * stride + 17
+    sh, sl, _ = workload.stream(n, seed=37)
+    wb = workload.init_weights(cfg, seed=3000, bias_std=0.05)
+    slides = [1, 2, 5, -3, 0]
+    ref = oracle.forward_stream(cfg, wb, sh, sl, W, stride, slides=slides)
+    m = _model(cfg, wb)
+    out = m.forward(torch.from_numpy(sh).to(dev), torch.from_numpy(sl).to(dev), W, stride, slides=slides)
+    m.sync()
+    err = np.max(np.abs(out.cpu().numpy() - ref))
+    print("bf16 30-layer slides max|dprob|", err)
+    assert err <= TOL_BF16
+    # the zero-lag slide equals the plain forward
+    z = m.forward(torch.from_numpy(sh).to(dev), torch.from_numpy(sl).to(dev), W, stride)
+    m.sync()
+    assert np.max(np.abs(out[4].cpu().numpy() - z[0].cpu().numpy())) <= 2e-3
