@@ -280,6 +280,17 @@ gwe_status gwe_profile_read(int idx, char *name, int name_cap, double *total_ms,
 /* Total number of kernels this library has launched in the process (all calls). */
 int64_t gwe_launch_count(void);
 
+/*
+ * Failure-detection test hook (the paper has no counterpart).  Every wait
+ * inside the tensor-core kernels is bounded; wait_seconds sets that bound
+ * (default 4 s, at most 60).  drop = 1 makes the Hanford branch's producer warp
+ * issue nothing, so a consumer's wait runs out: the kernel records the wait
+ * site, every role drains the copies and MMAs it issued and leaves, TMEM is
+ * freed, and gwe_sync returns GWE_ERR_TIMEOUT; the CUDA context stays usable.
+ * drop = 0 restores normal operation.  Process-wide; not for production use.
+ */
+gwe_status gwe_debug_config(int drop, double wait_seconds);
+
 /* Thread-local description of the last error ("" if none). */
 const char *gwe_last_error(void);
 

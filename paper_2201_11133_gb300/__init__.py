@@ -83,6 +83,7 @@ def load():
             "gwe_triggers": (I, [P, I, I, I64, I, I, F, D, I64, I, P, I64, P, P]),
             "gwe_whiten": (I, [P, I64, D, I, I, P, P]),
             "gwe_sync": (I, [P, P]),
+            "gwe_debug_config": (I, [I, D]),
             "gwe_forward_static": (I, [P, P, P, I64, I, I, P, P, P]),
             "gwe_profile_enable": (I, [I]),
             "gwe_profile_read": (I, [I, P, I, P, P]),
@@ -215,6 +216,11 @@ def gwe_forward_static(model: int, strain_H, strain_L, n_samples: int, window: i
     _check(load().gwe_forward_static(model, _dptr(strain_H), _dptr(strain_L), int(n_samples), int(window),
                                      int(stride), _dptr(out_prob), _dptr(status), _stream(stream)),
            "gwe_forward_static")
+
+
+def gwe_debug_config(drop: int, wait_seconds: float) -> None:
+    """Failure-detection test hook: bound of device waits and a dropped producer (see include/gwe.h)."""
+    _check(load().gwe_debug_config(int(drop), float(wait_seconds)), "gwe_debug_config")
 
 
 def gwe_sync(model: int, stream=None) -> None:

@@ -225,6 +225,11 @@ gwe_status gwe_sync(gwe_model *m, void *stream) {
     return GWE_OK;
 }
 
+gwe_status gwe_debug_config(int drop, double wait_seconds) {
+    clear_error();
+    return debug_config(drop, wait_seconds);
+}
+
 gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream) {
     clear_error();
     GWE_ARG_CHECK(strain != nullptr && out != nullptr, "NULL buffer");

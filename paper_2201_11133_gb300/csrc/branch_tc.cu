@@ -159,6 +159,8 @@ struct TcParams {
     // P_L = W_h1[:, L] ReLU(s_L), FP16, laid out [branch][window][Hc/8][W][8] (relative to model
     // model0's block); time slides then only evaluate ReLU(P_H + P_L') . w_h2 + b_h2.
     uint16_t *proj;
+    uint64_t wait_ns;          // limit of every device-side wait
+    int dbg_drop;              // test hook: 1 = branch 0's producer issues nothing (its consumers' waits run out)
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -280,11 +282,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             // streams the head weight pieces through its two entries.
             if (lane == 0) {
                 uint32_t it[2] = {0, 0};       // items issued per entry
-                uint32_t lag_issued = 0, ph_h = 0, g = 0;
+                uint32_t lag_issued = 0, ph_h = 0, g = 0, g_conv = 0, g_res = 0;
                 bool ok = true, first = true;
                 uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * (2 * R);
                 auto take = [&](int e, int site) -> bool {
-                    return mbar_wait(&bar[B_WEMPTY + 2 * b + e], ((it[e] & 1) ^ 1), abort_flag, p.err, site, kWaitNs);
+                    return mbar_wait(&bar[B_WEMPTY + 2 * b + e], ((it[e] & 1) ^ 1), abort_flag, p.err, site, p.wait_ns);
                 };
                 auto issue_lag = [&](int l, int t0) {
                     const int d = 1 << (l % lps);
@@ -300,6 +302,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                                  &bar[B_LAG + b]);
                     ++lag_issued;
                 };
+                // test hook: branch 0's producer issues nothing, so the MMA warp's first wait runs out
+                if (p.dbg_drop == 1 && b == 0) ok = false;
                 for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
                     const Job q = decode_job(p, j);
                     const uint8_t *wm = p.wimg + (uint64_t)q.m * p.wimg_stride;
@@ -317,14 +321,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             mbar_arrive_expect_tx(&bar[B_BIAS + 4 * b + (g & 1)], Sh::BIAS_BYTES);
                             bulk_g2s(smem + Sh::OFF_BIAS + b * Sh::BIAS_BR + (g & 1) * Sh::BIAS_BYTES,
                                      play + (uint64_t)l * Sh::PL_BYTES, Sh::BIAS_BYTES, &bar[B_BIAS + 4 * b + (g & 1)]);
+                            g_conv = g + 1;
                             ++it[0];
                             // lagged rows: the staging buffer is free once the previous conv completed
                             // (layer 0: once the previous tile's head has read it)
                             if (l > 0 || first) {
                                 issue_lag(l, tt * kTile);
                             } else {
-                                ok = mbar_wait(&bar[B_HREADY + b], ph_h & 1, abort_flag, p.err, 3, kWaitNs) &&
-                                     mbar_wait(&bar[B_HEAD], ph_h & 1, abort_flag, p.err, 4, kWaitNs);
+                                ok = mbar_wait(&bar[B_HREADY + b], ph_h & 1, abort_flag, p.err, 3, p.wait_ns) &&
+                                     mbar_wait(&bar[B_HEAD], ph_h & 1, abort_flag, p.err, 4, p.wait_ns);
                                 if (!ok) break;
                                 ++ph_h;
                                 issue_lag(0, tt * kTile);
@@ -340,6 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             bulk_g2s(smem + Sh::OFF_BIAS + b * Sh::BIAS_BR + (2 + (g & 1)) * Sh::BIAS_BYTES,
                                      play + (uint64_t)l * Sh::PL_BYTES + Sh::BIAS_BYTES, Sh::BIAS_BYTES,
                                      &bar[B_BIAS + 4 * b + 2 + (g & 1)]);
+                            g_res = g + 1;
                             ++it[1];
                         }
                         if (!ok || b != 0) continue;
@@ -354,16 +360,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         }
                     }
                 }
-                // never leave with copies in flight
+                // never leave with copies in flight (the copies issued last on every barrier land)
                 for (int e = 0; e < 2; ++e)
                     if (it[e] > 0)
-                        mbar_wait(&bar[B_WFULL + 2 * b + e], (it[e] - 1) & 1, abort_flag, p.err, 7, kWaitNs);
+                        mbar_wait_drain(&bar[B_WFULL + 2 * b + e], (it[e] - 1) & 1, p.err, 7, p.wait_ns);
                 if (lag_issued > 0)
-                    mbar_wait(&bar[B_LAG + b], (lag_issued - 1) & 1, abort_flag, p.err, 8, kWaitNs);
-                for (uint32_t k = 0; k < 2 && k < g; ++k) {       // last b_conv / b_res of both slots
-                    const uint32_t gg = g - 1 - k;
-                    mbar_wait(&bar[B_BIAS + 4 * b + (gg & 1)], (gg >> 1) & 1, abort_flag, p.err, 9, kWaitNs);
-                    mbar_wait(&bar[B_BIAS + 4 * b + 2 + (gg & 1)], (gg >> 1) & 1, abort_flag, p.err, 9, kWaitNs);
+                    mbar_wait_drain(&bar[B_LAG + b], (lag_issued - 1) & 1, p.err, 8, p.wait_ns);
+                for (uint32_t k = 0; k < 2 && k < g_conv; ++k) {  // last b_conv of both slots
+                    const uint32_t gg = g_conv - 1 - k;
+                    mbar_wait_drain(&bar[B_BIAS + 4 * b + (gg & 1)], (gg >> 1) & 1, p.err, 9, p.wait_ns);
+                }
+                for (uint32_t k = 0; k < 2 && k < g_res; ++k) {   // last b_res of both slots
+                    const uint32_t gg = g_res - 1 - k;
+                    mbar_wait_drain(&bar[B_BIAS + 4 * b + 2 + (gg & 1)], (gg >> 1) & 1, p.err, 9, p.wait_ns);
                 }
             }
         } else {
@@ -391,15 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         // Ping-pong: branch 1 starts a tile once branch 0's first gate is done, so
                         // that one branch's MMAs overlap the other's gate for the rest of the tile.
                         if (b == 1) {
-                            if (!(ok = mbar_wait(&bar[B_GO], ph_go & 1, abort_flag, p.err, 19, kWaitNs))) break;
+                            if (!(ok = mbar_wait(&bar[B_GO], ph_go & 1, abort_flag, p.err, 19, p.wait_ns))) break;
                             ++ph_go;
                         }
                         for (int l = 0; l < L; ++l) {
                             const int d = 1 << (l % lps);
                             const int n = d < kTile ? d : kTile;
-                            ok = mbar_wait(&bar[B_XREADY + b], ph_x & 1, abort_flag, p.err, 10, kWaitNs) &&
-                                 mbar_wait(&bar[B_LAG + b], ph_lag & 1, abort_flag, p.err, 11, kWaitNs) &&
-                                 mbar_wait(&bar[B_WFULL + 2 * b], it[0] & 1, abort_flag, p.err, 12, kWaitNs);
+                            ok = mbar_wait(&bar[B_XREADY + b], ph_x & 1, abort_flag, p.err, 10, p.wait_ns) &&
+                                 mbar_wait(&bar[B_LAG + b], ph_lag & 1, abort_flag, p.err, 11, p.wait_ns) &&
+                                 mbar_wait(&bar[B_WFULL + 2 * b], it[0] & 1, abort_flag, p.err, 12, p.wait_ns);
                             if (!ok) break;
                             ++ph_x;
                             ++ph_lag;
@@ -416,8 +425,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             mma_commit(&bar[B_CONV + b]);
                             mma_commit(&bar[B_WEMPTY + 2 * b]);
                             ++it[0];
-                            ok = mbar_wait(&bar[B_ZREADY + b], ph_z & 1, abort_flag, p.err, 13, kWaitNs) &&
-                                 mbar_wait(&bar[B_WFULL + 2 * b + 1], it[1] & 1, abort_flag, p.err, 14, kWaitNs);
+                            ok = mbar_wait(&bar[B_ZREADY + b], ph_z & 1, abort_flag, p.err, 13, p.wait_ns) &&
+                                 mbar_wait(&bar[B_WFULL + 2 * b + 1], it[1] & 1, abort_flag, p.err, 14, p.wait_ns);
                             if (!ok) break;
                             ++ph_z;
                             if (b == 0 && l == 0) mbar_arrive(&bar[B_GO]);
@@ -437,13 +446,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         }
                         if (!ok || b != 0) continue;
                         // head (branch 0's MMA warp): u[nh] = sum over K quarters of h . W_h1[nh, quarter]^T
-                        ok = mbar_wait(&bar[B_HREADY + 0], ph_h & 1, abort_flag, p.err, 15, kWaitNs) &&
-                             mbar_wait(&bar[B_HREADY + 1], ph_h & 1, abort_flag, p.err, 16, kWaitNs);
+                        ok = mbar_wait(&bar[B_HREADY + 0], ph_h & 1, abort_flag, p.err, 15, p.wait_ns) &&
+                             mbar_wait(&bar[B_HREADY + 1], ph_h & 1, abort_flag, p.err, 16, p.wait_ns);
                         if (!ok) break;
                         ++ph_h;
                         for (int pc = 0; pc < Sh::NHP && ok; ++pc) {
                             const int e = pc & 1, nh = pc >> 2, kq = pc & 3;
-                            ok = mbar_wait(&bar[B_WFULL + e], it[e] & 1, abort_flag, p.err, 17, kWaitNs);
+                            ok = mbar_wait(&bar[B_WFULL + e], it[e] & 1, abort_flag, p.err, 17, p.wait_ns);
                             if (!ok) break;
                             tc_fence_after();
                             const uint32_t ha = s_stage + (kq >> 1) * Sh::STAGE_BYTES + (kq & 1) * (Sh::HQ / 8) * (kTile * 16);
@@ -466,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 }
                 // all MMAs issued by this thread complete before TMEM is released
                 mma_commit(&bar[B_FIN + b]);
-                mbar_wait(&bar[B_FIN + b], 0, abort_flag, p.err, 18, kWaitNs);
+                mbar_wait_drain(&bar[B_FIN + b], 0, p.err, 18, p.wait_ns);
             }
         }
     } else {
@@ -489,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
         const uint32_t half2_half = 0x38003800u;     // (0.5, 0.5) in FP16x2
 
         auto warp_wait = [&](int idx, uint32_t parity, int site) -> bool {
-            bool w = mbar_wait(&bar[idx], parity, abort_flag, p.err, site, kWaitNs);
+            bool w = mbar_wait(&bar[idx], parity, abort_flag, p.err, site, p.wait_ns);
             return __all_sync(0xffffffffu, w);
         };
         auto warp_arrive = [&](int idx) {
@@ -788,6 +797,10 @@ __global__ void __launch_bounds__(128) k_slide_head(const uint16_t *__restrict__
 namespace gwe {
 namespace {
 
+// Test hooks (gwe_debug_config): limit of every device-side wait, and a dropped producer.
+uint64_t g_wait_ns = kWaitNs;
+int g_dbg_drop = 0;
+
 struct TcState {
     int variant = -1;            // 0: (R, S, Hc) = (32, 32, 32); 1: (64, 128, 256)
     DevBuf img, pblob, ring, zeros, err, slides, proj, koff;
@@ -961,6 +974,8 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     p.err = s.err.as<int>();
     p.model0 = 0;
     p.proj = nullptr;
+    p.wait_ns = g_wait_ns;
+    p.dbg_drop = g_dbg_drop;
     if (n_slides == 0) {
         ProfScope prof("k_branch_tc", st);
         k_branch_tc<R, S, HC><<<grid_max, kThreads, Sh::SMEM, st>>>(p);
@@ -1069,6 +1084,16 @@ gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
     return launch_tc<64, 128, 256>(m, *s, sH, sL, nw, W, stride, slides, n_slides, out, logits, st);
 }
 
+gwe_status debug_config(int drop, double wait_seconds) {
+    if (drop < 0 || drop > 1 || !(wait_seconds > 0.0) || wait_seconds > 60.0) {
+        set_error("gwe_debug_config: drop must be 0 or 1 and wait_seconds in (0, 60]");
+        return GWE_ERR_ARG;
+    }
+    g_dbg_drop = drop;
+    g_wait_ns = (uint64_t)(wait_seconds * 1e9);
+    return GWE_OK;
+}
+
 gwe_status bf16_check(gwe_model *m, cudaStream_t st) {
     TcState *s = reinterpret_cast<TcState *>(m->bf16);
     if (!s) return GWE_OK;
@@ -1172,6 +1197,8 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.err = err;
     p.model0 = 0;
     p.proj = nullptr;
+    p.wait_ns = g_wait_ns;
+    p.dbg_drop = g_dbg_drop;
     k_branch_tc<R, S, HC><<<grid, kThreads, Sh::SMEM, st>>>(p);
     note_launch();
     GWE_CUDA_TRY(cudaGetLastError());

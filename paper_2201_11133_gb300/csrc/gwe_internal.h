@@ -127,6 +127,7 @@ void fp32_backward_release(gwe_model *m);
 
 // branch_tc.cu (tensor-core path: GWE_BF16)
 gwe_status bf16_check(gwe_model *m, cudaStream_t st);
+gwe_status debug_config(int drop, double wait_seconds);
 gwe_status bf16_prepare(gwe_model *m, const float *host_blob);
 void bf16_release(gwe_model *m);
 gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
