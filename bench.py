@@ -235,6 +235,7 @@ def main():
 
     import torch
     import paper_2201_11133_gb300 as gwe
+    from paper_2201_11133_gb300 import multi
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,11 +306,8 @@ def main():
     gwe.gwe_profile_enable(False)
     clk = clocks.stop()
     torch.cuda.synchronize()
-    total_ms = sum(times)
+    total_ms = multi.max_over_ranks(sum(times), dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
     strain_s = n / FS
@@ -337,10 +335,7 @@ def main():
             torch.cuda.synchronize()
             t_tot += time.perf_counter() - t0
             d2h = recs.nbytes + 8
-        if dist:
-            t = torch.tensor([t_tot], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_tot = float(t.item())
+        t_tot = multi.max_over_ranks(t_tot, dist, dev)
         e2e = {"value": world * strain_s * e2e_steps / t_tot, "unit": UNIT,
                "h2d_bytes_per_step": int(hH.nbytes + hL.nbytes), "d2h_bytes_per_step": int(d2h)}
 
@@ -376,11 +371,7 @@ def main():
             st_ms.append(e0.elapsed_time(e1))
         prof_sl = gwe.gwe_profile_read()
         gwe.gwe_profile_enable(False)
-        t_sl = sum(st_ms) / len(st_ms)
-        if dist:
-            t = torch.tensor([t_sl], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_sl = float(t.item())
+        t_sl = multi.max_over_ranks(sum(st_ms) / len(st_ms), dist, dev)
         slides_res = {"offsets": k_sl, "ms_per_step": t_sl,
                       "physical_strain_s_per_s": world * strain_s / (t_sl / 1000.0),
                       "effective_strain_s_per_s": world * strain_s * k_sl / (t_sl / 1000.0),
