@@ -118,6 +118,35 @@ gwe_status gwe_model_create(const gwe_model_config *cfg, const float *host_weigh
  * derived low-precision copies are rebuilt.  Synchronous. */
 gwe_status gwe_model_set_weights(gwe_model *model, const float *host_weights);
 
+/*
+ * Activation scales of a GWE_FP8 handle (the paper's TensorRT paragraph runs
+ * the network at reduced precision; it does not state how activations are
+ * scaled, so this call is the library's own).  Runs the FP32 forward of every
+ * model over the windows of one segment, records max |x_l[c]| per model,
+ * branch, layer l and residual channel c, and rebuilds the E4M3 weights with
+ * s_l[c] = 16 * max / 448 (values up to 16x the calibrated maximum stay in
+ * range; larger ones saturate).  Until it is called, a GWE_FP8 handle uses
+ * scales calibrated on 64 windows of synthetic unit-variance white Gaussian
+ * noise (whitened strain has unit standard deviation).
+ *   strain_H, strain_L  device, FP32, n_samples each (whitened strain).
+ *   window, stride      as in gwe_forward.
+ * Synchronous on `stream`.  GWE_ERR_UNSUPPORTED for a handle of another
+ * precision; GWE_ERR_ARG if stride > window or n_samples < window.
+ */
+gwe_status gwe_model_calibrate(gwe_model *model, const float *strain_H, const float *strain_L, int64_t n_samples,
+                               int window, int stride, void *stream);
+
+/*
+ * The calibration maxima of a GWE_FP8 handle, host FP32 [n_models][2 branches
+ * (H, L)][L layers][R channels]: max |x_l[c]| of the input of layer l.
+ * set: copies them (entries must be finite and >= 0; 0 means scale 1) and
+ * rebuilds the E4M3 weights (synchronous), so that scales computed elsewhere,
+ * for example by a reference implementation, can be applied.  get: copies the
+ * current values out.  GWE_ERR_UNSUPPORTED for a handle of another precision.
+ */
+gwe_status gwe_model_set_fp8_amax(gwe_model *model, const float *host_amax);
+gwe_status gwe_model_get_fp8_amax(gwe_model *model, float *host_amax);
+
 void gwe_model_destroy(gwe_model *model);
 
 /*
@@ -193,7 +222,7 @@ gwe_status gwe_sync(gwe_model *model, void *stream);
  * other work, or a process whose device memory is fully reserved up front by
  * a framework's pool.  The handle itself is still created (and allocated)
  * once, beforehand, with gwe_model_create.
- *   model       handle created with precision GWE_BF16.
+ *   model       handle created with precision GWE_BF16 or GWE_FP8.
  *   strain_H/L  device, FP32, n_samples each; out_prob device, FP32
  *               [n_models][n_windows][window] (caller-owned, as for gwe_forward).
  *   status      device pointer to one int owned by the caller, or NULL.  It is
@@ -202,8 +231,9 @@ gwe_status gwe_sync(gwe_model *model, void *stream);
  *               then invalid).  With NULL the code is written into the array.
  * Limits: window must be a multiple of 128; the number of CTAs is reduced so
  * that their lag rings fit the array (the 30-layer, R = 64 configuration
- * needs 768 KiB per CTA, so at most 32 CTAs run and the call is slower than
- * gwe_forward); a configuration whose single-CTA ring exceeds the array is
+ * needs 768 KiB per CTA in BF16 and 384 KiB in FP8, so at most 32 or 64 CTAs
+ * run and the call is slower than gwe_forward); a configuration whose
+ * single-CTA ring exceeds the array is
  * rejected with GWE_ERR_ARG.
  * The first call on each device looks up the array's device address for that
  * device (cudaGetSymbolAddress) with that device current; make that first call

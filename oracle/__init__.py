@@ -78,6 +78,13 @@ def _load():
         lib.orc_find_peaks.restype = i64
         lib.orc_coincidence.argtypes = [P, P, ctypes.c_int, i64, P]
         lib.orc_coincidence.restype = i64
+        lib.orc_e4m3.argtypes = [ctypes.c_double]
+        lib.orc_e4m3.restype = ctypes.c_double
+        lib.orc_forward_windows_q8.argtypes = [P, P, P, ctypes.c_double, P, P, ctypes.c_int, ctypes.c_int, P,
+                                               ctypes.c_int]
+        lib.orc_forward_windows_q8.restype = None
+        lib.orc_act_amax.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
+        lib.orc_act_amax.restype = None
         _lib = lib
         return lib
 
@@ -125,6 +132,46 @@ def branch_trace(cfg, wblob: np.ndarray, branch: int, s: np.ndarray):
     w = np.ascontiguousarray(wblob, dtype=np.float64)
     lib.orc_branch_trace(_ptr(c), _ptr(w), int(branch), _ptr(s), W, _ptr(xs), _ptr(as_), _ptr(zs), _ptr(sk))
     return xs, as_, zs, sk
+
+
+def e4m3(v) -> np.ndarray:
+    """E4M3 rounding (nearest, ties to even, saturating at +-448) of every element, as FP64."""
+    lib = _load()
+    a = np.asarray(v, dtype=np.float64)
+    return np.vectorize(lambda x: lib.orc_e4m3(float(x)), otypes=[np.float64])(a) if a.size else a.copy()
+
+
+def act_amax(cfg, wblob: np.ndarray, branch: int, s: np.ndarray, nthreads=None) -> np.ndarray:
+    """Calibration of the FP8 reading: max |x_l[i]| [L, R] of one branch over windows s [B, W]."""
+    lib = _load()
+    c = _cfg_arr(cfg)
+    L = int(cfg["stacks"]) * int(cfg["layers_per_stack"])
+    R = int(cfg["r_ch"])
+    s = np.ascontiguousarray(np.atleast_2d(s), dtype=np.float64)
+    B, W = s.shape
+    out = np.zeros((L, R), dtype=np.float64)
+    w = np.ascontiguousarray(wblob, dtype=np.float64)
+    lib.orc_act_amax(_ptr(c), _ptr(w), int(branch), _ptr(s), B, W, _ptr(out), _threads(nthreads))
+    return out
+
+
+def forward_windows_q8(cfg, wblob: np.ndarray, amax: np.ndarray, xh: np.ndarray, xl: np.ndarray,
+                       margin: float = 16.0, nthreads=None) -> np.ndarray:
+    """Logits [B, W] of one model under the FP8 reading (E4M3 convolution operands, scales from
+    amax [2, L, R]); everything else exact."""
+    lib = _load()
+    c = _cfg_arr(cfg)
+    w = np.ascontiguousarray(wblob, dtype=np.float64)
+    a = np.ascontiguousarray(amax, dtype=np.float64)
+    L = int(cfg["stacks"]) * int(cfg["layers_per_stack"])
+    assert a.shape == (2, L, int(cfg["r_ch"]))
+    xh = np.ascontiguousarray(xh, dtype=np.float64)
+    xl = np.ascontiguousarray(xl, dtype=np.float64)
+    B, W = xh.shape
+    out = np.zeros((B, W), dtype=np.float64)
+    lib.orc_forward_windows_q8(_ptr(c), _ptr(w), _ptr(a), float(margin), _ptr(xh), _ptr(xl), B, W, _ptr(out),
+                               _threads(nthreads))
+    return out
 
 
 def n_windows(n: int, window: int, stride: int) -> int:

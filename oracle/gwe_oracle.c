@@ -96,6 +96,61 @@ static double sigm(double x) { return 1.0 / (1.0 + exp(-x)); }
 int64_t orc_param_count(const int *cfg) { ocfg c = ocfg_make(cfg); return c.P; }
 
 /* ---------------------------------------------------------------------------
+ * FP8 reading (for error statements of the reduced-precision path).  The
+ * paper's TensorRT deployment quantises "where appropriate" without saying
+ * how; the library's FP8 path takes this reading, emulated here exactly in
+ * FP64 except for the quantisation itself:
+ *   E4M3: sign, 4 exponent bits (bias 7), 3 mantissa bits, no infinities,
+ *   largest finite value 448, subnormals k * 2^-9.  Conversion rounds to the
+ *   nearest value, ties to the even mantissa, and saturates at +-448.
+ *   Activation scale of input channel i of layer l: s_i = margin * amax_l[i] / 448
+ *   (1 when amax_l[i] is 0), amax_l[i] the calibrated max |x_l[i]|.
+ *   The scales are folded into the weights: W'[o][j][i] = W[o][j][i] s_i, and
+ *   every output row o takes its own scale w_o = max |W'[o][.][.]| / 448 (1 if 0).
+ *   a[t][o] = w_o * sum_{j,i} e4m3(W'[o][j][i] / w_o) e4m3(x[t - lag_j][i] / s_i) + b[o].
+ * ------------------------------------------------------------------------- */
+double orc_e4m3(double v) {
+    if (v != v) return v;
+    double a = fabs(v);
+    if (a >= 448.0) return v < 0 ? -448.0 : 448.0;
+    if (a == 0.0) return v;
+    int ex;
+    frexp(a, &ex);                   /* a = m 2^ex, m in [0.5, 1): binade [2^(ex-1), 2^ex) */
+    int e = ex - 1;
+    if (e < -6) e = -6;              /* subnormal range shares the spacing of the lowest binade */
+    double q = ldexp(1.0, e - 3);    /* spacing: 3 mantissa bits */
+    double n = nearbyint(a / q);     /* a / q is exact (power-of-two divisor); ties to even */
+    double r = n * q;
+    if (r > 448.0) r = 448.0;
+    return v < 0 ? -r : r;
+}
+
+/* e4m3 operands of one layer: q_x [W][R] = e4m3(x / s), q_w [2R][k][R], w_o [2R] */
+static void quant_layer(const ocfg *c, const double *w_conv, const double *x, int W, const double *amax,
+                        double margin, double *qx, double *qw, double *wo) {
+    const int R = c->R, K = c->k;
+    double *sc = (double *)malloc(sizeof(double) * R);
+    for (int i = 0; i < R; i++) sc[i] = amax[i] > 0 ? margin * amax[i] / 448.0 : 1.0;
+    for (int t = 0; t < W; t++)
+        for (int i = 0; i < R; i++) qx[(int64_t)t * R + i] = orc_e4m3(x[(int64_t)t * R + i] / sc[i]);
+    for (int o = 0; o < 2 * R; o++) {
+        double mx = 0.0;
+        for (int j = 0; j < K; j++)
+            for (int i = 0; i < R; i++) {
+                double v = fabs(w_conv[((int64_t)o * K + j) * R + i] * sc[i]);
+                if (v > mx) mx = v;
+            }
+        wo[o] = mx > 0 ? mx / 448.0 : 1.0;
+        for (int j = 0; j < K; j++)
+            for (int i = 0; i < R; i++) {
+                int64_t k = ((int64_t)o * K + j) * R + i;
+                qw[k] = orc_e4m3(w_conv[k] * sc[i] / wo[o]);
+            }
+    }
+    free(sc);
+}
+
+/* ---------------------------------------------------------------------------
  * One branch over one window of W samples.  Optional traces:
  *   xs [L+1][W][R]  residual-stream inputs of every layer (xs[L] = final)
  *   as [L][W][2R]   pre-activations
@@ -103,12 +158,16 @@ int64_t orc_param_count(const int *cfg) { ocfg c = ocfg_make(cfg); return c.P; }
  * skip [W][S] receives the skip sum.
  * ------------------------------------------------------------------------- */
 static void branch_fwd(const ocfg *c, const double *wb, const double *s, int W,
-                       double *skip, double *xs, double *as, double *zs) {
+                       double *skip, double *xs, double *as, double *zs, const double *amax, double margin) {
+    /* amax: NULL for exact arithmetic, else [L][R] and the convolutions take the FP8 reading */
     const int R = c->R, S = c->S, K = c->k, L = c->L;
     double *x = (double *)malloc(sizeof(double) * W * R);
     double *xn = (double *)malloc(sizeof(double) * W * R);
     double *a = (double *)malloc(sizeof(double) * W * 2 * R);
     double *z = (double *)malloc(sizeof(double) * W * R);
+    double *qx = amax ? (double *)malloc(sizeof(double) * W * R) : NULL;
+    double *qw = amax ? (double *)malloc(sizeof(double) * 2 * R * K * R) : NULL;
+    double *wo = amax ? (double *)malloc(sizeof(double) * 2 * R) : NULL;
     const double *w_in = wb, *b_in = wb + R;
     for (int t = 0; t < W; t++)
         for (int ch = 0; ch < R; ch++) x[t * R + ch] = w_in[ch] * s[t] + b_in[ch];
@@ -118,17 +177,34 @@ static void branch_fwd(const ocfg *c, const double *wb, const double *s, int W,
         int d = dil(c, l);
         if (xs) memcpy(xs + (int64_t)l * W * R, x, sizeof(double) * W * R);
         /* dilated causal convolution, direct sum */
-        for (int t = 0; t < W; t++) {
-            for (int o = 0; o < 2 * R; o++) {
-                double acc = p.b_conv[o];
-                for (int j = 0; j < K; j++) {
-                    int tt = t - (K - 1 - j) * d;
-                    if (tt < 0) continue;
-                    const double *wr = p.w_conv + ((int64_t)o * K + j) * R;
-                    const double *xr = x + (int64_t)tt * R;
-                    for (int i = 0; i < R; i++) acc += wr[i] * xr[i];
+        if (amax) {
+            quant_layer(c, p.w_conv, x, W, amax + (int64_t)l * R, margin, qx, qw, wo);
+            for (int t = 0; t < W; t++) {
+                for (int o = 0; o < 2 * R; o++) {
+                    double acc = 0.0;
+                    for (int j = 0; j < K; j++) {
+                        int tt = t - (K - 1 - j) * d;
+                        if (tt < 0) continue;
+                        const double *wr = qw + ((int64_t)o * K + j) * R;
+                        const double *xr = qx + (int64_t)tt * R;
+                        for (int i = 0; i < R; i++) acc += wr[i] * xr[i];
+                    }
+                    a[(int64_t)t * 2 * R + o] = wo[o] * acc + p.b_conv[o];
                 }
-                a[(int64_t)t * 2 * R + o] = acc;
+            }
+        } else {
+            for (int t = 0; t < W; t++) {
+                for (int o = 0; o < 2 * R; o++) {
+                    double acc = p.b_conv[o];
+                    for (int j = 0; j < K; j++) {
+                        int tt = t - (K - 1 - j) * d;
+                        if (tt < 0) continue;
+                        const double *wr = p.w_conv + ((int64_t)o * K + j) * R;
+                        const double *xr = x + (int64_t)tt * R;
+                        for (int i = 0; i < R; i++) acc += wr[i] * xr[i];
+                    }
+                    a[(int64_t)t * 2 * R + o] = acc;
+                }
             }
         }
         if (as) memcpy(as + (int64_t)l * W * 2 * R, a, sizeof(double) * W * 2 * R);
@@ -156,7 +232,7 @@ static void branch_fwd(const ocfg *c, const double *wb, const double *s, int W,
         double *tmp = x; x = xn; xn = tmp;
     }
     if (xs) memcpy(xs + (int64_t)L * W * R, x, sizeof(double) * W * R);
-    free(x); free(xn); free(a); free(z);
+    free(x); free(xn); free(a); free(z); free(qx); free(qw); free(wo);
 }
 
 /* head over W samples: u_pre [W][Hc] optional trace, logit [W] */
@@ -205,8 +281,8 @@ void orc_forward_windows(const int *cfg, const double *wblob, const double *xh, 
     for (int b = 0; b < B; b++) {
         double *skH = (double *)malloc(sizeof(double) * W * c.S);
         double *skL = (double *)malloc(sizeof(double) * W * c.S);
-        branch_fwd(&c, branch_base(&c, w, 0), xh + (int64_t)b * W, W, skH, NULL, NULL, NULL);
-        branch_fwd(&c, branch_base(&c, w, 1), xl + (int64_t)b * W, W, skL, NULL, NULL, NULL);
+        branch_fwd(&c, branch_base(&c, w, 0), xh + (int64_t)b * W, W, skH, NULL, NULL, NULL, NULL, 0.0);
+        branch_fwd(&c, branch_base(&c, w, 1), xl + (int64_t)b * W, W, skL, NULL, NULL, NULL, NULL, 0.0);
         head_fwd(&c, w, skH, skL, W, logit + (int64_t)b * W, NULL);
         free(skH); free(skL);
     }
@@ -218,7 +294,67 @@ void orc_branch_trace(const int *cfg, const double *wblob, int branch, const dou
                       double *xs, double *as, double *zs, double *skip) {
     ocfg c = ocfg_make(cfg);
     double *w = to_double(wblob, c.P);
-    branch_fwd(&c, branch_base(&c, w, branch), s, W, skip, xs, as, zs);
+    branch_fwd(&c, branch_base(&c, w, branch), s, W, skip, xs, as, zs, NULL, 0.0);
+    free(w);
+}
+
+/* ---------------------------------------------------------------------------
+ * FP8 reading: forward of one model over B explicit windows with E4M3
+ * convolution operands (see orc_e4m3); amax [2][L][R] per branch, layer and
+ * input channel; logits out.
+ * ------------------------------------------------------------------------- */
+void orc_forward_windows_q8(const int *cfg, const double *wblob, const double *amax, double margin,
+                            const double *xh, const double *xl, int B, int W, double *logit, int nthreads) {
+    ocfg c = ocfg_make(cfg);
+    double *w = to_double(wblob, c.P);
+    const int64_t ab = (int64_t)c.L * c.R;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int b = 0; b < B; b++) {
+        double *skH = (double *)malloc(sizeof(double) * W * c.S);
+        double *skL = (double *)malloc(sizeof(double) * W * c.S);
+        branch_fwd(&c, branch_base(&c, w, 0), xh + (int64_t)b * W, W, skH, NULL, NULL, NULL, amax, margin);
+        branch_fwd(&c, branch_base(&c, w, 1), xl + (int64_t)b * W, W, skL, NULL, NULL, NULL, amax + ab, margin);
+        head_fwd(&c, w, skH, skL, W, logit + (int64_t)b * W, NULL);
+        free(skH); free(skL);
+    }
+    free(w);
+}
+
+/* Calibration for the FP8 reading: amax [L][R] = max over the B windows s [B][W] and time of
+ * |x_l[t][i]|, the input of layer l of branch `branch` (exact arithmetic). */
+void orc_act_amax(const int *cfg, const double *wblob, int branch, const double *s, int B, int W, double *amax,
+                  int nthreads) {
+    ocfg c = ocfg_make(cfg);
+    double *w = to_double(wblob, c.P);
+    const int64_t per = (int64_t)(c.L + 1) * W * c.R;
+    double *part = (double *)calloc((size_t)B * c.L * c.R, sizeof(double));
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int b = 0; b < B; b++) {
+        double *xs = (double *)malloc(sizeof(double) * per);
+        double *sk = (double *)malloc(sizeof(double) * W * c.S);
+        branch_fwd(&c, branch_base(&c, w, branch), s + (int64_t)b * W, W, sk, xs, NULL, NULL, NULL, 0.0);
+        double *pb = part + (int64_t)b * c.L * c.R;
+        for (int l = 0; l < c.L; l++)
+            for (int t = 0; t < W; t++)
+                for (int i = 0; i < c.R; i++) {
+                    double v = fabs(xs[((int64_t)l * W + t) * c.R + i]);
+                    if (v > pb[l * c.R + i]) pb[l * c.R + i] = v;
+                }
+        free(xs); free(sk);
+    }
+    for (int k = 0; k < c.L * c.R; k++) {
+        double m = 0.0;
+        for (int b = 0; b < B; b++)
+            if (part[(int64_t)b * c.L * c.R + k] > m) m = part[(int64_t)b * c.L * c.R + k];
+        amax[k] = m;
+    }
+    free(part);
     free(w);
 }
 
@@ -267,8 +403,8 @@ void orc_forward_stream(const int *cfg, const double *wblobs, const float *sH, c
         double *skH = (double *)malloc(sizeof(double) * W * c.S);
         double *skL = (double *)malloc(sizeof(double) * W * c.S);
         double *lg = (double *)malloc(sizeof(double) * W);
-        branch_fwd(&c, branch_base(&c, wm, 0), xh, W, skH, NULL, NULL, NULL);
-        branch_fwd(&c, branch_base(&c, wm, 1), xl, W, skL, NULL, NULL, NULL);
+        branch_fwd(&c, branch_base(&c, wm, 0), xh, W, skH, NULL, NULL, NULL, NULL, 0.0);
+        branch_fwd(&c, branch_base(&c, wm, 1), xl, W, skL, NULL, NULL, NULL, NULL, 0.0);
         head_fwd(&c, wm, skH, skL, W, lg, NULL);
         double *out = prob + (((int64_t)si * c.n_models + m) * nw + wi) * W;
         for (int t = 0; t < W; t++) out[t] = sigm(lg[t]);
@@ -376,7 +512,7 @@ static void window_bwd(const ocfg *c, const double *w, const double *xh, const d
         zs[b] = (double *)malloc(sizeof(double) * (size_t)L * W * R);
         sk[b] = (double *)malloc(sizeof(double) * (size_t)W * S);
         dsk[b] = (double *)calloc((size_t)W * S, sizeof(double));
-        branch_fwd(c, branch_base(c, w, b), in[b], W, sk[b], xs[b], as[b], zs[b]);
+        branch_fwd(c, branch_base(c, w, b), in[b], W, sk[b], xs[b], as[b], zs[b], NULL, 0.0);
     }
     double *lg = (double *)malloc(sizeof(double) * W);
     double *upre = (double *)malloc(sizeof(double) * (size_t)W * Hc);

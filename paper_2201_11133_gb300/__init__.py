@@ -19,7 +19,8 @@ from . import _build
 
 __all__ = [
     "GWE_FP32", "GWE_BF16", "GWE_FP8", "GweError", "load", "build",
-    "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_destroy",
+    "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_calibrate", "gwe_model_set_fp8_amax", "gwe_model_get_fp8_amax",
+    "gwe_model_destroy",
     "gwe_forward", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
     "gwe_version", "gwe_sync", "gwe_forward_static", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
@@ -76,6 +77,9 @@ def load():
             "gwe_n_windows": (I64, [I64, I, I]),
             "gwe_model_create": (I, [P, P, I, P]),
             "gwe_model_set_weights": (I, [P, P]),
+            "gwe_model_calibrate": (I, [P, P, P, I64, I, I, P]),
+            "gwe_model_set_fp8_amax": (I, [P, P]),
+            "gwe_model_get_fp8_amax": (I, [P, P]),
             "gwe_model_destroy": (None, [P]),
             "gwe_forward": (I, [P, P, P, I64, I, I, P, I, P, P]),
             "gwe_forward_logits": (I, [P, P, P, I, I, P, P]),
@@ -162,6 +166,26 @@ def gwe_model_create(cfg, host_weights: np.ndarray, precision: int = GWE_FP32) -
 def gwe_model_set_weights(model: int, host_weights: np.ndarray) -> None:
     w = np.ascontiguousarray(host_weights, dtype=np.float32)
     _check(load().gwe_model_set_weights(model, w.ctypes.data), "gwe_model_set_weights")
+
+
+def gwe_model_calibrate(model: int, strain_H, strain_L, n_samples: int, window: int, stride: int,
+                        stream=None) -> None:
+    """FP8 activation scales from the FP32 forward over one segment of (device) whitened strain."""
+    _check(load().gwe_model_calibrate(model, _dptr(strain_H), _dptr(strain_L), int(n_samples), int(window),
+                                      int(stride), _stream(stream)), "gwe_model_calibrate")
+
+
+def gwe_model_set_fp8_amax(model: int, amax: np.ndarray) -> None:
+    """Set the FP8 calibration maxima, host [n_models, 2, L, R]; rebuilds the E4M3 weights."""
+    a = np.ascontiguousarray(amax, dtype=np.float32)
+    _check(load().gwe_model_set_fp8_amax(model, a.ctypes.data), "gwe_model_set_fp8_amax")
+
+
+def gwe_model_get_fp8_amax(model: int, shape) -> np.ndarray:
+    """The FP8 calibration maxima as float32 [n_models, 2, L, R] (`shape`)."""
+    out = np.zeros(shape, dtype=np.float32)
+    _check(load().gwe_model_get_fp8_amax(model, out.ctypes.data), "gwe_model_get_fp8_amax")
+    return out
 
 
 def gwe_model_destroy(model: int) -> None:
@@ -285,6 +309,24 @@ class Model:
 
     def sync(self, stream=None):
         gwe_sync(self.handle, stream)
+
+    def calibrate(self, strain_H, strain_L, window: int, stride: int, stream=None):
+        gwe_model_calibrate(self.handle, strain_H, strain_L, int(strain_H.shape[0]), window, stride, stream)
+
+    def _amax_shape(self):
+        c = self.cfg
+        return (int(c["n_models"]), 2, int(c["stacks"]) * int(c["layers_per_stack"]), int(c["r_ch"]))
+
+    @property
+    def fp8_amax(self) -> np.ndarray:
+        return gwe_model_get_fp8_amax(self.handle, self._amax_shape())
+
+    @fp8_amax.setter
+    def fp8_amax(self, amax) -> None:
+        a = np.asarray(amax, dtype=np.float32)
+        if a.shape != self._amax_shape():
+            raise ValueError(f"amax must have shape {self._amax_shape()}")
+        gwe_model_set_fp8_amax(self.handle, a)
 
     def logits(self, x_H, x_L, out=None, stream=None):
         import torch

@@ -2,6 +2,8 @@
 // model handles and dispatch to the precision-specific paths.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <cstring>
 #include <new>
 #include <string>
@@ -136,19 +138,54 @@ gwe_status gwe_model_set_weights(gwe_model *m, const float *hb) {
     GWE_CUDA_TRY(cudaMemcpy(m->w32.ptr, hb, bytes, cudaMemcpyHostToDevice));
     gwe_status st = fp32_prepare(m, hb);
     if (st != GWE_OK && m->precision == GWE_FP32) return st;
-    if (m->precision == GWE_BF16) {
-        st = bf16_prepare(m, hb);
+    if (m->precision == GWE_BF16 || m->precision == GWE_FP8) {
+        if (st != GWE_OK) return st;   // the FP8 calibration runs on the FP32 path
+        st = tc_prepare(m, hb, m->precision == GWE_FP8);
         if (st != GWE_OK) return st;
-    } else if (m->precision == GWE_FP8) {
-        set_error("FP8 path not built yet");
-        return GWE_ERR_UNSUPPORTED;
     }
     return GWE_OK;
 }
 
+gwe_status gwe_model_calibrate(gwe_model *m, const float *sH, const float *sL, int64_t n, int window, int stride,
+                               void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    GWE_ARG_CHECK(sH != nullptr && sL != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(window > 0 && stride > 0 && stride <= window, "bad window/stride");
+    GWE_ARG_CHECK(n >= window, "n_samples < window");
+    if (m->precision != GWE_FP8) {
+        set_error("gwe_model_calibrate: only FP8 handles take activation scales");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    return tc_calibrate(m, sH, sL, n, window, stride, as_stream(stream));
+}
+
+gwe_status gwe_model_set_fp8_amax(gwe_model *m, const float *amax) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr && amax != nullptr, "NULL argument");
+    if (m->precision != GWE_FP8) {
+        set_error("gwe_model_set_fp8_amax: not an FP8 handle");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    const int64_t n = (int64_t)m->dims.n_models * 2 * m->dims.L * m->dims.R;
+    for (int64_t i = 0; i < n; ++i)
+        GWE_ARG_CHECK(std::isfinite(amax[i]) && amax[i] >= 0.f, "amax entries must be finite and >= 0");
+    return tc_set_amax(m, amax);
+}
+
+gwe_status gwe_model_get_fp8_amax(gwe_model *m, float *amax) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr && amax != nullptr, "NULL argument");
+    if (m->precision != GWE_FP8) {
+        set_error("gwe_model_get_fp8_amax: not an FP8 handle");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    return tc_get_amax(m, amax);
+}
+
 void gwe_model_destroy(gwe_model *m) {
     if (!m) return;
-    bf16_release(m);
+    tc_release(m);
     fp32_backward_release(m);
     m->w32.release();
     m->f32.buf.release();
@@ -165,7 +202,7 @@ static gwe_status dispatch_forward(gwe_model *m, const float *sH, const float *s
                                    int64_t nw, const int32_t *slides, int n_slides, float *out, bool logits,
                                    cudaStream_t st) {
     if (m->precision == GWE_FP32) return fp32_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out, logits, st);
-    return bf16_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out, logits, st);
+    return tc_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out, logits, st);
 }
 
 gwe_status gwe_forward(gwe_model *m, const float *sH, const float *sL, int64_t n, int window, int stride,
@@ -221,7 +258,7 @@ gwe_status gwe_sync(gwe_model *m, void *stream) {
     cudaStream_t st = as_stream(stream);
     GWE_CUDA_TRY(cudaStreamSynchronize(st));
     GWE_CUDA_TRY(cudaGetLastError());
-    if (m->precision == GWE_BF16) return bf16_check(m, st);
+    if (m->precision != GWE_FP32) return tc_check(m, st);
     return GWE_OK;
 }
 

@@ -36,6 +36,7 @@
 // site in an error word, lets every role leave its loops and frees TMEM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,23 +65,31 @@ constexpr uint32_t pow2ceil(uint32_t x) {
 }
 constexpr uint32_t cmax(uint32_t a, uint32_t b) { return a > b ? a : b; }
 
-template <int R, int S, int HC>
+// F8 = false: conv operands BF16.  F8 = true: conv operands FP8 E4M3 (the residual stream's copy
+// scaled per input channel, the weights per output channel); everything after the conv as for BF16.
+template <int R, int S, int HC, bool F8 = false>
 struct TcShape {
+    static constexpr int XB = F8 ? 1 : 2;         // bytes per conv-operand element
+    static constexpr int XROW = R * XB;           // bytes of one row of x (lag ring row)
     static constexpr int N1 = 2 * R;              // conv outputs: f then g
-    static constexpr int RC = R / 8;              // 16-byte chunks of an R-wide row
+    static constexpr int RC = R * XB / 16;        // 16-byte chunks of one row of x
+    static constexpr int KR = R / 16;             // K steps of the residual/skip MMAs (FP16 z)
     static constexpr int NH = HC <= 128 ? 1 : 2;  // head output pieces
     static constexpr int HP = HC / NH;
     static constexpr int HQ = S / 2;              // K width of one head weight piece
     static constexpr int NHP = 4 * NH;            // head weight pieces: (nh, K quarter)
     static constexpr uint32_t STAGE_ROWS = 256;
     static constexpr uint32_t STAGE_LBO = STAGE_ROWS * 16;
-    static constexpr uint32_t STAGE_BYTES = STAGE_LBO * RC;
-    static constexpr uint32_t CONV_BYTES = N1 * 2 * R * 2;
+    static constexpr uint32_t STAGE_BYTES = cmax(STAGE_LBO * RC, 256 * S);   // x rows, or the head operand
+    static constexpr uint32_t CONV_BYTES = N1 * 2 * R * XB;
     static constexpr uint32_t RES_BYTES = R * R * 2;
     static constexpr uint32_t SKIP_BYTES = S * R * 2;
     static constexpr uint32_t RS_BYTES = RES_BYTES + SKIP_BYTES;
     static constexpr uint32_t HEADP_BYTES = HP * HQ * 2;
-    static constexpr uint32_t BIAS_BYTES = 4 * R;   // b_conv as FP16 [2R] or b_res as FP32 [R]
+    // per-layer bias slots: conv = FP16 b_conv [2R] (BF16) or FP32 {scale, bias} [2R] (FP8);
+    // res = FP32 b_res [R] (+ FP8: the next layer's input quantisation factors [R])
+    static constexpr uint32_t CB_BYTES = F8 ? 16 * R : 4 * R;
+    static constexpr uint32_t RB_BYTES = F8 ? 8 * R : 4 * R;
     static constexpr uint32_t ECONV = cmax(CONV_BYTES, HEADP_BYTES);
     static constexpr uint32_t ERS = cmax(RS_BYTES, HEADP_BYTES);
     static constexpr uint32_t TMEM_BR = 2 * R + S;
@@ -90,17 +99,18 @@ struct TcShape {
     static constexpr uint32_t OFF_STAGE = 0;
     static constexpr uint32_t OFF_ENT = 2 * STAGE_BYTES;               // [branch]{conv entry, rs entry}
     static constexpr uint32_t ENT_BR = ECONV + ERS;
-    static constexpr uint32_t OFF_BIAS = OFF_ENT + 2 * ENT_BR;         // [branch]{b_conv[2 slots], b_res[2 slots]}
-    static constexpr uint32_t BIAS_BR = 4 * BIAS_BYTES;
+    static constexpr uint32_t OFF_BIAS = OFF_ENT + 2 * ENT_BR;         // [branch]{conv slots x2, res slots x2}
+    static constexpr uint32_t BIAS_BR = 2 * CB_BYTES + 2 * RB_BYTES;
     static constexpr uint32_t OFF_PART = OFF_BIAS + 2 * BIAS_BR;
     static constexpr uint32_t OFF_BAR = OFF_PART + 4 * kTile * 4;
     static constexpr uint32_t N_BAR = 40;
     static constexpr uint32_t OFF_MISC = OFF_BAR + N_BAR * 8;
     static constexpr uint32_t SMEM = OFF_MISC + 64 + 128;    // + alignment slack
-    // per-branch parameter block (bytes): w_in[R], b_in[R], bskip_sum[S] (FP32), then per layer
-    // b_conv as FP16 [2R] (g half pre-halved) and b_res FP32 [R]
-    static constexpr uint32_t PL_BYTES = 2 * BIAS_BYTES;
-    static __host__ __device__ constexpr uint32_t pb_bytes(int L) { return 8 * R + 4 * S + L * PL_BYTES; }
+    // per-branch parameter block (bytes): w_in[R], b_in[R], bskip_sum[S] (FP32), FP8: the input
+    // projection's quantisation factors [R]; then per layer the conv slot and the res slot
+    static constexpr uint32_t HDR_BYTES = 8 * R + 4 * S + (F8 ? 4 * R : 0);
+    static constexpr uint32_t PL_BYTES = CB_BYTES + RB_BYTES;
+    static __host__ __device__ constexpr uint32_t pb_bytes(int L) { return HDR_BYTES + L * PL_BYTES; }
     static __host__ __device__ constexpr uint32_t ph_bytes() { return ((8 * HC + 4) + 15) & ~15u; }
     static __host__ __device__ constexpr uint32_t pm_bytes(int L) { return 2 * pb_bytes(L) + ph_bytes(); }
     // per-model weight image: per layer [conv H][conv L][rs H][rs L], then the head pieces
@@ -108,10 +118,9 @@ struct TcShape {
     static __host__ __device__ constexpr uint64_t img_bytes(int L) {
         return (uint64_t)L * LAYER_IMG + (uint64_t)NHP * HEADP_BYTES;
     }
-    static_assert(R % 16 == 0 && S % 32 == 0 && HP % 16 == 0, "channel counts");
+    static_assert(R % 32 == 0 && S % 32 == 0 && HP % 16 == 0, "channel counts");
     static_assert(N1 <= 256 && S <= 256 && HP <= 256, "MMA N limit");
     static_assert(HP <= 2 * R, "head piece must fit the conv TMEM columns");
-    static_assert(256 * S <= STAGE_BYTES, "head operand must fit one staging buffer");
     static_assert(TMEM_COLS <= 512, "TMEM");
     static_assert(OFF_MISC + 64 + 128 <= 232448, "shared memory per block");
 };
@@ -220,9 +229,9 @@ __device__ __forceinline__ Job decode_job(const TcParams &p, int64_t j) {
     return q;
 }
 
-template <int R, int S, int HC>
+template <int R, int S, int HC, bool F8>
 __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
-    using Sh = TcShape<R, S, HC>;
+    using Sh = TcShape<R, S, HC, F8>;
     constexpr int RH = R / 2;          // channels per epilogue thread (half of a row)
     constexpr int SH = S / 2;
     constexpr int HPH = Sh::HP / 2;
@@ -284,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 uint32_t it[2] = {0, 0};       // items issued per entry
                 uint32_t lag_issued = 0, ph_h = 0, g = 0, g_conv = 0, g_res = 0;
                 bool ok = true, first = true;
-                uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * (2 * R);
+                uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * Sh::XROW;
                 auto take = [&](int e, int site) -> bool {
                     return mbar_wait(&bar[B_WEMPTY + 2 * b + e], ((it[e] & 1) ^ 1), abort_flag, p.err, site, p.wait_ns);
                 };
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     const uint32_t bytes = (uint32_t)n * 16;
                     mbar_arrive_expect_tx(&bar[B_LAG + b], bytes * Sh::RC);
                     const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
-                    const uint8_t *src = ring_b + roff * (2 * R) + (uint64_t)(t0 & (d - 1)) * 16;
+                    const uint8_t *src = ring_b + roff * Sh::XROW + (uint64_t)(t0 & (d - 1)) * 16;
                     uint8_t *dst0 = smem + Sh::OFF_STAGE + b * Sh::STAGE_BYTES + (kTile - n) * 16;
 #pragma unroll
                     for (int c = 0; c < Sh::RC; ++c)
@@ -307,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
                     const Job q = decode_job(p, j);
                     const uint8_t *wm = p.wimg + (uint64_t)q.m * p.wimg_stride;
-                    const uint8_t *play = p.pblob + (uint64_t)q.m * p.pblob_stride + b * Sh::pb_bytes(L) + 8 * R + 4 * S;
+                    const uint8_t *play = p.pblob + (uint64_t)q.m * p.pblob_stride + b * Sh::pb_bytes(L) + Sh::HDR_BYTES;
                     for (int tt = 0; tt < NT && ok; ++tt) {
                         for (int l = 0; l < L; ++l, ++g) {
                             // conv entry: free once the previous conv (or head piece) MMA completed
@@ -318,9 +327,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                                      &bar[B_WFULL + 2 * b + 0]);
                             // b_conv of this layer into slot g & 1 (its previous reader, the gate two
                             // layers back, finished before the conv that just freed the entry)
-                            mbar_arrive_expect_tx(&bar[B_BIAS + 4 * b + (g & 1)], Sh::BIAS_BYTES);
-                            bulk_g2s(smem + Sh::OFF_BIAS + b * Sh::BIAS_BR + (g & 1) * Sh::BIAS_BYTES,
-                                     play + (uint64_t)l * Sh::PL_BYTES, Sh::BIAS_BYTES, &bar[B_BIAS + 4 * b + (g & 1)]);
+                            mbar_arrive_expect_tx(&bar[B_BIAS + 4 * b + (g & 1)], Sh::CB_BYTES);
+                            bulk_g2s(smem + Sh::OFF_BIAS + b * Sh::BIAS_BR + (g & 1) * Sh::CB_BYTES,
+                                     play + (uint64_t)l * Sh::PL_BYTES, Sh::CB_BYTES, &bar[B_BIAS + 4 * b + (g & 1)]);
                             g_conv = g + 1;
                             ++it[0];
                             // lagged rows: the staging buffer is free once the previous conv completed
@@ -341,9 +350,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             bulk_g2s(smem + Sh::OFF_ENT + b * Sh::ENT_BR + Sh::ECONV,
                                      wm + (uint64_t)l * Sh::LAYER_IMG + 2ull * Sh::CONV_BYTES + (uint64_t)b * Sh::RS_BYTES,
                                      Sh::RS_BYTES, &bar[B_WFULL + 2 * b + 1]);
-                            mbar_arrive_expect_tx(&bar[B_BIAS + 4 * b + 2 + (g & 1)], Sh::BIAS_BYTES);
-                            bulk_g2s(smem + Sh::OFF_BIAS + b * Sh::BIAS_BR + (2 + (g & 1)) * Sh::BIAS_BYTES,
-                                     play + (uint64_t)l * Sh::PL_BYTES + Sh::BIAS_BYTES, Sh::BIAS_BYTES,
+                            mbar_arrive_expect_tx(&bar[B_BIAS + 4 * b + 2 + (g & 1)], Sh::RB_BYTES);
+                            bulk_g2s(smem + Sh::OFF_BIAS + b * Sh::BIAS_BR + 2 * Sh::CB_BYTES + (g & 1) * Sh::RB_BYTES,
+                                     play + (uint64_t)l * Sh::PL_BYTES + Sh::CB_BYTES, Sh::RB_BYTES,
                                      &bar[B_BIAS + 4 * b + 2 + (g & 1)]);
                             g_res = g + 1;
                             ++it[1];
@@ -378,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
         } else {
             // -------------------------------------------------------- MMA issuer of branch b (+ head on branch 0)
             if (lane == 0) {
-                constexpr uint32_t ID_CONV = idesc_f16(128, Sh::N1, 1);
+                constexpr uint32_t ID_CONV = F8 ? idesc_e4m3(128, Sh::N1) : idesc_f16(128, Sh::N1, 1);
                 constexpr uint32_t ID_RES = idesc_f16(128, R, 0);
                 constexpr uint32_t ID_SKIP = idesc_f16(128, S, 0);
                 constexpr uint32_t ID_HEAD = idesc_f16(128, Sh::HP, 0);
@@ -415,13 +424,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             tc_fence_after();
                             // K = 2R in steps of 16: the lagged rows (staging rows 128 - n ..), then the current ones
                             const uint64_t a_lag = a_lag0 + (uint64_t)(kTile - n);
-                            mma_f16(dcol, a_lag, b_conv0, ID_CONV, 0u);
+                            auto conv_mma = [&](uint64_t ad, uint64_t bd, uint32_t acc) {
+                                if constexpr (F8)
+                                    mma_f8(dcol, ad, bd, ID_CONV, acc);
+                                else
+                                    mma_f16(dcol, ad, bd, ID_CONV, acc);
+                            };
+                            conv_mma(a_lag, b_conv0, 0u);
 #pragma unroll
                             for (int ks = 1; ks < Sh::RC / 2; ++ks)
-                                mma_f16(dcol, a_lag + ks * A_STEP, b_conv0 + ks * (2 * Sh::N1), ID_CONV, 1u);
+                                conv_mma(a_lag + ks * A_STEP, b_conv0 + ks * (2 * Sh::N1), 1u);
 #pragma unroll
                             for (int ks = Sh::RC / 2; ks < Sh::RC; ++ks)
-                                mma_f16(dcol, a_cur0 + (ks - Sh::RC / 2) * A_STEP, b_conv0 + ks * (2 * Sh::N1), ID_CONV, 1u);
+                                conv_mma(a_cur0 + (ks - Sh::RC / 2) * A_STEP, b_conv0 + ks * (2 * Sh::N1), 1u);
                             mma_commit(&bar[B_CONV + b]);
                             mma_commit(&bar[B_WEMPTY + 2 * b]);
                             ++it[0];
@@ -434,11 +449,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             // z (FP16, two per column) sits in the f columns: channels [16ks, 16ks+16)
                             // at column zcol(ks); r goes to the g columns, s accumulates after them
 #pragma unroll
-                            for (int ks = 0; ks < Sh::RC / 2; ++ks)
+                            for (int ks = 0; ks < Sh::KR; ++ks)
                                 mma_f16_ta(dcol + R, dcol + zcol(ks), b_res0 + ks * (2 * R), ID_RES, ks > 0 ? 1u : 0u);
                             mma_f16_ta(dcol + 2 * R, dcol + zcol(0), b_skip0, ID_SKIP, l > 0 ? 1u : 0u);
 #pragma unroll
-                            for (int ks = 1; ks < Sh::RC / 2; ++ks)
+                            for (int ks = 1; ks < Sh::KR; ++ks)
                                 mma_f16_ta(dcol + 2 * R, dcol + zcol(ks), b_skip0 + ks * (2 * S), ID_SKIP, 1u);
                             mma_commit(&bar[B_RS + b]);
                             mma_commit(&bar[B_WEMPTY + 2 * b + 1]);
@@ -491,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
         const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
         const uint32_t sb = s_bias + b * Sh::BIAS_BR;
         const int c0 = hf * RH;                        // first channel of this thread
-        uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * (2 * R);
+        uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * Sh::XROW;
         uint32_t ph_conv = 0, ph_rs = 0, ph_head = 0, ph_wg = 0, ph_pair = 0, tiles = 0;
         bool ok = true;
         float x[RH];
@@ -505,19 +520,62 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[idx]);
         };
-        auto store_x = [&]() {
+        // x (FP32 registers) -> this thread's chunks of the staging row: BF16, or FP8 E4M3 after
+        // multiplying by the next layer's per-channel quantisation factors `inv` (FP32)
+        auto store_x = [&](const float *inv_g, uint32_t inv_s) {
+            if constexpr (F8) {
 #pragma unroll
-            for (int c = 0; c < RH / 8; ++c) {
-                uint4 v;
-                v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
-                v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
-                v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
-                v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
-                sts128(st + (hf * (RH / 8) + c) * Sh::STAGE_LBO + (kTile + r) * 16, v);
+                for (int c = 0; c < RH / 16; ++c) {
+                    uint32_t wv[4];
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        float4 iv;
+                        if (inv_g)
+                            iv = __ldg(reinterpret_cast<const float4 *>(inv_g) + 4 * c + k4);
+                        else {
+                            const uint4 u = lds128(inv_s + (16 * c + 4 * k4) * 4);
+                            iv = make_float4(__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z),
+                                             __uint_as_float(u.w));
+                        }
+                        const int o = 16 * c + 4 * k4;
+                        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(x[o] * iv.x, x[o + 1] * iv.y),
+                                                                     __NV_SATFINITE, __NV_E4M3);
+                        const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(x[o + 2] * iv.z, x[o + 3] * iv.w),
+                                                                     __NV_SATFINITE, __NV_E4M3);
+                        wv[k4] = lo | (hi << 16);
+                    }
+                    sts128(st + (hf * (RH / 16) + c) * Sh::STAGE_LBO + (kTile + r) * 16,
+                           make_uint4(wv[0], wv[1], wv[2], wv[3]));
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < RH / 8; ++c) {
+                    uint4 v;
+                    v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
+                    v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
+                    v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
+                    v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+                    sts128(st + (hf * (RH / 8) + c) * Sh::STAGE_LBO + (kTile + r) * 16, v);
+                }
             }
         };
         // z for 16 channels starting at ch from the f / g accumulator columns
         auto gate16 = [&](const uint32_t (&fr)[16], const uint32_t (&gr)[16], int ch, uint32_t bslot, uint32_t (&zz)[8]) {
+            if constexpr (F8) {
+                // a = acc * scale + bias per output channel (FP32 {scale, bias} pairs), then as below
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const uint4 sf = lds128(bslot + (ch + 2 * jj) * 8);          // {s, b} of f channels 2jj, 2jj+1
+                    const uint4 sg4 = lds128(bslot + (R + ch + 2 * jj) * 8);     // same for g
+                    const float f0 = fmaf(__uint_as_float(fr[2 * jj]), __uint_as_float(sf.x), __uint_as_float(sf.y));
+                    const float f1 = fmaf(__uint_as_float(fr[2 * jj + 1]), __uint_as_float(sf.z), __uint_as_float(sf.w));
+                    const float g0 = fmaf(__uint_as_float(gr[2 * jj]), __uint_as_float(sg4.x), __uint_as_float(sg4.y));
+                    const float g1 = fmaf(__uint_as_float(gr[2 * jj + 1]), __uint_as_float(sg4.z), __uint_as_float(sg4.w));
+                    const uint32_t sgm = hfma2(tanh_h2(pack_h2(g0, g1)), half2_half, half2_half);
+                    zz[jj] = hmul2(tanh_h2(pack_h2(f0, f1)), sgm);
+                }
+                return;
+            }
             const uint4 bf0 = lds128(bslot + ch * 2), bf1 = lds128(bslot + ch * 2 + 16);
             const uint4 bg0 = lds128(bslot + (R + ch) * 2), bg1 = lds128(bslot + (R + ch) * 2 + 16);
             const uint32_t bfw[8] = {bf0.x, bf0.y, bf0.z, bf0.w, bf1.x, bf1.y, bf1.z, bf1.w};
@@ -556,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         x[4 * c4 + 2] = fmaf(wi.z, sval, bi.z);
                         x[4 * c4 + 3] = fmaf(wi.w, sval, bi.w);
                     }
-                    store_x();
+                    store_x(reinterpret_cast<const float *>(pbr + 8 * R + 4 * S) + c0, 0u);
                     fence_proxy_async_smem();
                     tc_fence_before();
                     warp_arrive(B_XREADY + b);
@@ -572,20 +630,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     // lag history of layer l for the following tiles: rows t0+r, r >= 128 - n
                     if (tt + 1 < NT && r >= kTile - n) {
                         const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
-                        uint8_t *dst = ring_b + roff * (2 * R) + (uint64_t)((t0 + r) & (d - 1)) * 16;
+                        uint8_t *dst = ring_b + roff * Sh::XROW + (uint64_t)((t0 + r) & (d - 1)) * 16;
+                        if constexpr (F8) {
+                            // the quantised row is still in the staging buffer (rewritten after the rs MMA)
 #pragma unroll
-                        for (int c = 0; c < RH / 8; ++c) {
-                            uint4 v;
-                            v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
-                            v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
-                            v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
-                            v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
-                            *reinterpret_cast<uint4 *>(dst + (uint64_t)(hf * (RH / 8) + c) * d * 16) = v;
+                            for (int c = 0; c < RH / 16; ++c) {
+                                const int ck = hf * (RH / 16) + c;
+                                *reinterpret_cast<uint4 *>(dst + (uint64_t)ck * d * 16) =
+                                    lds128(st + ck * Sh::STAGE_LBO + (kTile + r) * 16);
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < RH / 8; ++c) {
+                                uint4 v;
+                                v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
+                                v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
+                                v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
+                                v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+                                *reinterpret_cast<uint4 *>(dst + (uint64_t)(hf * (RH / 8) + c) * d * 16) = v;
+                            }
                         }
                     }
                     // gate: z = tanh(f + b_f) * (0.5 tanh(g/2 + b_g/2) + 0.5), FP16x2
                     {
-                        const uint32_t bslot = sb + (g & 1) * Sh::BIAS_BYTES;
+                        const uint32_t bslot = sb + (g & 1) * Sh::CB_BYTES;
                         uint32_t fa[16], ga[16];
                         tmem_ld16(t_conv + c0, fa);
                         tmem_ld16(t_conv + R + c0, ga);
@@ -613,7 +681,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     tc_fence_after();
                     if (l + 1 < L) {
                         // residual: x_{l+1} = x_l + (W_res z) + b_res  (FP32)
-                        const uint32_t bres = sb + (2 + (g & 1)) * Sh::BIAS_BYTES + c0 * 4;
+                        const uint32_t rslot = sb + 2 * Sh::CB_BYTES + (g & 1) * Sh::RB_BYTES;
+                        const uint32_t bres = rslot + c0 * 4;
                         uint32_t rr[RH];
                         if constexpr (RH == 32) {
                             tmem_ld32(t_conv + R + c0, rr);
@@ -629,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             x[4 * k4 + 2] += __uint_as_float(rr[4 * k4 + 2]) + __uint_as_float(bb.z);
                             x[4 * k4 + 3] += __uint_as_float(rr[4 * k4 + 3]) + __uint_as_float(bb.w);
                         }
-                        store_x();
+                        store_x(nullptr, rslot + (R + c0) * 4);
                         fence_proxy_async_smem();
                         tc_fence_before();
                         warp_arrive(B_XREADY + b);
@@ -803,6 +872,8 @@ int g_dbg_drop = 0;
 
 struct TcState {
     int variant = -1;            // 0: (R, S, Hc) = (32, 32, 32); 1: (64, 128, 256)
+    bool f8 = false;             // FP8 E4M3 dilated convolutions (else BF16)
+    std::vector<float> amax;     // FP8: calibrated max |x_l| per [model][branch][layer][channel]
     DevBuf img, pblob, ring, zeros, err, slides, proj, koff;
     uint64_t img_stride = 0, pblob_stride = 0;
     int sms = 0;
@@ -831,12 +902,27 @@ inline uint16_t to_f16(float f) {
 
 // element (n, k) of a K-major operand with `rows` rows in the chunk-column layout
 inline size_t chunk_off(int rows, int n, int k) { return (size_t)(k / 8) * rows * 16 + (size_t)n * 16 + (k % 8) * 2; }
+inline size_t chunk_off8(int rows, int n, int k) { return (size_t)(k / 16) * rows * 16 + (size_t)n * 16 + (k % 16); }
 inline void put16(std::vector<uint8_t> &v, size_t off, uint16_t x) { std::memcpy(v.data() + off, &x, 2); }
 
-template <int R, int S, int HC>
-void build_images(const Dims &d, const float *hb, std::vector<uint8_t> &img, std::vector<uint8_t> &pbl,
-                  uint64_t &img_stride, uint64_t &pb_stride) {
-    using Sh = TcShape<R, S, HC>;
+// FP8 scaling.  Activations: x_l[i] ~ s_l[i] * q with q E4M3 and s_l[i] = kF8Margin * amax_l[i] / 448,
+// so that the calibrated maximum lands at 448 / kF8Margin and values up to kF8Margin times it stay
+// in range (larger ones saturate).  Weights: the activation scales are folded into the input
+// columns, then every output row o is scaled by its own w_o = max_k |W'[o][k]| / 448.
+constexpr float kF8Margin = 16.f;
+constexpr float kE4M3Max = 448.f;
+
+inline float f8_act_scale(float amax) { return amax > 0.f ? kF8Margin * amax / kE4M3Max : 1.f; }
+inline uint8_t to_e4m3(float f) { return (uint8_t)__nv_cvt_float_to_fp8(f, __NV_SATFINITE, __NV_E4M3); }
+
+template <int R, int S, int HC, bool F8>
+void build_images(const Dims &d, const float *hb, const float *amax, std::vector<uint8_t> &img,
+                  std::vector<uint8_t> &pbl, uint64_t &img_stride, uint64_t &pb_stride) {
+    using Sh = TcShape<R, S, HC, F8>;
+    // amax (FP8 only): [model][branch][layer][channel]
+    auto act_s = [&](int mi, int b, int l, int i) -> float {
+        return f8_act_scale(amax[(((int64_t)mi * 2 + b) * d.L + l) * R + i]);
+    };
     const int L = d.L;
     img_stride = (Sh::img_bytes(L) + 255) & ~uint64_t(255);
     pb_stride = ((uint64_t)Sh::pm_bytes(L) + 255) & ~uint64_t(255);
@@ -846,18 +932,34 @@ void build_images(const Dims &d, const float *hb, std::vector<uint8_t> &img, std
         const float *src = hb + (int64_t)mi * d.P;
         uint8_t *im0 = img.data() + img_stride * mi;
         std::vector<uint8_t> tmp;
+        std::vector<float> wscale(F8 ? (size_t)2 * L * 2 * R : 0);   // FP8: w_o per [branch][layer][o]
         for (int l = 0; l < L; ++l) {
             for (int b = 0; b < 2; ++b) {
                 // conv item: rows n = output channel (g half pre-halved), k < R lag tap, k >= R current tap
                 tmp.assign(Sh::CONV_BYTES, 0);
                 const float *wc = src + off_wconv(d, b, l);
-                for (int o = 0; o < 2 * R; ++o)
-                    for (int k = 0; k < 2 * R; ++k) {
-                        const int tap = k < R ? 0 : 1, i = k % R;
-                        float v = wc[((int64_t)o * 2 + tap) * R + i];
-                        if (o >= R) v *= 0.5f;
-                        put16(tmp, chunk_off(2 * R, o, k), to_bf16(v));
+                if constexpr (F8) {
+                    // E4M3 W'[o][k] / w_o with W' = W * s_l (per input channel); w_o goes to the conv slot
+                    for (int o = 0; o < 2 * R; ++o) {
+                        float mx = 0.f;
+                        for (int k = 0; k < 2 * R; ++k)
+                            mx = std::max(mx, std::fabs(wc[((int64_t)o * 2 + (k / R)) * R + k % R] * act_s(mi, b, l, k % R)));
+                        const float wo = mx > 0.f ? mx / kE4M3Max : 1.f;
+                        for (int k = 0; k < 2 * R; ++k) {
+                            const float v = wc[((int64_t)o * 2 + (k / R)) * R + k % R] * act_s(mi, b, l, k % R);
+                            tmp[chunk_off8(2 * R, o, k)] = to_e4m3(v / wo);
+                        }
+                        wscale[((int64_t)b * L + l) * 2 * R + o] = wo;
                     }
+                } else {
+                    for (int o = 0; o < 2 * R; ++o)
+                        for (int k = 0; k < 2 * R; ++k) {
+                            const int tap = k < R ? 0 : 1, i = k % R;
+                            float v = wc[((int64_t)o * 2 + tap) * R + i];
+                            if (o >= R) v *= 0.5f;
+                            put16(tmp, chunk_off(2 * R, o, k), to_bf16(v));
+                        }
+                }
                 std::memcpy(im0 + (uint64_t)l * Sh::LAYER_IMG + (uint64_t)b * Sh::CONV_BYTES, tmp.data(), tmp.size());
                 // rs item: W_res [R x R] then W_skip [S x R], FP16
                 tmp.assign(Sh::RS_BYTES, 0);
@@ -897,15 +999,32 @@ void build_images(const Dims &d, const float *hb, std::vector<uint8_t> &img, std
                 for (int l = 0; l < L; ++l) acc += src[off_bskip(d, b, l) + c];
                 bsk[c] = (float)acc;
             }
+            if constexpr (F8) {   // quantisation factors 1 / s_0 of the input projection's output
+                float *inv0 = bsk + S;
+                for (int c = 0; c < R; ++c) inv0[c] = 1.f / act_s(mi, b, 0, c);
+            }
             for (int l = 0; l < L; ++l) {
-                uint8_t *pl = pb + 8 * R + 4 * S + (uint64_t)l * Sh::PL_BYTES;
+                uint8_t *pl = pb + Sh::HDR_BYTES + (uint64_t)l * Sh::PL_BYTES;
                 const float *bc = src + off_bconv(d, b, l);
-                for (int o = 0; o < 2 * R; ++o) {
-                    const uint16_t h = to_f16(o < R ? bc[o] : 0.5f * bc[o]);
-                    std::memcpy(pl + 2 * o, &h, 2);
+                if constexpr (F8) {
+                    // {scale, bias} per output channel, g half pre-halved
+                    float *sb = reinterpret_cast<float *>(pl);
+                    for (int o = 0; o < 2 * R; ++o) {
+                        const float hlf = o < R ? 1.f : 0.5f;
+                        sb[2 * o] = hlf * wscale[((int64_t)b * L + l) * 2 * R + o];
+                        sb[2 * o + 1] = hlf * bc[o];
+                    }
+                } else {
+                    for (int o = 0; o < 2 * R; ++o) {
+                        const uint16_t h = to_f16(o < R ? bc[o] : 0.5f * bc[o]);
+                        std::memcpy(pl + 2 * o, &h, 2);
+                    }
                 }
-                float *br = reinterpret_cast<float *>(pl + 4 * R);
+                float *br = reinterpret_cast<float *>(pl + Sh::CB_BYTES);
                 for (int c = 0; c < R; ++c) br[c] = src[off_bres(d, b, l) + c];
+                if constexpr (F8) {   // quantisation factors of the next layer's input
+                    for (int c = 0; c < R; ++c) br[R + c] = l + 1 < L ? 1.f / act_s(mi, b, l + 1, c) : 1.f;
+                }
             }
         }
         float *ph = reinterpret_cast<float *>(pm + 2ull * Sh::pb_bytes(L));
@@ -917,24 +1036,24 @@ void build_images(const Dims &d, const float *hb, std::vector<uint8_t> &img, std
     }
 }
 
-template <int R, int S, int HC>
+template <int R, int S, int HC, bool F8>
 cudaError_t set_tc_attr() {
-    cudaError_t e = cudaFuncSetAttribute(k_branch_tc<R, S, HC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TcShape<R, S, HC>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_branch_tc<R, S, HC, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TcShape<R, S, HC, F8>::SMEM);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_slide_head<HC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)((HC / 8) * kSlideT * 16));
 }
 
-template <int R, int S, int HC>
+template <int R, int S, int HC, bool F8>
 gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL, int64_t nw, int W, int stride,
                      const int32_t *slides_host, int n_slides, float *out, bool logits, cudaStream_t st) {
-    using Sh = TcShape<R, S, HC>;
+    using Sh = TcShape<R, S, HC, F8>;
     const Dims &d = m->dims;
     if (nw <= 0) return GWE_OK;
     uint64_t ring_rows = 0;
     for (int l = 0; l < d.L; ++l) ring_rows += (uint64_t)1 << (l % d.lps);
-    const uint64_t ring_cta = (2 * ring_rows * 2 * R + 255) & ~uint64_t(255);
+    const uint64_t ring_cta = (2 * ring_rows * Sh::XROW + 255) & ~uint64_t(255);
     const int64_t max_jobs = (int64_t)d.n_models * nw;
     const int grid_max = (int)std::min<int64_t>(s.sms, max_jobs);
     GWE_CUDA_TRY(s.ring.ensure(ring_cta * grid_max));
@@ -978,7 +1097,7 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     p.dbg_drop = g_dbg_drop;
     if (n_slides == 0) {
         ProfScope prof("k_branch_tc", st);
-        k_branch_tc<R, S, HC><<<grid_max, kThreads, Sh::SMEM, st>>>(p);
+        k_branch_tc<R, S, HC, F8><<<grid_max, kThreads, Sh::SMEM, st>>>(p);
         note_launch();
         GWE_CUDA_TRY(cudaGetLastError());
         return GWE_OK;
@@ -994,7 +1113,7 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
         q.proj = s.proj.as<uint16_t>();
         {
             ProfScope prof("k_branch_tc", st);
-            k_branch_tc<R, S, HC><<<grid, kThreads, Sh::SMEM, st>>>(q);
+            k_branch_tc<R, S, HC, F8><<<grid, kThreads, Sh::SMEM, st>>>(q);
             note_launch();
         }
         const float *w2 = m->w32.as<float>() + (int64_t)mi * d.P + off_wh2(d);
@@ -1012,32 +1131,116 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     return GWE_OK;
 }
 
+// compile-time shape of one instantiation of the tensor-core kernel
+template <int R_, int S_, int HC_, bool F8_>
+struct TcTag {
+    static constexpr int R = R_, S = S_, HC = HC_;
+    static constexpr bool F8 = F8_;
+};
+
+// fn(TcTag<...>{}) for the handle's shape and operand type
+template <class Fn>
+auto tc_dispatch(const TcState &s, Fn &&fn) {
+    if (s.variant == 0) return s.f8 ? fn(TcTag<32, 32, 32, true>{}) : fn(TcTag<32, 32, 32, false>{});
+    return s.f8 ? fn(TcTag<64, 128, 256, true>{}) : fn(TcTag<64, 128, 256, false>{});
+}
+
+// Unit-variance white Gaussian noise for the default FP8 calibration: sample i of stream `seed`
+// is Box-Muller on two 24-bit uniforms drawn from splitmix64(seed * 2^32 + i).
+__global__ void k_calib_noise(float *__restrict__ out, int64_t n, uint64_t seed) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t z = (seed << 32) + (uint64_t)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const float u1 = ((float)(z >> 40) + 1.f) * (1.f / 16777216.f);      // (0, 1]
+    const float u2 = (float)((z >> 16) & 0xffffffu) * (1.f / 16777216.f); // [0, 1)
+    out[i] = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+
+constexpr int kCalibWindows = 64;
+
+// releases a temporary device buffer on every return path
+struct TmpBuf {
+    DevBuf b;
+    ~TmpBuf() { b.release(); }
+};
+
+// FP32 activation maxima over the windows of (sH, sL) into s.amax
+gwe_status measure_amax(gwe_model *m, TcState &s, const float *sH, const float *sL, int W, int stride, int64_t nw,
+                        cudaStream_t st) {
+    const Dims &d = m->dims;
+    const size_t na = (size_t)d.n_models * 2 * d.L * d.R;
+    TmpBuf tb;
+    DevBuf &buf = tb.b;
+    GWE_CUDA_TRY(buf.ensure(na * sizeof(float) + 64));
+    float *amax = buf.as<float>();
+    unsigned *keys = reinterpret_cast<unsigned *>(buf.as<uint8_t>() + na * sizeof(float));
+    gwe_status r = fp32_act_amax(m, sH, sL, W, stride, nw, amax, keys, st);
+    if (r == GWE_OK) {
+        s.amax.assign(na, 0.f);
+        cudaError_t e = cudaMemcpyAsync(s.amax.data(), amax, na * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error(std::string("FP8 calibration: ") + cudaGetErrorString(e));
+            r = GWE_ERR_CUDA;
+        }
+    }
+    return r;
+}
+
+// weight images of the handle's shape and operand type from the host blob, uploaded
+gwe_status build_upload(gwe_model *m, TcState &s, const float *hb) {
+    const Dims &d = m->dims;
+    std::vector<uint8_t> img, pbl;
+    tc_dispatch(s, [&](auto t) {
+        using T = decltype(t);
+        build_images<T::R, T::S, T::HC, T::F8>(d, hb, s.amax.data(), img, pbl, s.img_stride, s.pblob_stride);
+        return 0;
+    });
+    GWE_CUDA_TRY(s.img.ensure(img.size()));
+    GWE_CUDA_TRY(cudaMemcpy(s.img.ptr, img.data(), img.size(), cudaMemcpyHostToDevice));
+    GWE_CUDA_TRY(s.pblob.ensure(pbl.size()));
+    GWE_CUDA_TRY(cudaMemcpy(s.pblob.ptr, pbl.data(), pbl.size(), cudaMemcpyHostToDevice));
+    return GWE_OK;
+}
+
 }  // namespace
 
-bool bf16_supported(const Dims &d) { return tc_variant(d) >= 0 && d.lps <= 10; }
+bool tc_supported(const Dims &d) { return tc_variant(d) >= 0 && d.lps <= 10; }
 
-gwe_status bf16_prepare(gwe_model *m, const float *hb) {
+gwe_status tc_prepare(gwe_model *m, const float *hb, bool f8) {
     const Dims &d = m->dims;
-    if (!bf16_supported(d)) {
+    if (!tc_supported(d)) {
         set_error("tensor-core path supports (R, S, Hc) = (32, 32, 32) or (64, 128, 256), kernel 2, "
                   "layers_per_stack <= 10");
         return GWE_ERR_UNSUPPORTED;
     }
-    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
     if (!s) {
         s = new TcState();
-        m->bf16 = s;
+        m->tc = s;
     }
     s->variant = tc_variant(d);
-    std::vector<uint8_t> img, pbl;
-    if (s->variant == 0)
-        build_images<32, 32, 32>(d, hb, img, pbl, s->img_stride, s->pblob_stride);
-    else
-        build_images<64, 128, 256>(d, hb, img, pbl, s->img_stride, s->pblob_stride);
-    GWE_CUDA_TRY(s->img.ensure(img.size()));
-    GWE_CUDA_TRY(cudaMemcpy(s->img.ptr, img.data(), img.size(), cudaMemcpyHostToDevice));
-    GWE_CUDA_TRY(s->pblob.ensure(pbl.size()));
-    GWE_CUDA_TRY(cudaMemcpy(s->pblob.ptr, pbl.data(), pbl.size(), cudaMemcpyHostToDevice));
+    s->f8 = f8;
+    if (f8 && s->amax.size() != (size_t)d.n_models * 2 * d.L * d.R) {
+        // default activation scales: FP32 pass over synthetic whitened (unit-variance white) noise
+        const int W = 4096, stride = 2048;
+        const int64_t n = (int64_t)(kCalibWindows - 1) * stride + W;
+        TmpBuf tn;
+        DevBuf &noise = tn.b;
+        GWE_CUDA_TRY(noise.ensure(2 * n * sizeof(float)));
+        k_calib_noise<<<(unsigned)((n + 255) / 256), 256>>>(noise.as<float>(), n, 1);
+        k_calib_noise<<<(unsigned)((n + 255) / 256), 256>>>(noise.as<float>() + n, n, 2);
+        note_launch();
+        note_launch();
+        GWE_CUDA_TRY(cudaGetLastError());
+        gwe_status r = measure_amax(m, *s, noise.as<float>(), noise.as<float>() + n, W, stride, kCalibWindows, 0);
+        if (r != GWE_OK) return r;
+    }
+    gwe_status r = build_upload(m, *s, hb);
+    if (r != GWE_OK) return r;
     GWE_CUDA_TRY(s->zeros.ensure(4096));
     GWE_CUDA_TRY(cudaMemset(s->zeros.ptr, 0, 4096));
     GWE_CUDA_TRY(s->err.ensure(256));
@@ -1045,16 +1248,54 @@ gwe_status bf16_prepare(gwe_model *m, const float *hb) {
     GWE_CUDA_TRY(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, m->device));
     s->b2_host.resize(d.n_models);
     for (int mi = 0; mi < d.n_models; ++mi) s->b2_host[mi] = hb[(int64_t)mi * d.P + off_bh2(d)];
-    if (s->variant == 0) {
-        GWE_CUDA_TRY((set_tc_attr<32, 32, 32>()));
-    } else {
-        GWE_CUDA_TRY((set_tc_attr<64, 128, 256>()));
-    }
+    GWE_CUDA_TRY(tc_dispatch(*s, [](auto t) {
+        using T = decltype(t);
+        return set_tc_attr<T::R, T::S, T::HC, T::F8>();
+    }));
     return GWE_OK;
 }
 
-void bf16_release(gwe_model *m) {
-    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+gwe_status tc_calibrate(gwe_model *m, const float *sH, const float *sL, int64_t n, int W, int stride,
+                        cudaStream_t st) {
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
+    if (!s || s->variant < 0 || !s->f8) {
+        set_error("FP8 path not prepared");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    const Dims &d = m->dims;
+    const int64_t nw = (n - W) / stride + 1;
+    gwe_status r = measure_amax(m, *s, sH, sL, W, stride, nw, st);
+    if (r != GWE_OK) return r;
+    std::vector<float> hb((size_t)d.P * d.n_models);
+    GWE_CUDA_TRY(cudaMemcpy(hb.data(), m->w32.ptr, hb.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    return build_upload(m, *s, hb.data());
+}
+
+gwe_status tc_set_amax(gwe_model *m, const float *amax) {
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
+    if (!s || s->variant < 0 || !s->f8) {
+        set_error("FP8 path not prepared");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    const Dims &d = m->dims;
+    s->amax.assign(amax, amax + (size_t)d.n_models * 2 * d.L * d.R);
+    std::vector<float> hb((size_t)d.P * d.n_models);
+    GWE_CUDA_TRY(cudaMemcpy(hb.data(), m->w32.ptr, hb.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    return build_upload(m, *s, hb.data());
+}
+
+gwe_status tc_get_amax(gwe_model *m, float *amax) {
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
+    if (!s || s->variant < 0 || !s->f8) {
+        set_error("FP8 path not prepared");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    std::copy(s->amax.begin(), s->amax.end(), amax);
+    return GWE_OK;
+}
+
+void tc_release(gwe_model *m) {
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
     if (!s) return;
     s->img.release();
     s->pblob.release();
@@ -1065,13 +1306,13 @@ void bf16_release(gwe_model *m) {
     s->proj.release();
     s->koff.release();
     delete s;
-    m->bf16 = nullptr;
+    m->tc = nullptr;
 }
 
-gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int W, int stride,
+gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int W, int stride,
                         int64_t nw, const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st) {
     (void)n_samples;
-    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
     if (!s || s->variant < 0) {
         set_error("tensor-core path not prepared");
         return GWE_ERR_UNSUPPORTED;
@@ -1080,8 +1321,10 @@ gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
         set_error("tensor-core path needs window to be a multiple of 128");
         return GWE_ERR_UNSUPPORTED;
     }
-    if (s->variant == 0) return launch_tc<32, 32, 32>(m, *s, sH, sL, nw, W, stride, slides, n_slides, out, logits, st);
-    return launch_tc<64, 128, 256>(m, *s, sH, sL, nw, W, stride, slides, n_slides, out, logits, st);
+    return tc_dispatch(*s, [&](auto t) {
+        using T = decltype(t);
+        return launch_tc<T::R, T::S, T::HC, T::F8>(m, *s, sH, sL, nw, W, stride, slides, n_slides, out, logits, st);
+    });
 }
 
 gwe_status debug_config(int drop, double wait_seconds) {
@@ -1094,8 +1337,8 @@ gwe_status debug_config(int drop, double wait_seconds) {
     return GWE_OK;
 }
 
-gwe_status bf16_check(gwe_model *m, cudaStream_t st) {
-    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+gwe_status tc_check(gwe_model *m, cudaStream_t st) {
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
     if (!s) return GWE_OK;
     GWE_CUDA_TRY(cudaStreamSynchronize(st));
     int e = 0;
@@ -1152,15 +1395,15 @@ gwe_status static_scratch(uint8_t **out) {
     return GWE_OK;
 }
 
-template <int R, int S, int HC>
+template <int R, int S, int HC, bool F8>
 gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const float *sH, const float *sL, int64_t nw,
                             int W, int stride, float *out, int *status, cudaStream_t st) {
-    using Sh = TcShape<R, S, HC>;
+    using Sh = TcShape<R, S, HC, F8>;
     const Dims &d = m->dims;
     const int64_t n_jobs = (int64_t)d.n_models * nw;
     uint64_t ring_rows = 0;
     for (int l = 0; l < d.L; ++l) ring_rows += (uint64_t)1 << (l % d.lps);
-    const uint64_t ring_cta = (2 * ring_rows * 2 * R + 255) & ~uint64_t(255);
+    const uint64_t ring_cta = (2 * ring_rows * Sh::XROW + 255) & ~uint64_t(255);
     const uint64_t cap = kStaticScratchBytes - kStaticRingOff;
     if (ring_cta > cap) {
         set_error("gwe_forward_static: one CTA's lag ring (" + std::to_string(ring_cta) +
@@ -1199,7 +1442,7 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.proj = nullptr;
     p.wait_ns = g_wait_ns;
     p.dbg_drop = g_dbg_drop;
-    k_branch_tc<R, S, HC><<<grid, kThreads, Sh::SMEM, st>>>(p);
+    k_branch_tc<R, S, HC, F8><<<grid, kThreads, Sh::SMEM, st>>>(p);
     note_launch();
     GWE_CUDA_TRY(cudaGetLastError());
     return GWE_OK;
@@ -1217,11 +1460,11 @@ extern "C" gwe_status gwe_forward_static(gwe_model *m, const float *strain_H, co
     GWE_ARG_CHECK(strain_H != nullptr && strain_L != nullptr && out_prob != nullptr, "NULL buffer");
     GWE_ARG_CHECK(window > 0 && stride > 0 && stride <= window, "bad window/stride");
     GWE_ARG_CHECK(n >= window, "n_samples < window");
-    if (m->precision != GWE_BF16) {
-        set_error("gwe_forward_static: the handle must use the tensor-core precision (GWE_BF16)");
+    if (m->precision != GWE_BF16 && m->precision != GWE_FP8) {
+        set_error("gwe_forward_static: the handle must use a tensor-core precision (GWE_BF16 or GWE_FP8)");
         return GWE_ERR_UNSUPPORTED;
     }
-    TcState *s = reinterpret_cast<TcState *>(m->bf16);
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
     if (!s || s->variant < 0) {
         set_error("gwe_forward_static: tensor-core path not prepared");
         return GWE_ERR_UNSUPPORTED;
@@ -1235,7 +1478,9 @@ extern "C" gwe_status gwe_forward_static(gwe_model *m, const float *strain_H, co
     gwe_status st = static_scratch(&scratch);
     if (st != GWE_OK) return st;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    if (s->variant == 0)
-        return launch_tc_static<32, 32, 32>(m, *s, scratch, strain_H, strain_L, nw, window, stride, out_prob, status, cs);
-    return launch_tc_static<64, 128, 256>(m, *s, scratch, strain_H, strain_L, nw, window, stride, out_prob, status, cs);
+    return tc_dispatch(*s, [&](auto t) {
+        using T = decltype(t);
+        return launch_tc_static<T::R, T::S, T::HC, T::F8>(m, *s, scratch, strain_H, strain_L, nw, window, stride,
+                                                          out_prob, status, cs);
+    });
 }

@@ -444,6 +444,124 @@ gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
     return GWE_OK;
 }
 
+// ============================================================================ activation statistics
+// Largest |x_l[c]| per (model, branch, layer, channel) over a set of windows, from the FP32
+// forward: the calibration the FP8 tensor-core path takes its activation scales from.
+namespace {
+
+// monotone unsigned key of a float (ordered like the float), for atomic min / max
+__device__ __forceinline__ unsigned f_key(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float f_unkey(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// keys[2b], keys[2b+1]: keys of the minimum and maximum of strain b over [0, n)
+__global__ void k_strain_minmax(const float *__restrict__ sH, const float *__restrict__ sL, int64_t n,
+                                unsigned *__restrict__ keys) {
+    const int b = blockIdx.y;
+    const float *s = b ? sL : sH;
+    unsigned kmin = 0xffffffffu, kmax = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned k = f_key(s[i]);
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+    }
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(keys + 2 * b, kmin);
+        atomicMax(keys + 2 * b + 1, kmax);
+    }
+}
+
+// x_0 = w_in s + b_in is affine in s: its largest magnitude over the samples is taken at the
+// smallest or the largest sample.  amax[b * bstride + c] (layer 0) = that maximum.
+__global__ void k_amax_x0(const unsigned *__restrict__ keys, const float *__restrict__ win, int R,
+                          float *__restrict__ amax, int64_t bstride) {
+    const int b = blockIdx.x, c = threadIdx.x;
+    if (c >= R) return;
+    const float w = win[b * R + c], bi = win[2 * R + b * R + c];
+    const float lo = f_unkey(keys[2 * b]), hi = f_unkey(keys[2 * b + 1]);
+    const float m = fmaxf(fabsf(fmaf(w, lo, bi)), fabsf(fmaf(w, hi, bi)));
+    float *a = amax + b * bstride + c;
+    *a = fmaxf(*a, m);
+}
+
+// amax[b * bstride + c] = max(itself, max over the rows of branch b of |x[row][c]|)
+__global__ void k_amax_cols(const float *__restrict__ x, int64_t rows_per_branch, int R, float *__restrict__ amax,
+                            int64_t bstride) {
+    __shared__ unsigned sh[256];
+    const int b = blockIdx.y;
+    const int c = threadIdx.x % R, sub = threadIdx.x / R, nsub = blockDim.x / R;
+    if (threadIdx.x < R) sh[threadIdx.x] = 0u;
+    __syncthreads();
+    float m = 0.f;
+    const float *xb = x + (int64_t)b * rows_per_branch * R;
+    for (int64_t row = (int64_t)blockIdx.x * nsub + sub; row < rows_per_branch; row += (int64_t)gridDim.x * nsub)
+        m = fmaxf(m, fabsf(xb[row * R + c]));
+    atomicMax(sh + c, __float_as_uint(m));   // non-negative floats order like their bits
+    __syncthreads();
+    if (threadIdx.x < R) atomicMax(reinterpret_cast<unsigned *>(amax + b * bstride + threadIdx.x), sh[threadIdx.x]);
+}
+
+}  // namespace
+
+gwe_status fp32_act_amax(gwe_model *m, const float *sH, const float *sL, int W, int stride, int64_t nw,
+                         float *amax, unsigned *keys, cudaStream_t st) {
+    const Dims &d = m->dims;
+    const Variant v = variant_of(d);
+    if (v == kNone) {
+        set_error("FP32 path: unsupported configuration");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    const int R = d.R, L = d.L;
+    const int64_t chunk = std::min<int64_t>(nw, 128);
+    const size_t rows = (size_t)(2 * chunk) * W;
+    GWE_CUDA_TRY(m->ws.x0.ensure(rows * R * sizeof(float)));
+    GWE_CUDA_TRY(m->ws.x1.ensure(rows * R * sizeof(float)));
+    const Fp32Weights &f = m->f32;
+    const int64_t bstride = (int64_t)L * R;   // amax layout [model][branch][layer][channel]
+    GWE_CUDA_TRY(cudaMemsetAsync(amax, 0, sizeof(float) * d.n_models * 2 * bstride, st));
+    const unsigned init[4] = {0xffffffffu, 0u, 0xffffffffu, 0u};
+    GWE_CUDA_TRY(cudaMemcpyAsync(keys, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    GWE_CUDA_TRY(cudaStreamSynchronize(st));   // `init` is pageable stack memory
+    const int64_t n_used = (nw - 1) * (int64_t)stride + W;
+    k_strain_minmax<<<dim3(256, 2), 256, 0, st>>>(sH, sL, n_used, keys);
+    note_launch();
+    for (int mi = 0; mi < d.n_models; ++mi) {
+        const float *wm = f.buf.as<float>() + (int64_t)mi * f.model_stride;
+        const float *layers = wm + ((4 * R + 3) & ~3);
+        float *am = amax + (int64_t)mi * 2 * bstride;
+        k_amax_x0<<<2, 64, 0, st>>>(keys, wm, R, am, bstride);
+        note_launch();
+        for (int64_t w0 = 0; w0 < nw; w0 += chunk) {
+            const int C = (int)std::min<int64_t>(chunk, nw - w0);
+            float *xin = m->ws.x0.as<float>();
+            float *xout = m->ws.x1.as<float>();
+            for (int l = 0; l + 1 < L; ++l) {
+                const int dl = 1 << (l % d.lps);
+                const float *wl = layers + (int64_t)l * f.layer_stride;
+                const int64_t lstride = (int64_t)L * f.layer_stride;
+                const int flags = (l == 0 ? LF_FROM_STRAIN : 0) | LF_NO_SKIP;
+                if (v == kSmall)
+                    launch_layer<32, 32>(xin, xout, nullptr, wl, lstride, wm, sH, sL, w0, stride, W, C, dl, flags, st);
+                else
+                    launch_layer<64, 128>(xin, xout, nullptr, wl, lstride, wm, sH, sL, w0, stride, W, C, dl, flags, st);
+                const int64_t rpb = (int64_t)C * W;
+                const unsigned blocks = (unsigned)std::min<int64_t>(1024, (rpb + 255) / 256);
+                k_amax_cols<<<dim3(blocks, 2), 256, 0, st>>>(xout, rpb, R, am + (int64_t)(l + 1) * R, bstride);
+                note_launch();
+                std::swap(xin, xout);
+            }
+        }
+        GWE_CUDA_TRY(cudaGetLastError());
+    }
+    return GWE_OK;
+}
+
 // ============================================================================ backward (FP32)
 // Reverse-mode pass of one model over a batch of explicit windows (paper paragraph "AI ensemble
 // construction": per-time-step labels, binary cross-entropy on the logits), in FP32 with

@@ -106,7 +106,7 @@ struct gwe_model {
     int device = 0;
     gwe::DevBuf w32;              // FP32 blob [n_models][P] as given
     gwe::Fp32Weights f32;         // FP32 kernel layout
-    void *bf16 = nullptr;         // tensor-core path state (opaque, branch_tc.cu)
+    void *tc = nullptr;           // tensor-core path state (opaque, branch_tc.cu)
     void *bwd = nullptr;          // backward workspace (opaque, fp32_path.cu)
     gwe::Workspace ws;
 };
@@ -125,15 +125,25 @@ gwe_status fp32_backward(gwe_model *m, int model_index, const float *xH, const f
                          const float *dlogit, float *grad_w, float *grad_H, float *grad_L, cudaStream_t st);
 void fp32_backward_release(gwe_model *m);
 
-// branch_tc.cu (tensor-core path: GWE_BF16)
-gwe_status bf16_check(gwe_model *m, cudaStream_t st);
+// Largest |x_l[c]| per [model][branch][layer][channel] (device array `amax`) over the windows of
+// one segment, from the FP32 forward; `keys` is 4 unsigned of device scratch.
+gwe_status fp32_act_amax(gwe_model *m, const float *sH, const float *sL, int window, int stride, int64_t n_windows,
+                         float *amax, unsigned *keys, cudaStream_t st);
+
+// branch_tc.cu (tensor-core path: GWE_BF16, GWE_FP8)
+gwe_status tc_check(gwe_model *m, cudaStream_t st);
 gwe_status debug_config(int drop, double wait_seconds);
-gwe_status bf16_prepare(gwe_model *m, const float *host_blob);
-void bf16_release(gwe_model *m);
-gwe_status bf16_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
+// f8: E4M3 convolutions, calibrated on synthetic unit-variance white noise until tc_calibrate runs
+gwe_status tc_prepare(gwe_model *m, const float *host_blob, bool f8);
+gwe_status tc_calibrate(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window, int stride,
+                        cudaStream_t st);
+gwe_status tc_set_amax(gwe_model *m, const float *host_amax);   // [n_models][2][L][R]
+gwe_status tc_get_amax(gwe_model *m, float *host_amax);
+void tc_release(gwe_model *m);
+gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
                         int stride, int64_t n_windows, const int32_t *slides, int n_slides, float *out,
                         bool logits, cudaStream_t st);
-bool bf16_supported(const Dims &d);
+bool tc_supported(const Dims &d);
 
 // whiten.cu: Welch PSD (FP64 accumulation) and spectral whitening of one detector's strain
 gwe_status whiten_run(const float *x, int64_t n, double fs, int seg, float *out, cudaStream_t st);
