@@ -229,6 +229,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--slides", type=int, default=64,
                     help="also time the time-slide background pass with this many Livingston offsets (0: skip)")
+    ap.add_argument("--compare-minutes", type=float, default=6.0,
+                    help="time the other precisions' forward steps too (FP8 on the whole workload, FP32 on "
+                         "this many minutes of it); 0: skip")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -382,6 +385,49 @@ def main():
                               "slide heads per offset, triggers on every (offset, model) series"}
         del out_sl
 
+    # the same step in the other precisions (FP32: the plain SIMT path the speed-ups are quoted against)
+    precisions = None
+    if args.compare_minutes > 0:
+        precisions = {args.precision: {"value": value, "ms_per_step": ms_per_step, "strain_s": strain_s}}
+        for pname, pcode in PREC_NAMES.items():
+            if pname == args.precision:
+                continue
+            n_p = n if pname != "fp32" else min(n, int(args.compare_minutes * 60 * FS))
+            nw_p = gwe.gwe_n_windows(n_p, WINDOW, STRIDE)
+            m_p = gwe.Model(cfg, wb, pcode)
+            out_p = out if nw_p == nw else torch.empty((1, cfg["n_models"], nw_p, WINDOW), dtype=torch.float32,
+                                                       device=dev)
+            Hp, Lp = H[:n_p], L[:n_p]
+
+            def step_p():
+                gwe.gwe_whiten(Hp, n_p, float(FS), WELCH_SEG, Hw[:n_p], stream=stream)
+                gwe.gwe_whiten(Lp, n_p, float(FS), WELCH_SEG, Lw[:n_p], stream=stream)
+                gwe.gwe_forward(m_p.handle, Hw[:n_p], Lw[:n_p], n_p, WINDOW, STRIDE, None, out_p, stream)
+                return gwe.gwe_triggers(out_p, cfg["n_models"], 1, nw_p, WINDOW, STRIDE, thr, min_width, coinc,
+                                        flags=0, stream=stream)
+
+            step_p()
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            ts = []
+            for _ in range(2):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step_p()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            t_p = multi.max_over_ranks(sum(ts) / len(ts), dist, dev)
+            precisions[pname] = {"value": world * (n_p / FS) / (t_p / 1000.0), "ms_per_step": t_p,
+                                 "strain_s": n_p / FS}
+            m_p.close()
+        if "fp32" in precisions:
+            for pname in precisions:
+                precisions[pname]["speedup_vs_fp32"] = precisions[pname]["value"] / precisions["fp32"]["value"]
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -440,6 +486,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "time_slides": slides_res,
+        "precisions": precisions,
         "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                     for k, v in prof.items()},
     }

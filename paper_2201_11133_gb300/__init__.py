@@ -22,7 +22,7 @@ __all__ = [
     "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_calibrate", "gwe_model_set_fp8_amax", "gwe_model_get_fp8_amax",
     "gwe_model_destroy",
     "gwe_forward", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
-    "gwe_version", "gwe_sync", "gwe_forward_static", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
+    "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
 
 GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
@@ -87,6 +87,7 @@ def load():
             "gwe_triggers": (I, [P, I, I, I64, I, I, F, D, I64, I, P, I64, P, P]),
             "gwe_whiten": (I, [P, I64, D, I, I, P, P]),
             "gwe_sync": (I, [P, P]),
+            "gwe_set_cross_window_reuse": (I, [I]),
             "gwe_debug_config": (I, [I, D]),
             "gwe_forward_static": (I, [P, P, P, I64, I, I, P, P, P]),
             "gwe_profile_enable": (I, [I]),
@@ -240,6 +241,11 @@ def gwe_forward_static(model: int, strain_H, strain_L, n_samples: int, window: i
     _check(load().gwe_forward_static(model, _dptr(strain_H), _dptr(strain_L), int(n_samples), int(window),
                                      int(stride), _dptr(out_prob), _dptr(status), _stream(stream)),
            "gwe_forward_static")
+
+
+def gwe_set_cross_window_reuse(enable: bool) -> None:
+    """Process-wide switch of the tensor-core path's cross-window reuse (results are bit-identical)."""
+    _check(load().gwe_set_cross_window_reuse(1 if enable else 0), "gwe_set_cross_window_reuse")
 
 
 def gwe_debug_config(drop: int, wait_seconds: float) -> None:

@@ -262,6 +262,13 @@ gwe_status gwe_sync(gwe_model *m, void *stream) {
     return GWE_OK;
 }
 
+gwe_status gwe_set_cross_window_reuse(int enable) {
+    clear_error();
+    GWE_ARG_CHECK(enable == 0 || enable == 1, "enable must be 0 or 1");
+    set_cross_window_reuse(enable);
+    return GWE_OK;
+}
+
 gwe_status gwe_debug_config(int drop, double wait_seconds) {
     clear_error();
     return debug_config(drop, wait_seconds);

@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -157,7 +158,8 @@ struct TcParams {
     float *out;
     int logits;
     uint8_t *ring;             // per-CTA lag history
-    uint64_t ring_cta_bytes;
+    uint64_t ring_cta_bytes;   // per-CTA stride
+    uint64_t ring_pp;          // offset of the second ring of a CTA (cross-window reuse), 0: one ring
     const uint8_t *zeros;      // >= 2 KiB of zeros
     int L, lps;
     uint64_t ring_rows;        // lag-history rows per branch (sum of dilations)
@@ -170,7 +172,30 @@ struct TcParams {
     uint16_t *proj;
     uint64_t wait_ns;          // limit of every device-side wait
     int dbg_drop;              // test hook: 1 = branch 0's producer issues nothing (its consumers' waits run out)
+    // Cross-window reuse (0 = off).  Window w+1 of a segment starts stride samples after window w,
+    // so its tile t is window w's tile t + reuse_shift.  Layer l's output at a position p that is at
+    // least r_l - 1 samples from the window start (r_l the receptive field after layer l) does not
+    // see the zero padding and equals window w's at p + stride.  For tile t, layers 0 .. lstar[t]
+    // satisfy this on all 128 rows (lstar[t] = -1: none); their x_{lstar+1} and partial skip sum
+    // are taken from window w's tile t + reuse_shift (exactly the values recomputation would give)
+    // through a per-CTA carry buffer, and the tile starts at layer lstar[t] + 1.
+    // With reuse the CTA keeps two rings and alternates them per job: a tile that computes every
+    // layer may need lagged rows of a layer that an earlier (reusing) tile of the same window
+    // skipped; those rows are the previous window's, at the same ring offsets (the shift is a
+    // multiple of every dilation), and are read from the previous job's ring.
+    int reuse_shift;
+    float *carry;              // per CTA: [branch][tile < NT - reuse_shift][(RH + SH) / 4][256 threads] float4
+    uint64_t carry_cta_floats;
+    int8_t lstar[64];
 };
+
+// contiguous job range [j0, j1) of this CTA: consecutive windows of one model follow each other,
+// which cross-window reuse needs
+__device__ __forceinline__ void job_range(int64_t n_jobs, int64_t &j0, int64_t &j1) {
+    const int64_t q = n_jobs / gridDim.x, rm = n_jobs % gridDim.x, c = blockIdx.x;
+    j0 = c * q + (c < rm ? c : rm);
+    j1 = j0 + q + (c < rm ? 1 : 0);
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -293,17 +318,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 uint32_t it[2] = {0, 0};       // items issued per entry
                 uint32_t lag_issued = 0, ph_h = 0, g = 0, g_conv = 0, g_res = 0;
                 bool ok = true, first = true;
-                uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * Sh::XROW;
+                uint8_t *ring_c = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * Sh::XROW;
                 auto take = [&](int e, int site) -> bool {
                     return mbar_wait(&bar[B_WEMPTY + 2 * b + e], ((it[e] & 1) ^ 1), abort_flag, p.err, site, p.wait_ns);
                 };
-                auto issue_lag = [&](int l, int t0) {
+                // lagged rows of layer l for the tile at t0 (ring par of this job, or the previous
+                // job's ring when the source rows were taken over from the previous window)
+                auto issue_lag = [&](int l, int t0, bool ru, uint32_t par) {
                     const int d = 1 << (l % lps);
                     const int n = d < kTile ? d : kTile;
                     const uint32_t bytes = (uint32_t)n * 16;
                     mbar_arrive_expect_tx(&bar[B_LAG + b], bytes * Sh::RC);
                     const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
-                    const uint8_t *src = ring_b + roff * Sh::XROW + (uint64_t)(t0 & (d - 1)) * 16;
+                    const int ts = t0 / kTile - (d < kTile ? 1 : d / kTile);   // tile holding the source rows
+                    const bool prev = ru && ts >= 0 && ts < NT - p.reuse_shift && l <= p.lstar[ts];
+                    const uint8_t *src = ring_c + (uint64_t)(par ^ (prev ? 1u : 0u)) * p.ring_pp + roff * Sh::XROW +
+                                         (uint64_t)(t0 & (d - 1)) * 16;
                     uint8_t *dst0 = smem + Sh::OFF_STAGE + b * Sh::STAGE_BYTES + (kTile - n) * 16;
 #pragma unroll
                     for (int c = 0; c < Sh::RC; ++c)
@@ -313,12 +343,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 };
                 // test hook: branch 0's producer issues nothing, so the MMA warp's first wait runs out
                 if (p.dbg_drop == 1 && b == 0) ok = false;
-                for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
+                int64_t j0, j1;
+                job_range(n_jobs, j0, j1);
+                for (int64_t j = j0; j < j1 && ok; ++j) {
                     const Job q = decode_job(p, j);
+                    const bool ru = p.reuse_shift > 0 && j > j0 && q.w > 0;
+                    const uint32_t par = (uint32_t)((j - j0) & 1);
                     const uint8_t *wm = p.wimg + (uint64_t)q.m * p.wimg_stride;
                     const uint8_t *play = p.pblob + (uint64_t)q.m * p.pblob_stride + b * Sh::pb_bytes(L) + Sh::HDR_BYTES;
                     for (int tt = 0; tt < NT && ok; ++tt) {
-                        for (int l = 0; l < L; ++l, ++g) {
+                        const int l0 = ru ? p.lstar[tt] + 1 : 0;
+                        for (int l = l0; l < L; ++l, ++g) {
                             // conv entry: free once the previous conv (or head piece) MMA completed
                             if (!(ok = take(0, 1))) break;
                             mbar_arrive_expect_tx(&bar[B_WFULL + 2 * b + 0], Sh::CONV_BYTES);
@@ -333,15 +368,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             g_conv = g + 1;
                             ++it[0];
                             // lagged rows: the staging buffer is free once the previous conv completed
-                            // (layer 0: once the previous tile's head has read it)
-                            if (l > 0 || first) {
-                                issue_lag(l, tt * kTile);
+                            // (first layer of a tile: once the previous tile's head has read it)
+                            if (l > l0 || first) {
+                                issue_lag(l, tt * kTile, ru, par);
                             } else {
                                 ok = mbar_wait(&bar[B_HREADY + b], ph_h & 1, abort_flag, p.err, 3, p.wait_ns) &&
                                      mbar_wait(&bar[B_HEAD], ph_h & 1, abort_flag, p.err, 4, p.wait_ns);
                                 if (!ok) break;
                                 ++ph_h;
-                                issue_lag(0, tt * kTile);
+                                issue_lag(l, tt * kTile, ru, par);
                             }
                             first = false;
                             // rs entry
@@ -404,15 +439,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 const uint64_t b_res0 = sdesc(e_rs, R * 16, 128);
                 const uint64_t b_skip0 = sdesc(e_rs + Sh::RES_BYTES, S * 16, 128);
                 constexpr uint64_t A_STEP = 2 * Sh::STAGE_LBO / 16;
-                for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
+                int64_t j0, j1;
+                job_range(n_jobs, j0, j1);
+                for (int64_t j = j0; j < j1 && ok; ++j) {
+                    const bool ru = p.reuse_shift > 0 && j > j0 && (j % p.nw) > 0;
                     for (int tt = 0; tt < NT && ok; ++tt) {
+                        const int l0 = ru ? p.lstar[tt] + 1 : 0;
                         // Ping-pong: branch 1 starts a tile once branch 0's first gate is done, so
                         // that one branch's MMAs overlap the other's gate for the rest of the tile.
                         if (b == 1) {
                             if (!(ok = mbar_wait(&bar[B_GO], ph_go & 1, abort_flag, p.err, 19, p.wait_ns))) break;
                             ++ph_go;
                         }
-                        for (int l = 0; l < L; ++l) {
+                        for (int l = l0; l < L; ++l) {
                             const int d = 1 << (l % lps);
                             const int n = d < kTile ? d : kTile;
                             ok = mbar_wait(&bar[B_XREADY + b], ph_x & 1, abort_flag, p.err, 10, p.wait_ns) &&
@@ -444,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                                  mbar_wait(&bar[B_WFULL + 2 * b + 1], it[1] & 1, abort_flag, p.err, 14, p.wait_ns);
                             if (!ok) break;
                             ++ph_z;
-                            if (b == 0 && l == 0) mbar_arrive(&bar[B_GO]);
+                            if (b == 0 && l == l0) mbar_arrive(&bar[B_GO]);
                             tc_fence_after();
                             // z (FP16, two per column) sits in the f columns: channels [16ks, 16ks+16)
                             // at column zcol(ks); r goes to the g columns, s accumulates after them
@@ -506,8 +545,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
         const uint32_t st = s_stage + b * Sh::STAGE_BYTES;
         const uint32_t sb = s_bias + b * Sh::BIAS_BR;
         const int c0 = hf * RH;                        // first channel of this thread
-        uint8_t *ring_b = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * Sh::XROW;
-        uint32_t ph_conv = 0, ph_rs = 0, ph_head = 0, ph_wg = 0, ph_pair = 0, tiles = 0;
+        uint8_t *ring_c = p.ring + (uint64_t)blockIdx.x * p.ring_cta_bytes + (uint64_t)b * p.ring_rows * Sh::XROW;
+        uint32_t ph_conv = 0, ph_rs = 0, ph_head = 0, ph_wg = 0, ph_pair = 0;
+        uint32_t g = 0;                                // computed layers so far: bias slot g & 1, use (g >> 1)
+        const int ntr = NT - p.reuse_shift;            // tiles that can take layers from the previous window
+        float4 *carry_t = reinterpret_cast<float4 *>(p.carry + (uint64_t)blockIdx.x * p.carry_cta_floats) +
+                          (uint64_t)b * ntr * ((RH + SH) / 4) * 256 + (hf * kTile + r);
         bool ok = true;
         float x[RH];
         const uint32_t half2_half = 0x38003800u;     // (0.5, 0.5) in FP16x2
@@ -589,8 +632,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             }
         };
 
-        for (int64_t j = blockIdx.x; j < n_jobs && ok; j += gridDim.x) {
+        int64_t j0, j1;
+        job_range(n_jobs, j0, j1);
+        for (int64_t j = j0; j < j1 && ok; ++j) {
             const Job jb = decode_job(p, j);
+            const bool ru = p.reuse_shift > 0 && j > j0 && jb.w > 0;                // take from the previous window
+            const bool cw = p.reuse_shift > 0 && j + 1 < j1 && jb.w + 1 < p.nw;     // give to the next one
+            uint8_t *ring_b = ring_c + (uint64_t)((j - j0) & 1) * p.ring_pp;
             const uint8_t *pm = p.pblob + (uint64_t)jb.m * p.pblob_stride;
             const uint8_t *pbr = pm + b * Sh::pb_bytes(L);
             const float4 *w_in4 = reinterpret_cast<const float4 *>(pbr) + c0 / 4;
@@ -601,10 +649,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             const float b2 = __ldg(phd + 2 * HC);
             const float *sv = b ? p.sL + jb.wl * (int64_t)p.stride : p.sH + jb.w * (int64_t)p.stride;
             float *outp = p.out + (((int64_t)jb.si * p.n_models + jb.m) * p.nw + jb.w) * (int64_t)p.W;
-            for (int tt = 0; tt < NT && ok; ++tt, ++tiles) {
+            for (int tt = 0; tt < NT && ok; ++tt) {
                 const int t0 = tt * kTile;
-                // input 1x1 convolution x_0 = w_in s + b_in (FP32), BF16 copy for the MMA
-                {
+                const int l0 = ru ? p.lstar[tt] + 1 : 0;
+                // carry slot written by this tile for the next window's tile tt - shift (-1: none)
+                const int lgive = (cw && tt >= p.reuse_shift) ? p.lstar[tt - p.reuse_shift] : -1;
+                if (l0 > 0) {
+                    // x_{l0} and the skip sum of layers < l0 from the previous window (same thread wrote them)
+                    const float4 *cs = carry_t + (uint64_t)tt * ((RH + SH) / 4) * 256;
+#pragma unroll
+                    for (int k4 = 0; k4 < RH / 4; ++k4) {
+                        const float4 v = cs[(uint64_t)k4 * 256];
+                        x[4 * k4 + 0] = v.x;
+                        x[4 * k4 + 1] = v.y;
+                        x[4 * k4 + 2] = v.z;
+                        x[4 * k4 + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int k8 = 0; k8 < SH / 8; ++k8) {
+                        const float4 u0 = cs[(uint64_t)(RH / 4 + 2 * k8) * 256];
+                        const float4 u1 = cs[(uint64_t)(RH / 4 + 2 * k8 + 1) * 256];
+                        const uint32_t sv8[8] = {__float_as_uint(u0.x), __float_as_uint(u0.y), __float_as_uint(u0.z),
+                                                 __float_as_uint(u0.w), __float_as_uint(u1.x), __float_as_uint(u1.y),
+                                                 __float_as_uint(u1.z), __float_as_uint(u1.w)};
+                        tmem_st8(t_skip + hf * SH + 8 * k8, sv8);
+                    }
+                    tmem_st_wait();
+                    // quantisation factors of layer l0 (FP8): the residual slot of layer l0 - 1
+                    store_x(reinterpret_cast<const float *>(pbr + Sh::HDR_BYTES + (uint64_t)(l0 - 1) * Sh::PL_BYTES +
+                                                            Sh::CB_BYTES) + R + c0, 0u);
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    warp_arrive(B_XREADY + b);
+                } else {
+                    // input 1x1 convolution x_0 = w_in s + b_in (FP32), BF16 copy for the MMA
                     const float sval = __ldg(sv + t0 + r);
 #pragma unroll
                     for (int c4 = 0; c4 < RH / 4; ++c4) {
@@ -619,16 +697,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     tc_fence_before();
                     warp_arrive(B_XREADY + b);
                 }
-                for (int l = 0; l < L; ++l) {
+                for (int l = l0; l < L; ++l, ++g) {
                     const int d = 1 << (l % lps);
                     const int n = d < kTile ? d : kTile;
-                    const uint32_t g = tiles * (uint32_t)L + l;   // layer ordinal: bias slot g & 1, use (g >> 1)
                     if (!warp_wait(B_CONV + b, ph_conv & 1, 30) ||
                         !warp_wait(B_BIAS + 4 * b + (g & 1), (g >> 1) & 1, 36)) { ok = false; break; }
                     ++ph_conv;
                     tc_fence_after();
-                    // lag history of layer l for the following tiles: rows t0+r, r >= 128 - n
-                    if (tt + 1 < NT && r >= kTile - n) {
+                    // lag history of layer l for the following tiles (and, when the next window takes
+                    // over layers, for its full tiles): rows t0+r, r >= 128 - n
+                    if ((tt + 1 < NT || cw) && r >= kTile - n) {
                         const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
                         uint8_t *dst = ring_b + roff * Sh::XROW + (uint64_t)((t0 + r) & (d - 1)) * 16;
                         if constexpr (F8) {
@@ -702,6 +780,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         fence_proxy_async_smem();
                         tc_fence_before();
                         warp_arrive(B_XREADY + b);
+                        if (l == lgive) {
+                            // x_{l+1} and the skip sum of layers <= l for the next window's tile tt - shift
+                            float4 *cd = carry_t + (uint64_t)(tt - p.reuse_shift) * ((RH + SH) / 4) * 256;
+#pragma unroll
+                            for (int k4 = 0; k4 < RH / 4; ++k4)
+                                cd[(uint64_t)k4 * 256] = make_float4(x[4 * k4], x[4 * k4 + 1], x[4 * k4 + 2], x[4 * k4 + 3]);
+#pragma unroll
+                            for (int cc = 0; cc < SH / 16; ++cc) {
+                                uint32_t sr[16];
+                                tmem_ld16(t_skip + hf * SH + 16 * cc, sr);
+                                tmem_ld_wait();
+#pragma unroll
+                                for (int k4 = 0; k4 < 4; ++k4)
+                                    cd[(uint64_t)(RH / 4 + 4 * cc + k4) * 256] =
+                                        make_float4(__uint_as_float(sr[4 * k4]), __uint_as_float(sr[4 * k4 + 1]),
+                                                    __uint_as_float(sr[4 * k4 + 2]), __uint_as_float(sr[4 * k4 + 3]));
+                            }
+                        }
                     }
                 }
                 if (!ok) break;
@@ -869,12 +965,47 @@ namespace {
 // Test hooks (gwe_debug_config): limit of every device-side wait, and a dropped producer.
 uint64_t g_wait_ns = kWaitNs;
 int g_dbg_drop = 0;
+std::atomic<int> g_reuse{1};   // cross-window reuse on (gwe_set_cross_window_reuse)
+
+// Cross-window reuse plan (fields of TcParams): for stride a multiple of the tile with
+// W/2 <= stride < W, window w+1's tile t is window w's tile t + stride/128; layer l's output there
+// is free of the window-start padding once 128 t >= r_l - 1, r_l = 1 + sum_{l' <= l} (k - 1) d_l'.
+// The last layer is always computed (lstar <= L - 2).  stride < W/2 would make a tile both take
+// and give, which the carry buffer does not support: no reuse then.
+void plan_reuse(const Dims &d, int W, int stride, bool enable, TcParams &p) {
+    p.reuse_shift = 0;
+    p.carry = nullptr;
+    p.carry_cta_floats = 0;
+    std::memset(p.lstar, -1, sizeof(p.lstar));
+    const int NT = W / kTile;
+    if (!enable || stride % kTile != 0 || stride >= W || 2 * stride < W || NT > 64 || d.L < 2) return;
+    const int shift = stride / kTile;
+    std::vector<int64_t> rl(d.L);
+    int64_t rf = 1;
+    for (int l = 0; l < d.L; ++l) {
+        rf += (int64_t)(d.k - 1) << (l % d.lps);
+        rl[l] = rf;
+    }
+    bool any = false;
+    for (int t = 0; t < NT - shift; ++t) {
+        int ls = -1;
+        for (int l = 0; l < d.L - 1 && l < 127; ++l) {
+            if (rl[l] - 1 <= (int64_t)kTile * t)
+                ls = l;
+            else
+                break;
+        }
+        p.lstar[t] = (int8_t)ls;
+        any = any || ls >= 0;
+    }
+    if (any) p.reuse_shift = shift;
+}
 
 struct TcState {
     int variant = -1;            // 0: (R, S, Hc) = (32, 32, 32); 1: (64, 128, 256)
     bool f8 = false;             // FP8 E4M3 dilated convolutions (else BF16)
     std::vector<float> amax;     // FP8: calibrated max |x_l| per [model][branch][layer][channel]
-    DevBuf img, pblob, ring, zeros, err, slides, proj, koff;
+    DevBuf img, pblob, ring, zeros, err, slides, proj, koff, carry;
     uint64_t img_stride = 0, pblob_stride = 0;
     int sms = 0;
     std::vector<float> b2_host;   // b_h2 per model (slide heads take it by value)
@@ -1056,7 +1187,10 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     const uint64_t ring_cta = (2 * ring_rows * Sh::XROW + 255) & ~uint64_t(255);
     const int64_t max_jobs = (int64_t)d.n_models * nw;
     const int grid_max = (int)std::min<int64_t>(s.sms, max_jobs);
-    GWE_CUDA_TRY(s.ring.ensure(ring_cta * grid_max));
+    TcParams p;
+    plan_reuse(d, W, stride, g_reuse.load() != 0, p);
+    const uint64_t n_rings = p.reuse_shift > 0 ? 2 : 1;
+    GWE_CUDA_TRY(s.ring.ensure(n_rings * ring_cta * grid_max));
     const int32_t *dsl = nullptr;
     if (n_slides > 0) {
         // offsets reduced to [0, n_w) on the host (pageable source: the copy is staged before return)
@@ -1069,7 +1203,6 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
         GWE_CUDA_TRY(cudaMemcpyAsync(s.koff.ptr, red.data(), sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
         dsl = s.koff.as<int32_t>();
     }
-    TcParams p;
     p.wimg = s.img.as<uint8_t>();
     p.wimg_stride = s.img_stride;
     p.pblob = s.pblob.as<uint8_t>();
@@ -1085,7 +1218,8 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     p.out = out;
     p.logits = logits ? 1 : 0;
     p.ring = s.ring.as<uint8_t>();
-    p.ring_cta_bytes = ring_cta;
+    p.ring_cta_bytes = n_rings * ring_cta;
+    p.ring_pp = n_rings > 1 ? ring_cta : 0;
     p.zeros = s.zeros.as<uint8_t>();
     p.L = d.L;
     p.lps = d.lps;
@@ -1095,6 +1229,12 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     p.proj = nullptr;
     p.wait_ns = g_wait_ns;
     p.dbg_drop = g_dbg_drop;
+    if (p.reuse_shift > 0) {
+        const int ntr = W / kTile - p.reuse_shift;
+        p.carry_cta_floats = (uint64_t)2 * ntr * (R / 2 + S / 2) * 256;
+        GWE_CUDA_TRY(s.carry.ensure(sizeof(float) * p.carry_cta_floats * grid_max));
+        p.carry = s.carry.as<float>();
+    }
     if (n_slides == 0) {
         ProfScope prof("k_branch_tc", st);
         k_branch_tc<R, S, HC, F8><<<grid_max, kThreads, Sh::SMEM, st>>>(p);
@@ -1305,6 +1445,7 @@ void tc_release(gwe_model *m) {
     s->slides.release();
     s->proj.release();
     s->koff.release();
+    s->carry.release();
     delete s;
     m->tc = nullptr;
 }
@@ -1326,6 +1467,8 @@ gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_
         return launch_tc<T::R, T::S, T::HC, T::F8>(m, *s, sH, sL, nw, W, stride, slides, n_slides, out, logits, st);
     });
 }
+
+void set_cross_window_reuse(int enable) { g_reuse.store(enable ? 1 : 0); }
 
 gwe_status debug_config(int drop, double wait_seconds) {
     if (drop < 0 || drop > 1 || !(wait_seconds > 0.0) || wait_seconds > 60.0) {
@@ -1433,6 +1576,7 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.logits = 0;
     p.ring = scratch + kStaticRingOff;
     p.ring_cta_bytes = ring_cta;
+    p.ring_pp = 0;
     p.zeros = scratch + kStaticZeroOff;
     p.L = d.L;
     p.lps = d.lps;
@@ -1442,6 +1586,7 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.proj = nullptr;
     p.wait_ns = g_wait_ns;
     p.dbg_drop = g_dbg_drop;
+    plan_reuse(d, W, stride, false, p);   // no carry buffer in the fixed scratch
     k_branch_tc<R, S, HC, F8><<<grid, kThreads, Sh::SMEM, st>>>(p);
     note_launch();
     GWE_CUDA_TRY(cudaGetLastError());

@@ -53,3 +53,14 @@ def test_model_create_without_gpu_fails_loudly():
         assert e.status == 2
     else:
         raise AssertionError("model creation succeeded without a GPU")
+
+
+def test_reuse_switch_host_only():
+    gwe.gwe_set_cross_window_reuse(False)
+    gwe.gwe_set_cross_window_reuse(True)
+    try:
+        gwe._check(gwe.load().gwe_set_cross_window_reuse(2), "gwe_set_cross_window_reuse")
+    except gwe.GweError as e:
+        assert e.status == 1
+    else:
+        raise AssertionError("enable = 2 accepted")
