@@ -202,6 +202,29 @@ gwe_status gwe_backward(gwe_model *model, int model_index, const float *x_H, con
                         void *stream);
 
 /*
+ * Ensemble forward over a batch of science segments of uneven length in one
+ * pass (section "Statistical Analysis": the data come as segments, and time
+ * slides pair windows within a segment).  Equivalent to one gwe_forward per
+ * segment with the outputs concatenated, but every kernel launch covers all
+ * segments (the persistent tensor-core kernel walks the windows of all
+ * segments and models; cross-window reuse stops at segment boundaries).
+ *   strain_H, strain_L  device FP32; segment g is samples
+ *                       [seg_start[g], seg_start[g] + seg_len[g]) of both.
+ *   seg_start, seg_len  host int64 [n_segments]; a segment shorter than one
+ *                       window has no windows.
+ *   slides              as in gwe_forward; Livingston windows wrap within
+ *                       each segment: (w + k) mod n_windows(segment).
+ *   out_prob            device FP32 [max(n_slides,1)][n_models][N][window],
+ *                       N = sum over segments of gwe_n_windows(seg_len[g]);
+ *                       segment g's windows follow those of segments < g.
+ * GWE_ERR_ARG for n_segments < 1, a negative start or length, or the
+ * conditions of gwe_forward.
+ */
+gwe_status gwe_forward_segments(gwe_model *model, const float *strain_H, const float *strain_L,
+                                const int64_t *seg_start, const int64_t *seg_len, int n_segments, int window,
+                                int stride, const int32_t *slides, int n_slides, float *out_prob, void *stream);
+
+/*
  * Wait for the work queued on `stream` and report device-side failures of the
  * handle's kernels: GWE_ERR_TIMEOUT when a bounded wait inside a tensor-core
  * kernel gave up (its outputs are then invalid), GWE_ERR_CUDA for a CUDA
@@ -285,6 +308,19 @@ gwe_status gwe_forward_static(gwe_model *model, const float *strain_H, const flo
 gwe_status gwe_triggers(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,
                         int stride, float height_thr, double min_width, int64_t coinc, int flags,
                         gwe_trigger *out, int64_t cap, int64_t *n_out, void *stream);
+
+/*
+ * Peaks and ensemble triggers of every segment of a gwe_forward_segments
+ * output: the same as gwe_triggers applied to each segment's windows (series
+ * never span segments; `index` is relative to the segment's first sample).
+ *   seg_len      host int64 [n_segments], the lengths given to gwe_forward_segments.
+ *   out_segment  host int32 [cap] or NULL: the segment of each record.
+ * Records are ordered by segment, then as in gwe_triggers.  Synchronises `stream`.
+ */
+gwe_status gwe_triggers_segments(const float *prob, int n_models, int n_slides, const int64_t *seg_len,
+                                 int n_segments, int window, int stride, float height_thr, double min_width,
+                                 int64_t coinc, int flags, gwe_trigger *out, int32_t *out_segment, int64_t cap,
+                                 int64_t *n_out, void *stream);
 
 /*
  * Whitening front end (paper section "Materials and Methods", paragraph "Data

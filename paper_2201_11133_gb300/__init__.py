@@ -21,7 +21,7 @@ __all__ = [
     "GWE_FP32", "GWE_BF16", "GWE_FP8", "GweError", "load", "build",
     "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_calibrate", "gwe_model_set_fp8_amax", "gwe_model_get_fp8_amax",
     "gwe_model_destroy",
-    "gwe_forward", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
+    "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
     "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
 
@@ -82,6 +82,8 @@ def load():
             "gwe_model_get_fp8_amax": (I, [P, P]),
             "gwe_model_destroy": (None, [P]),
             "gwe_forward": (I, [P, P, P, I64, I, I, P, I, P, P]),
+            "gwe_forward_segments": (I, [P, P, P, P, P, I, I, I, P, I, P, P]),
+            "gwe_triggers_segments": (I, [P, I, I, P, I, I, I, F, D, I64, I, P, P, I64, P, P]),
             "gwe_forward_logits": (I, [P, P, P, I, I, P, P]),
             "gwe_backward": (I, [P, I, P, P, I, I, P, P, P, P, P]),
             "gwe_triggers": (I, [P, I, I, I64, I, I, F, D, I64, I, P, I64, P, P]),
@@ -206,6 +208,47 @@ def gwe_forward(model: int, strain_H, strain_L, n_samples: int, window: int, str
     _check(load().gwe_forward(model, _dptr(strain_H), _dptr(strain_L), int(n_samples), int(window), int(stride),
                               sl.ctypes.data if sl is not None else None, ns, _dptr(out_prob), _stream(stream)),
            "gwe_forward")
+
+
+def segment_windows(seg_len, window: int, stride: int) -> np.ndarray:
+    """Windows per segment (int64), as gwe_forward_segments lays them out."""
+    return np.array([gwe_n_windows(int(n), window, stride) for n in seg_len], dtype=np.int64)
+
+
+def gwe_forward_segments(model: int, strain_H, strain_L, seg_start, seg_len, window: int, stride: int, slides,
+                         out_prob, stream=None) -> None:
+    """Ensemble forward over segments [seg_start[g], seg_start[g] + seg_len[g]) of the (device) strain;
+    out_prob [max(n_slides,1), n_models, sum of windows, window] (device)."""
+    s0 = np.ascontiguousarray(seg_start, dtype=np.int64)
+    ln = np.ascontiguousarray(seg_len, dtype=np.int64)
+    if s0.shape != ln.shape or s0.ndim != 1:
+        raise ValueError("seg_start and seg_len must be 1-D of equal length")
+    if slides is None or len(slides) == 0:
+        sl, ns = None, 0
+    else:
+        sl = np.ascontiguousarray(slides, dtype=np.int32)
+        ns = int(sl.shape[0])
+    _check(load().gwe_forward_segments(model, _dptr(strain_H), _dptr(strain_L), s0.ctypes.data, ln.ctypes.data,
+                                       int(s0.shape[0]), int(window), int(stride),
+                                       sl.ctypes.data if sl is not None else None, ns, _dptr(out_prob),
+                                       _stream(stream)), "gwe_forward_segments")
+
+
+def gwe_triggers_segments(prob, n_models: int, n_slides: int, seg_len, window: int, stride: int, height_thr: float,
+                          min_width: float, coinc: int, flags: int = GWE_TRIG_PER_MODEL, cap: int = 1 << 20,
+                          stream=None):
+    """(records of TRIGGER_DTYPE, their segment ids) over the segments of a gwe_forward_segments output."""
+    lib = load()
+    ln = np.ascontiguousarray(seg_len, dtype=np.int64)
+    out = np.zeros(max(1, int(cap)), dtype=TRIGGER_DTYPE)
+    seg = np.zeros(max(1, int(cap)), dtype=np.int32)
+    n_out = ctypes.c_int64(0)
+    st = lib.gwe_triggers_segments(_dptr(prob), int(n_models), int(n_slides), ln.ctypes.data, int(ln.shape[0]),
+                                   int(window), int(stride), float(height_thr), float(min_width), int(coinc),
+                                   int(flags), out.ctypes.data, seg.ctypes.data, int(cap), ctypes.byref(n_out),
+                                   _stream(stream))
+    _check(st, "gwe_triggers_segments")
+    return out[:n_out.value].copy(), seg[:n_out.value].copy()
 
 
 def gwe_forward_logits(model: int, x_H, x_L, batch: int, window: int, out_logit, stream=None) -> None:

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gwe_internal.h"
 
@@ -198,11 +199,18 @@ void gwe_model_destroy(gwe_model *m) {
     delete m;
 }
 
-static gwe_status dispatch_forward(gwe_model *m, const float *sH, const float *sL, int64_t n, int window, int stride,
-                                   int64_t nw, const int32_t *slides, int n_slides, float *out, bool logits,
+static gwe_status dispatch_forward(gwe_model *m, const float *sH, const float *sL, const Segments &sg, int window,
+                                   int stride, const int32_t *slides, int n_slides, float *out, bool logits,
                                    cudaStream_t st) {
-    if (m->precision == GWE_FP32) return fp32_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out, logits, st);
-    return tc_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out, logits, st);
+    if (m->precision == GWE_FP32) return fp32_forward(m, sH, sL, sg, window, stride, slides, n_slides, out, logits, st);
+    return tc_forward(m, sH, sL, sg, window, stride, slides, n_slides, out, logits, st);
+}
+
+static Segments one_segment(int64_t nw) {
+    Segments sg;
+    sg.s0.push_back(0);
+    sg.nw.push_back(nw);
+    return sg;
 }
 
 gwe_status gwe_forward(gwe_model *m, const float *sH, const float *sL, int64_t n, int window, int stride,
@@ -215,7 +223,28 @@ gwe_status gwe_forward(gwe_model *m, const float *sH, const float *sL, int64_t n
     GWE_ARG_CHECK(n >= window, "n_samples < window");
     GWE_ARG_CHECK(n_slides >= 0 && (n_slides == 0 || slides != nullptr), "slides is NULL with n_slides > 0");
     const int64_t nw = gwe_n_windows(n, window, stride);
-    return dispatch_forward(m, sH, sL, n, window, stride, nw, slides, n_slides, out_prob, false, as_stream(stream));
+    return dispatch_forward(m, sH, sL, one_segment(nw), window, stride, slides, n_slides, out_prob, false,
+                            as_stream(stream));
+}
+
+gwe_status gwe_forward_segments(gwe_model *m, const float *sH, const float *sL, const int64_t *seg_start,
+                                const int64_t *seg_len, int n_segments, int window, int stride, const int32_t *slides,
+                                int n_slides, float *out_prob, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    GWE_ARG_CHECK(sH != nullptr && sL != nullptr && out_prob != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(seg_start != nullptr && seg_len != nullptr && n_segments > 0, "no segments");
+    GWE_ARG_CHECK(window > 0 && stride > 0, "window and stride must be positive");
+    GWE_ARG_CHECK(stride <= window, "stride must not exceed window");
+    GWE_ARG_CHECK(n_slides >= 0 && (n_slides == 0 || slides != nullptr), "slides is NULL with n_slides > 0");
+    Segments sg;
+    for (int g = 0; g < n_segments; ++g) {
+        GWE_ARG_CHECK(seg_start[g] >= 0 && seg_len[g] >= 0, "negative segment start or length");
+        sg.s0.push_back(seg_start[g]);
+        sg.nw.push_back(gwe_n_windows(seg_len[g], window, stride));
+    }
+    if (sg.total_windows() == 0) return GWE_OK;
+    return dispatch_forward(m, sH, sL, sg, window, stride, slides, n_slides, out_prob, false, as_stream(stream));
 }
 
 gwe_status gwe_forward_logits(gwe_model *m, const float *xH, const float *xL, int batch, int window,
@@ -224,7 +253,7 @@ gwe_status gwe_forward_logits(gwe_model *m, const float *xH, const float *xL, in
     GWE_ARG_CHECK(m != nullptr, "model is NULL");
     GWE_ARG_CHECK(xH != nullptr && xL != nullptr && out_logit != nullptr, "NULL buffer");
     GWE_ARG_CHECK(batch > 0 && window > 0, "batch and window must be positive");
-    return dispatch_forward(m, xH, xL, (int64_t)batch * window, window, window, batch, nullptr, 0, out_logit, true,
+    return dispatch_forward(m, xH, xL, one_segment(batch), window, window, nullptr, 0, out_logit, true,
                             as_stream(stream));
 }
 
@@ -250,6 +279,25 @@ gwe_status gwe_triggers(const float *prob, int n_models, int n_slides, int64_t n
     GWE_ARG_CHECK(cap >= 0 && (cap == 0 || out != nullptr), "out is NULL with cap > 0");
     return triggers_run(prob, n_models, n_slides, n_windows, window, stride, height_thr, min_width, coinc, flags, out,
                         cap, n_out, as_stream(stream));
+}
+
+gwe_status gwe_triggers_segments(const float *prob, int n_models, int n_slides, const int64_t *seg_len,
+                                 int n_segments, int window, int stride, float height_thr, double min_width,
+                                 int64_t coinc, int flags, gwe_trigger *out, int32_t *out_segment, int64_t cap,
+                                 int64_t *n_out, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(prob != nullptr && n_out != nullptr && seg_len != nullptr, "NULL argument");
+    GWE_ARG_CHECK(n_models > 0 && n_slides >= 0 && n_segments > 0, "bad counts");
+    GWE_ARG_CHECK(window > 0 && stride > 0 && stride <= window, "bad window/stride");
+    GWE_ARG_CHECK(coinc >= 0, "coinc must be >= 0");
+    GWE_ARG_CHECK(cap >= 0 && (cap == 0 || out != nullptr), "out is NULL with cap > 0");
+    std::vector<int64_t> nw(n_segments);
+    for (int g = 0; g < n_segments; ++g) {
+        GWE_ARG_CHECK(seg_len[g] >= 0, "negative segment length");
+        nw[g] = gwe_n_windows(seg_len[g], window, stride);
+    }
+    return triggers_run_segments(prob, n_models, n_slides, nw.data(), n_segments, window, stride, height_thr,
+                                 min_width, coinc, flags, out, out_segment, cap, n_out, as_stream(stream));
 }
 
 gwe_status gwe_sync(gwe_model *m, void *stream) {

@@ -150,10 +150,14 @@ struct TcParams {
     const uint8_t *pblob;      // [n_models] parameter blocks
     uint64_t pblob_stride;
     const float *sH, *sL;
-    int64_t nw;
+    int64_t nw;                // windows of all segments
     int W, stride;
-    const int32_t *slides;     // device, n_slides (NULL: zero lag)
-    int n_slides;
+    // Segments (n_seg > 1): segment g holds windows [seg_w0[g], seg_w0[g + 1]) and starts at sample
+    // seg_s0[g] of the strain arrays; its window w is samples seg_s0[g] + (w - seg_w0[g]) * stride.
+    // n_seg == 1: one segment starting at sample 0 (tables unused).
+    int n_seg;
+    const int64_t *seg_w0;     // device [n_seg + 1]
+    const int64_t *seg_s0;     // device [n_seg]
     int n_models;
     float *out;
     int logits;
@@ -236,21 +240,41 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
     return v;
 }
 
-// job j -> (slide ordinal, model, window)
+// segment of window w (the last g with seg_w0[g] <= w; empty segments are skipped over)
+__device__ __forceinline__ int find_segment(const int64_t *w0, int n_seg, int64_t w) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w0[mid] <= w)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// job j -> (model, window): windows of all segments, model-major
 struct Job {
-    int si, m;
-    int64_t w, wl;
+    int m;
+    int64_t w;       // window index over all segments
+    int64_t wloc;    // window index within its segment
+    int64_t nws;     // windows of its segment
+    int64_t s0;      // first sample of the window in the strain arrays
 };
 __device__ __forceinline__ Job decode_job(const TcParams &p, int64_t j) {
     Job q;
     q.w = j % p.nw;
-    const int64_t r = j / p.nw;
-    q.m = p.model0 + (int)(r % p.n_models);
-    q.si = (int)(r / p.n_models);
-    int64_t k = p.slides ? (int64_t)p.slides[q.si] : 0;
-    int64_t wl = (q.w + k) % p.nw;
-    if (wl < 0) wl += p.nw;
-    q.wl = wl;
+    q.m = p.model0 + (int)(j / p.nw);
+    if (p.n_seg > 1) {
+        const int g = find_segment(p.seg_w0, p.n_seg, q.w);
+        q.wloc = q.w - p.seg_w0[g];
+        q.nws = p.seg_w0[g + 1] - p.seg_w0[g];
+        q.s0 = p.seg_s0[g] + q.wloc * (int64_t)p.stride;
+    } else {
+        q.wloc = q.w;
+        q.nws = p.nw;
+        q.s0 = q.w * (int64_t)p.stride;
+    }
     return q;
 }
 
@@ -277,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NT = p.W / kTile;
     const int L = p.L, lps = p.lps;
-    const int64_t n_jobs = (int64_t)(p.n_slides > 0 ? p.n_slides : 1) * p.n_models * p.nw;
+    const int64_t n_jobs = (int64_t)p.n_models * p.nw;
 
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
@@ -347,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 job_range(n_jobs, j0, j1);
                 for (int64_t j = j0; j < j1 && ok; ++j) {
                     const Job q = decode_job(p, j);
-                    const bool ru = p.reuse_shift > 0 && j > j0 && q.w > 0;
+                    const bool ru = p.reuse_shift > 0 && j > j0 && q.wloc > 0;
                     const uint32_t par = (uint32_t)((j - j0) & 1);
                     const uint8_t *wm = p.wimg + (uint64_t)q.m * p.wimg_stride;
                     const uint8_t *play = p.pblob + (uint64_t)q.m * p.pblob_stride + b * Sh::pb_bytes(L) + Sh::HDR_BYTES;
@@ -442,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 int64_t j0, j1;
                 job_range(n_jobs, j0, j1);
                 for (int64_t j = j0; j < j1 && ok; ++j) {
-                    const bool ru = p.reuse_shift > 0 && j > j0 && (j % p.nw) > 0;
+                    const bool ru = p.reuse_shift > 0 && j > j0 && decode_job(p, j).wloc > 0;
                     for (int tt = 0; tt < NT && ok; ++tt) {
                         const int l0 = ru ? p.lstar[tt] + 1 : 0;
                         // Ping-pong: branch 1 starts a tile once branch 0's first gate is done, so
@@ -636,8 +660,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
         job_range(n_jobs, j0, j1);
         for (int64_t j = j0; j < j1 && ok; ++j) {
             const Job jb = decode_job(p, j);
-            const bool ru = p.reuse_shift > 0 && j > j0 && jb.w > 0;                // take from the previous window
-            const bool cw = p.reuse_shift > 0 && j + 1 < j1 && jb.w + 1 < p.nw;     // give to the next one
+            const bool ru = p.reuse_shift > 0 && j > j0 && jb.wloc > 0;                 // take from the previous window
+            const bool cw = p.reuse_shift > 0 && j + 1 < j1 && jb.wloc + 1 < jb.nws;    // give to the next one
             uint8_t *ring_b = ring_c + (uint64_t)((j - j0) & 1) * p.ring_pp;
             const uint8_t *pm = p.pblob + (uint64_t)jb.m * p.pblob_stride;
             const uint8_t *pbr = pm + b * Sh::pb_bytes(L);
@@ -647,8 +671,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             const float *phd = reinterpret_cast<const float *>(pm + 2 * Sh::pb_bytes(L));
             const float *b1 = phd, *w2 = phd + HC;
             const float b2 = __ldg(phd + 2 * HC);
-            const float *sv = b ? p.sL + jb.wl * (int64_t)p.stride : p.sH + jb.w * (int64_t)p.stride;
-            float *outp = p.out + (((int64_t)jb.si * p.n_models + jb.m) * p.nw + jb.w) * (int64_t)p.W;
+            const float *sv = (b ? p.sL : p.sH) + jb.s0;
+            float *outp = p.out + ((int64_t)(jb.m - p.model0) * p.nw + jb.w) * (int64_t)p.W;
             for (int tt = 0; tt < NT && ok; ++tt) {
                 const int t0 = tt * kTile;
                 const int l0 = ru ? p.lstar[tt] + 1 : 0;
@@ -912,7 +936,8 @@ constexpr int kSlideT = 128;
 
 template <int HC>
 __global__ void __launch_bounds__(128) k_slide_head(const uint16_t *__restrict__ proj, int64_t nw, int W,
-                                                    const int32_t *__restrict__ koff, int n_slides,
+                                                    const int32_t *__restrict__ koff, int n_slides, int n_seg,
+                                                    const int64_t *__restrict__ seg_w0,
                                                     const float *__restrict__ w2, float b2, float *__restrict__ out,
                                                     int64_t slide_stride, int logits) {
     constexpr int NC = HC / 8;                    // 16-byte chunks per sample
@@ -920,6 +945,13 @@ __global__ void __launch_bounds__(128) k_slide_head(const uint16_t *__restrict__
     __shared__ uint32_t w2h[HC / 2];
     const int64_t w = blockIdx.x;
     const int t0 = blockIdx.y * kSlideT, t = threadIdx.x;
+    // the window's segment: Livingston windows wrap within it
+    int64_t sw0 = 0, snw = nw;
+    if (n_seg > 1) {
+        const int g = find_segment(seg_w0, n_seg, w);
+        sw0 = seg_w0[g];
+        snw = seg_w0[g + 1] - sw0;
+    }
     const uint64_t bstride = (uint64_t)nw * HC * W;   // elements per branch block
     const uint4 *pH = reinterpret_cast<const uint4 *>(proj + (uint64_t)w * HC * W);
     for (int c = 0; c < NC; ++c) ph_s[c * kSlideT + t] = pH[(uint64_t)c * W + t0 + t];
@@ -927,8 +959,9 @@ __global__ void __launch_bounds__(128) k_slide_head(const uint16_t *__restrict__
     __syncthreads();
     const uint32_t one2 = 0x3C003C00u;            // (1, 1) in FP16x2
     for (int si = 0; si < n_slides; ++si) {
-        int64_t wl = w + koff[si];                // koff[si] = slide offset reduced to [0, n_w)
-        if (wl >= nw) wl -= nw;
+        int64_t wl = (w - sw0 + koff[si]) % snw;   // koff[si]: slide offset in windows
+        if (wl < 0) wl += snw;
+        wl += sw0;
         const uint4 *pL = reinterpret_cast<const uint4 *>(proj + bstride + (uint64_t)wl * HC * W);
         float acc = 0.f;
 #pragma unroll 4
@@ -1005,7 +1038,7 @@ struct TcState {
     int variant = -1;            // 0: (R, S, Hc) = (32, 32, 32); 1: (64, 128, 256)
     bool f8 = false;             // FP8 E4M3 dilated convolutions (else BF16)
     std::vector<float> amax;     // FP8: calibrated max |x_l| per [model][branch][layer][channel]
-    DevBuf img, pblob, ring, zeros, err, slides, proj, koff, carry;
+    DevBuf img, pblob, ring, zeros, err, slides, proj, koff, carry, segtab;
     uint64_t img_stride = 0, pblob_stride = 0;
     int sms = 0;
     std::vector<float> b2_host;   // b_h2 per model (slide heads take it by value)
@@ -1177,10 +1210,11 @@ cudaError_t set_tc_attr() {
 }
 
 template <int R, int S, int HC, bool F8>
-gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL, int64_t nw, int W, int stride,
-                     const int32_t *slides_host, int n_slides, float *out, bool logits, cudaStream_t st) {
+gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL, const Segments &sg, int W,
+                     int stride, const int32_t *slides_host, int n_slides, float *out, bool logits, cudaStream_t st) {
     using Sh = TcShape<R, S, HC, F8>;
     const Dims &d = m->dims;
+    const int64_t nw = sg.total_windows();
     if (nw <= 0) return GWE_OK;
     uint64_t ring_rows = 0;
     for (int l = 0; l < d.L; ++l) ring_rows += (uint64_t)1 << (l % d.lps);
@@ -1191,29 +1225,41 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     plan_reuse(d, W, stride, g_reuse.load() != 0, p);
     const uint64_t n_rings = p.reuse_shift > 0 ? 2 : 1;
     GWE_CUDA_TRY(s.ring.ensure(n_rings * ring_cta * grid_max));
+    // small host tables go up with cudaMemcpyAsync from pageable memory, which stages them before
+    // returning; the slide offsets stay raw (they wrap within each window's segment on the device)
     const int32_t *dsl = nullptr;
     if (n_slides > 0) {
-        // offsets reduced to [0, n_w) on the host (pageable source: the copy is staged before return)
-        std::vector<int32_t> red(n_slides);
-        for (int i = 0; i < n_slides; ++i) {
-            int64_t k = (int64_t)slides_host[i] % nw;
-            red[i] = (int32_t)(k < 0 ? k + nw : k);
-        }
         GWE_CUDA_TRY(s.koff.ensure(sizeof(int32_t) * n_slides));
-        GWE_CUDA_TRY(cudaMemcpyAsync(s.koff.ptr, red.data(), sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
+        GWE_CUDA_TRY(cudaMemcpyAsync(s.koff.ptr, slides_host, sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
         dsl = s.koff.as<int32_t>();
+    }
+    const int n_seg = (int)sg.s0.size();
+    const int64_t *d_w0 = nullptr, *d_s0 = nullptr;
+    if (n_seg > 1) {
+        std::vector<int64_t> tab(2 * (size_t)n_seg + 1);
+        tab[0] = 0;
+        for (int g = 0; g < n_seg; ++g) {
+            tab[g + 1] = tab[g] + sg.nw[g];
+            tab[n_seg + 1 + g] = sg.s0[g];
+        }
+        GWE_CUDA_TRY(s.segtab.ensure(sizeof(int64_t) * tab.size()));
+        GWE_CUDA_TRY(cudaMemcpyAsync(s.segtab.ptr, tab.data(), sizeof(int64_t) * tab.size(), cudaMemcpyHostToDevice, st));
+        d_w0 = s.segtab.as<int64_t>();
+        d_s0 = d_w0 + n_seg + 1;
     }
     p.wimg = s.img.as<uint8_t>();
     p.wimg_stride = s.img_stride;
     p.pblob = s.pblob.as<uint8_t>();
     p.pblob_stride = s.pblob_stride;
-    p.sH = sH;
-    p.sL = sL;
     p.nw = nw;
     p.W = W;
     p.stride = stride;
-    p.slides = nullptr;
-    p.n_slides = 0;
+    p.n_seg = n_seg > 1 ? n_seg : 1;
+    p.seg_w0 = d_w0;
+    p.seg_s0 = d_s0;
+    if (n_seg == 1) sH += sg.s0[0], sL += sg.s0[0];
+    p.sH = sH;
+    p.sL = sL;
     p.n_models = d.n_models;
     p.out = out;
     p.logits = logits ? 1 : 0;
@@ -1261,9 +1307,9 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
         dim3 g2((unsigned)nw, (unsigned)(W / kSlideT));
         {
             ProfScope prof("k_slide_head", st);
-            k_slide_head<HC><<<g2, kSlideT, (HC / 8) * kSlideT * 16, st>>>(s.proj.as<uint16_t>(), nw, W, dsl, n_slides, w2, b2,
-                                                            out + (int64_t)mi * nw * W, (int64_t)d.n_models * nw * W,
-                                                            logits ? 1 : 0);
+            k_slide_head<HC><<<g2, kSlideT, (HC / 8) * kSlideT * 16, st>>>(
+                s.proj.as<uint16_t>(), nw, W, dsl, n_slides, p.n_seg, d_w0, w2, b2, out + (int64_t)mi * nw * W,
+                (int64_t)d.n_models * nw * W, logits ? 1 : 0);
             note_launch();
         }
         GWE_CUDA_TRY(cudaGetLastError());
@@ -1446,13 +1492,13 @@ void tc_release(gwe_model *m) {
     s->proj.release();
     s->koff.release();
     s->carry.release();
+    s->segtab.release();
     delete s;
     m->tc = nullptr;
 }
 
-gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int W, int stride,
-                        int64_t nw, const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st) {
-    (void)n_samples;
+gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, const Segments &sg, int W, int stride,
+                      const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st) {
     TcState *s = reinterpret_cast<TcState *>(m->tc);
     if (!s || s->variant < 0) {
         set_error("tensor-core path not prepared");
@@ -1464,7 +1510,7 @@ gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_
     }
     return tc_dispatch(*s, [&](auto t) {
         using T = decltype(t);
-        return launch_tc<T::R, T::S, T::HC, T::F8>(m, *s, sH, sL, nw, W, stride, slides, n_slides, out, logits, st);
+        return launch_tc<T::R, T::S, T::HC, T::F8>(m, *s, sH, sL, sg, W, stride, slides, n_slides, out, logits, st);
     });
 }
 
@@ -1569,8 +1615,9 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.nw = nw;
     p.W = W;
     p.stride = stride;
-    p.slides = nullptr;
-    p.n_slides = 0;
+    p.n_seg = 1;
+    p.seg_w0 = nullptr;
+    p.seg_s0 = nullptr;
     p.n_models = d.n_models;
     p.out = out;
     p.logits = 0;

@@ -380,9 +380,12 @@ gwe_status fp32_prepare(gwe_model *m, const float *hb) {
     return GWE_OK;
 }
 
-gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int W, int stride,
-                        int64_t nw, const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st) {
-    (void)n_samples;
+namespace {
+
+// one segment of nw windows; series (slide, model) of out start every out_nw windows
+gwe_status fp32_forward_segment(gwe_model *m, const float *sH, const float *sL, int W, int stride, int64_t nw,
+                                const int32_t *slides, int n_slides, float *out, int64_t out_nw, bool logits,
+                                cudaStream_t st) {
     const Dims &d = m->dims;
     const Variant v = variant_of(d);
     if (v == kNone) {
@@ -430,7 +433,7 @@ gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
             const float *b2 = w2 + Hc;
             for (int si = 0; si < ns; ++si) {
                 const int64_t k = (n_slides > 0) ? slides[si] : 0;
-                float *o = out + ((int64_t)si * d.n_models + mi) * nw * W;
+                float *o = out + ((int64_t)si * d.n_models + mi) * out_nw * W;
                 const int64_t nrows = (int64_t)C * W;
                 const int warps = 8;
                 const int64_t blocks = (nrows + warps - 1) / warps;
@@ -440,6 +443,23 @@ gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t 
             }
             GWE_CUDA_TRY(cudaGetLastError());
         }
+    }
+    return GWE_OK;
+}
+
+}  // namespace
+
+gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, const Segments &sg, int W, int stride,
+                        const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st) {
+    const int64_t nw_all = sg.total_windows();
+    int64_t wo = 0;
+    for (size_t g = 0; g < sg.s0.size(); ++g) {
+        if (sg.nw[g] > 0) {
+            gwe_status r = fp32_forward_segment(m, sH + sg.s0[g], sL + sg.s0[g], W, stride, sg.nw[g], slides, n_slides,
+                                                out + wo * W, nw_all, logits, st);
+            if (r != GWE_OK) return r;
+        }
+        wo += sg.nw[g];
     }
     return GWE_OK;
 }

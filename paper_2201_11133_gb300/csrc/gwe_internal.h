@@ -113,12 +113,22 @@ struct gwe_model {
 
 namespace gwe {
 
+// Science segments of one forward call: segment g starts at sample s0[g] of the strain arrays and
+// holds nw[g] windows; the outputs of its windows follow those of segments 0 .. g-1.
+struct Segments {
+    std::vector<int64_t> s0, nw;
+    int64_t total_windows() const {
+        int64_t t = 0;
+        for (int64_t v : nw) t += v;
+        return t;
+    }
+};
+
 // fp32_path.cu
 gwe_status fp32_prepare(gwe_model *m, const float *host_blob);
 // Forward of all models over one segment; writes probabilities (or logits).
-gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
-                        int stride, int64_t n_windows, const int32_t *slides, int n_slides, float *out,
-                        bool logits, cudaStream_t st);
+gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, const Segments &sg, int window,
+                        int stride, const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st);
 
 // Backward pass of one ensemble member (FP32, per-stack recomputation); grad_w is overwritten.
 gwe_status fp32_backward(gwe_model *m, int model_index, const float *xH, const float *xL, int batch, int W,
@@ -141,9 +151,8 @@ gwe_status tc_calibrate(gwe_model *m, const float *sH, const float *sL, int64_t 
 gwe_status tc_set_amax(gwe_model *m, const float *host_amax);   // [n_models][2][L][R]
 gwe_status tc_get_amax(gwe_model *m, float *host_amax);
 void tc_release(gwe_model *m);
-gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window,
-                        int stride, int64_t n_windows, const int32_t *slides, int n_slides, float *out,
-                        bool logits, cudaStream_t st);
+gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, const Segments &sg, int window, int stride,
+                      const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st);
 bool tc_supported(const Dims &d);
 
 // whiten.cu: Welch PSD (FP64 accumulation) and spectral whitening of one detector's strain
@@ -153,5 +162,10 @@ gwe_status whiten_run(const float *x, int64_t n, double fs, int seg, float *out,
 gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,
                         int stride, float thr, double min_width, int64_t coinc, int flags, gwe_trigger *out,
                         int64_t cap, int64_t *n_out, cudaStream_t st);
+// the same over the segments of a gwe_forward_segments output (segment g: seg_nw[g] windows);
+// out_seg (optional) receives each record's segment
+gwe_status triggers_run_segments(const float *prob, int n_models, int n_slides, const int64_t *seg_nw, int n_seg,
+                                 int W, int stride, float thr, double min_width, int64_t coinc, int flags,
+                                 gwe_trigger *out, int32_t *out_seg, int64_t cap, int64_t *n_out, cudaStream_t st);
 
 }  // namespace gwe

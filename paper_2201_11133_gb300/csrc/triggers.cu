@@ -47,12 +47,13 @@ struct Series {
 struct Geo {
     const float *prob;
     int64_t nw;
+    int64_t series_nw;   // windows between the starts of consecutive series
     int W, stride;
     int64_t n;           // stitched length (same for every series)
     int64_t nblk;        // statistics blocks per series
     __device__ __forceinline__ Series series(int s) const {
         Series v;
-        v.base = prob + (int64_t)s * nw * W;
+        v.base = prob + (int64_t)s * series_nw * W;
         v.n = n; v.W = W; v.stride = stride;
         return v;
     }
@@ -383,17 +384,19 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t nw, int W, int stride, float thr,
-                        double min_width, int64_t coinc, int flags, gwe_trigger *out, int64_t cap, int64_t *n_out,
-                        cudaStream_t st) {
+namespace {
+
+// all records of one segment's (slide, model) series, appended to recs
+gwe_status triggers_collect(const float *prob, int n_models, int n_slides, int64_t nw, int64_t series_nw, int W,
+                            int stride, float thr, double min_width, int64_t coinc, int flags,
+                            std::vector<gwe_trigger> &recs, cudaStream_t st) {
     TrigWs &ws = trig_ws();
     std::lock_guard<std::mutex> lock(ws.mu);
     const int ns = n_slides > 0 ? n_slides : 1;
     const int n_series = ns * n_models;
-    *n_out = 0;
     if (nw <= 0) return GWE_OK;
     Geo g;
-    g.prob = prob; g.nw = nw; g.W = W; g.stride = stride;
+    g.prob = prob; g.nw = nw; g.series_nw = series_nw; g.W = W; g.stride = stride;
     g.n = (nw - 1) * (int64_t)stride + W;
     g.nblk = (g.n + kBS - 1) / kBS;
     const int64_t nstat = g.nblk * n_series;
@@ -417,7 +420,6 @@ gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t n
     int64_t ncand = 0;
     GWE_CUDA_TRY(cudaMemcpyAsync(&ncand, ws.offsets.as<int64_t>() + ncnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GWE_CUDA_TRY(cudaStreamSynchronize(st));
-    std::vector<gwe_trigger> recs;
     if (ncand > 0) {
         GWE_CUDA_TRY(ws.cand_idx.ensure(ncand * sizeof(int64_t)));
         GWE_CUDA_TRY(ws.cand_ser.ensure(ncand * sizeof(int)));
@@ -495,14 +497,51 @@ gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t n
         }
     }
     GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
+gwe_status copy_out(const std::vector<gwe_trigger> &recs, const std::vector<int32_t> *segs, gwe_trigger *out,
+                    int32_t *out_seg, int64_t cap, int64_t *n_out) {
     *n_out = (int64_t)recs.size();
-    const int64_t nw_out = std::min<int64_t>(cap, (int64_t)recs.size());
-    if (nw_out > 0 && out) std::copy(recs.begin(), recs.begin() + nw_out, out);
+    const int64_t k = std::min<int64_t>(cap, (int64_t)recs.size());
+    if (k > 0 && out) std::copy(recs.begin(), recs.begin() + k, out);
+    if (k > 0 && out_seg && segs) std::copy(segs->begin(), segs->begin() + k, out_seg);
     if ((int64_t)recs.size() > cap) {
         set_error("gwe_triggers: output capacity too small");
         return GWE_ERR_CAPACITY;
     }
     return GWE_OK;
+}
+
+}  // namespace
+
+gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t nw, int W, int stride, float thr,
+                        double min_width, int64_t coinc, int flags, gwe_trigger *out, int64_t cap, int64_t *n_out,
+                        cudaStream_t st) {
+    *n_out = 0;
+    std::vector<gwe_trigger> recs;
+    gwe_status r = triggers_collect(prob, n_models, n_slides, nw, nw, W, stride, thr, min_width, coinc, flags, recs, st);
+    if (r != GWE_OK) return r;
+    return copy_out(recs, nullptr, out, nullptr, cap, n_out);
+}
+
+gwe_status triggers_run_segments(const float *prob, int n_models, int n_slides, const int64_t *seg_nw, int n_seg,
+                                 int W, int stride, float thr, double min_width, int64_t coinc, int flags,
+                                 gwe_trigger *out, int32_t *out_seg, int64_t cap, int64_t *n_out, cudaStream_t st) {
+    *n_out = 0;
+    int64_t nw_all = 0;
+    for (int g = 0; g < n_seg; ++g) nw_all += seg_nw[g];
+    std::vector<gwe_trigger> recs;
+    std::vector<int32_t> segs;
+    int64_t wo = 0;
+    for (int g = 0; g < n_seg; ++g) {
+        gwe_status r = triggers_collect(prob + wo * W, n_models, n_slides, seg_nw[g], nw_all, W, stride, thr,
+                                        min_width, coinc, flags, recs, st);
+        if (r != GWE_OK) return r;
+        segs.resize(recs.size(), g);
+        wo += seg_nw[g];
+    }
+    return copy_out(recs, &segs, out, out_seg, cap, n_out);
 }
 
 }  // namespace gwe
