@@ -141,7 +141,8 @@ enum {
     B_PAIR = 23,
     B_FIN = 24,        // [2]
     B_BIAS = 26,       // [2 branches][4 slots: b_conv x2, b_res x2]
-    B_GO = 34          // branch 1 may start its tile (branch 0's first gate is done)
+    B_GO = 34,         // branch 1 may start its tile (branch 0's first gate is done)
+    B_SKIP = 35        // [2] the skip MMAs of a layer completed
 };
 
 struct TcParams {
@@ -314,6 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             mbar_init(&bar[B_CONV + b], 1);
             mbar_init(&bar[B_ZREADY + b], 8);
             mbar_init(&bar[B_RS + b], 1);
+            mbar_init(&bar[B_SKIP + b], 1);
             mbar_init(&bar[B_HREADY + b], 8);
             mbar_init(&bar[B_WG + b], 8);
             mbar_init(&bar[B_FIN + b], 1);
@@ -478,9 +480,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         for (int l = l0; l < L; ++l) {
                             const int d = 1 << (l % lps);
                             const int n = d < kTile ? d : kTile;
-                            ok = mbar_wait(&bar[B_XREADY + b], ph_x & 1, abort_flag, p.err, 10, p.wait_ns) &&
-                                 mbar_wait(&bar[B_LAG + b], ph_lag & 1, abort_flag, p.err, 11, p.wait_ns) &&
-                                 mbar_wait(&bar[B_WFULL + 2 * b], it[0] & 1, abort_flag, p.err, 12, p.wait_ns);
+                            // the lagged rows and the weights land while the epilogue is still in the
+                            // residual of the previous layer: test them first, so that only the MMA
+                            // issue follows the epilogue's hand-off
+                            ok = mbar_wait(&bar[B_LAG + b], ph_lag & 1, abort_flag, p.err, 11, p.wait_ns) &&
+                                 mbar_wait(&bar[B_WFULL + 2 * b], it[0] & 1, abort_flag, p.err, 12, p.wait_ns) &&
+                                 mbar_wait(&bar[B_XREADY + b], ph_x & 1, abort_flag, p.err, 10, p.wait_ns);
                             if (!ok) break;
                             ++ph_x;
                             ++ph_lag;
@@ -503,8 +508,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             mma_commit(&bar[B_CONV + b]);
                             mma_commit(&bar[B_WEMPTY + 2 * b]);
                             ++it[0];
-                            ok = mbar_wait(&bar[B_ZREADY + b], ph_z & 1, abort_flag, p.err, 13, p.wait_ns) &&
-                                 mbar_wait(&bar[B_WFULL + 2 * b + 1], it[1] & 1, abort_flag, p.err, 14, p.wait_ns);
+                            ok = mbar_wait(&bar[B_WFULL + 2 * b + 1], it[1] & 1, abort_flag, p.err, 14, p.wait_ns) &&
+                                 mbar_wait(&bar[B_ZREADY + b], ph_z & 1, abort_flag, p.err, 13, p.wait_ns);
                             if (!ok) break;
                             ++ph_z;
                             if (b == 0 && l == l0) mbar_arrive(&bar[B_GO]);
@@ -514,11 +519,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
 #pragma unroll
                             for (int ks = 0; ks < Sh::KR; ++ks)
                                 mma_f16_ta(dcol + R, dcol + zcol(ks), b_res0 + ks * (2 * R), ID_RES, ks > 0 ? 1u : 0u);
+                            // the residual needs r only: release it before the skip MMAs (they run
+                            // while the epilogue updates x; this thread's MMAs execute in issue order,
+                            // so the next conv cannot overwrite z before the skip MMAs have read it)
+                            mma_commit(&bar[B_RS + b]);
                             mma_f16_ta(dcol + 2 * R, dcol + zcol(0), b_skip0, ID_SKIP, l > 0 ? 1u : 0u);
 #pragma unroll
                             for (int ks = 1; ks < Sh::KR; ++ks)
                                 mma_f16_ta(dcol + 2 * R, dcol + zcol(ks), b_skip0 + ks * (2 * S), ID_SKIP, 1u);
-                            mma_commit(&bar[B_RS + b]);
+                            mma_commit(&bar[B_SKIP + b]);
                             mma_commit(&bar[B_WEMPTY + 2 * b + 1]);
                             ++it[1];
                         }
@@ -728,31 +737,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         !warp_wait(B_BIAS + 4 * b + (g & 1), (g >> 1) & 1, 36)) { ok = false; break; }
                     ++ph_conv;
                     tc_fence_after();
-                    // lag history of layer l for the following tiles (and, when the next window takes
-                    // over layers, for its full tiles): rows t0+r, r >= 128 - n
-                    if ((tt + 1 < NT || cw) && r >= kTile - n) {
-                        const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
-                        uint8_t *dst = ring_b + roff * Sh::XROW + (uint64_t)((t0 + r) & (d - 1)) * 16;
-                        if constexpr (F8) {
-                            // the quantised row is still in the staging buffer (rewritten after the rs MMA)
-#pragma unroll
-                            for (int c = 0; c < RH / 16; ++c) {
-                                const int ck = hf * (RH / 16) + c;
-                                *reinterpret_cast<uint4 *>(dst + (uint64_t)ck * d * 16) =
-                                    lds128(st + ck * Sh::STAGE_LBO + (kTile + r) * 16);
-                            }
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < RH / 8; ++c) {
-                                uint4 v;
-                                v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
-                                v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
-                                v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
-                                v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
-                                *reinterpret_cast<uint4 *>(dst + (uint64_t)(hf * (RH / 8) + c) * d * 16) = v;
-                            }
-                        }
-                    }
                     // gate: z = tanh(f + b_f) * (0.5 tanh(g/2 + b_g/2) + 0.5), FP16x2
                     {
                         const uint32_t bslot = sb + (g & 1) * Sh::CB_BYTES;
@@ -777,6 +761,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     }
                     tc_fence_before();
                     warp_arrive(B_ZREADY + b);
+                    // lag history of layer l for the following tiles (and, when the next window takes
+                    // over layers, for its full tiles): rows t0+r, r >= 128 - n.  Written after the
+                    // gate's hand-off, while the res MMAs run (x still holds x_l, and the FP8 staging
+                    // row is rewritten only by the residual below), so that the warps holding the
+                    // last rows do not delay the gate.
+                    if ((tt + 1 < NT || cw) && r >= kTile - n) {
+                        const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
+                        uint8_t *dst = ring_b + roff * Sh::XROW + (uint64_t)((t0 + r) & (d - 1)) * 16;
+                        if constexpr (F8) {
+                            // the quantised row is still in the staging buffer (rewritten after the rs MMA)
+#pragma unroll
+                            for (int c = 0; c < RH / 16; ++c) {
+                                const int ck = hf * (RH / 16) + c;
+                                *reinterpret_cast<uint4 *>(dst + (uint64_t)ck * d * 16) =
+                                    lds128(st + ck * Sh::STAGE_LBO + (kTile + r) * 16);
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < RH / 8; ++c) {
+                                uint4 v;
+                                v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
+                                v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
+                                v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
+                                v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+                                *reinterpret_cast<uint4 *>(dst + (uint64_t)(hf * (RH / 8) + c) * d * 16) = v;
+                            }
+                        }
+                    }
                     if (!warp_wait(B_RS + b, ph_rs & 1, 31) ||
                         !warp_wait(B_BIAS + 4 * b + 2 + (g & 1), (g >> 1) & 1, 37)) { ok = false; break; }
                     ++ph_rs;
@@ -806,6 +818,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         warp_arrive(B_XREADY + b);
                         if (l == lgive) {
                             // x_{l+1} and the skip sum of layers <= l for the next window's tile tt - shift
+                            // (the skip MMAs of layer l complete after r is released)
+                            if (!warp_wait(B_SKIP + b, g & 1, 38)) { ok = false; break; }
+                            tc_fence_after();
                             float4 *cd = carry_t + (uint64_t)(tt - p.reuse_shift) * ((RH + SH) / 4) * 256;
 #pragma unroll
                             for (int k4 = 0; k4 < RH / 4; ++k4)
@@ -825,6 +840,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     }
                 }
                 if (!ok) break;
+                // the last layer's skip MMAs complete before the skip sum is read for the head
+                if (!warp_wait(B_SKIP + b, (g - 1) & 1, 39)) { ok = false; break; }
+                tc_fence_after();
                 // history rows written with ordinary stores are read by bulk copies of later tiles
                 fence_proxy_async_global();
                 // every row's history copy has read the staging buffer before it becomes the head operand
