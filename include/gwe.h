@@ -282,6 +282,62 @@ gwe_status gwe_set_cross_window_reuse(int enable);
 gwe_status gwe_forward_static(gwe_model *model, const float *strain_H, const float *strain_L, int64_t n_samples,
                               int window, int stride, float *out_prob, int *status, void *stream);
 
+/* Opaque forward plan (gwe_plan_create). */
+typedef struct gwe_plan gwe_plan;
+
+/* Flags of gwe_plan_create. */
+#define GWE_PLAN_AUTOTUNE 1   /* choose the slide heads' launch shape by timing the candidates */
+
+/*
+ * Forward plan: the batched ensemble forward over many science segments of
+ * uneven length times many time-slide offsets (section "Statistical
+ * Analysis": background from time-shifted Livingston data; the same
+ * computation as gwe_forward_segments with these arguments), prepared once and
+ * recorded into one CUDA graph, so that every execution is a single graph
+ * launch of the persistent tensor-core kernel(s) and the slide heads.
+ *   model            GWE_BF16 or GWE_FP8 handle (GWE_ERR_UNSUPPORTED otherwise).
+ *   strain_H/L, seg_start, seg_len, n_segments, window, stride, slides,
+ *   n_slides, out_prob   as for gwe_forward_segments.  The device buffers are
+ *                    bound at creation: every execution reads the strain
+ *                    buffers as they are then and overwrites out_prob; refill
+ *                    the strain in place between executions.  window must be a
+ *                    multiple of 128.
+ *   flags            0 or GWE_PLAN_AUTOTUNE.  With GWE_PLAN_AUTOTUNE and
+ *                    n_slides > 0 the plan times every candidate launch shape of
+ *                    the slide heads (64, 128 or 256 samples per block; all
+ *                    offsets per block or a quarter of them) on these buffers
+ *                    with CUDA events and keeps the fastest; the choice is
+ *                    cached per geometry for the process.  Without it, 128
+ *                    samples and all offsets per block.
+ *   stream           creation runs (and synchronises) on this stream; the graph
+ *                    is recorded on a private stream.
+ *   out              receives the plan.
+ * The plan owns its lag rings, carry buffer, slide projections (2 x windows x
+ * Hc x window FP16) and tables; the handle's weights are used in place (so
+ * gwe_model_set_weights and FP8 calibration take effect in later executions).
+ * Executions of one plan, and other calls on the same handle, must not overlap
+ * on the GPU.  A device-side wait that times out is reported by gwe_sync on
+ * the handle.
+ */
+gwe_status gwe_plan_create(gwe_model *model, const float *strain_H, const float *strain_L, const int64_t *seg_start,
+                           const int64_t *seg_len, int n_segments, int window, int stride, const int32_t *slides,
+                           int n_slides, float *out_prob, int flags, void *stream, gwe_plan **out);
+
+/* Launch the plan's graph on `stream` (asynchronous). */
+gwe_status gwe_plan_execute(gwe_plan *plan, void *stream);
+
+/*
+ * The launch shape the plan uses: samples per block and offsets per block of
+ * the slide heads, the number of kernels in its graph, and (after autotuning)
+ * the time of one model's slide heads with the chosen shape and with the
+ * default shape, in milliseconds (0 when not tuned).  NULL outputs are skipped.
+ */
+gwe_status gwe_plan_shape(const gwe_plan *plan, int *slide_tile, int *slides_per_block, int *n_kernels,
+                          double *tuned_ms, double *default_ms);
+
+/* Release a plan (after its executions have completed). */
+void gwe_plan_destroy(gwe_plan *plan);
+
 /* Flags of gwe_triggers. */
 #define GWE_TRIG_PER_MODEL 1   /* also return every model's kept peaks (model >= 0) */
 

@@ -22,11 +22,13 @@ __all__ = [
     "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_calibrate", "gwe_model_set_fp8_amax", "gwe_model_get_fp8_amax",
     "gwe_model_destroy",
     "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
-    "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
+    "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static",
+    "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
 
 GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
 GWE_TRIG_PER_MODEL = 1
+GWE_PLAN_AUTOTUNE = 1
 _STATUS = {0: "GWE_OK", 1: "GWE_ERR_ARG", 2: "GWE_ERR_CUDA", 3: "GWE_ERR_OOM", 4: "GWE_ERR_TIMEOUT",
            5: "GWE_ERR_UNSUPPORTED", 6: "GWE_ERR_CAPACITY"}
 
@@ -92,6 +94,10 @@ def load():
             "gwe_set_cross_window_reuse": (I, [I]),
             "gwe_debug_config": (I, [I, D]),
             "gwe_forward_static": (I, [P, P, P, I64, I, I, P, P, P]),
+            "gwe_plan_create": (I, [P, P, P, P, P, I, I, I, P, I, P, I, P, P]),
+            "gwe_plan_execute": (I, [P, P]),
+            "gwe_plan_shape": (I, [P, P, P, P, P, P]),
+            "gwe_plan_destroy": (None, [P]),
             "gwe_profile_enable": (I, [I]),
             "gwe_profile_read": (I, [I, P, I, P, P]),
             "gwe_last_error": (ctypes.c_char_p, []),
@@ -284,6 +290,46 @@ def gwe_forward_static(model: int, strain_H, strain_L, n_samples: int, window: i
     _check(load().gwe_forward_static(model, _dptr(strain_H), _dptr(strain_L), int(n_samples), int(window),
                                      int(stride), _dptr(out_prob), _dptr(status), _stream(stream)),
            "gwe_forward_static")
+
+
+def gwe_plan_create(model: int, strain_H, strain_L, seg_start, seg_len, window: int, stride: int, slides, out_prob,
+                    flags: int = GWE_PLAN_AUTOTUNE, stream=None) -> int:
+    """Forward plan over segments x slides recorded into one CUDA graph (see include/gwe.h); returns the handle."""
+    s0 = np.ascontiguousarray(seg_start, dtype=np.int64)
+    ln = np.ascontiguousarray(seg_len, dtype=np.int64)
+    if s0.shape != ln.shape or s0.ndim != 1:
+        raise ValueError("seg_start and seg_len must be 1-D of equal length")
+    if slides is None or len(slides) == 0:
+        sl, ns = None, 0
+    else:
+        sl = np.ascontiguousarray(slides, dtype=np.int32)
+        ns = int(sl.shape[0])
+    h = ctypes.c_void_p()
+    _check(load().gwe_plan_create(model, _dptr(strain_H), _dptr(strain_L), s0.ctypes.data, ln.ctypes.data,
+                                  int(s0.shape[0]), int(window), int(stride),
+                                  sl.ctypes.data if sl is not None else None, ns, _dptr(out_prob), int(flags),
+                                  _stream(stream), ctypes.byref(h)), "gwe_plan_create")
+    return h.value
+
+
+def gwe_plan_execute(plan: int, stream=None) -> None:
+    """One launch of the plan's CUDA graph (asynchronous)."""
+    _check(load().gwe_plan_execute(plan, _stream(stream)), "gwe_plan_execute")
+
+
+def gwe_plan_shape(plan: int) -> dict:
+    """Launch shape of a plan: slide-head samples and offsets per block, kernels in the graph, tuning times (ms)."""
+    tile, spb, nk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    t_ms, d_ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().gwe_plan_shape(plan, ctypes.byref(tile), ctypes.byref(spb), ctypes.byref(nk), ctypes.byref(t_ms),
+                                 ctypes.byref(d_ms)), "gwe_plan_shape")
+    return {"slide_tile": tile.value, "slides_per_block": spb.value, "n_kernels": nk.value,
+            "tuned_ms": t_ms.value, "default_ms": d_ms.value}
+
+
+def gwe_plan_destroy(plan: int) -> None:
+    if plan:
+        load().gwe_plan_destroy(plan)
 
 
 def gwe_set_cross_window_reuse(enable: bool) -> None:

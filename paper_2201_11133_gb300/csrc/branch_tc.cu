@@ -43,7 +43,9 @@
 #include <cmath>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -948,21 +950,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
 // (the head's first convolution is linear in [s_H ; s_L], so the branch pass runs once per window
 // and a slide costs 3 Hc operations per sample).  FP16x2 ReLU-add and products with FP16 partial
 // sums over 16 channels, FP32 across partials, FP32 logit and sigmoid.
-// Grid: x = window (fast, so that concurrent blocks share the Livingston tiles in L2), y = 128-sample
-// tile; 128 threads, thread = sample; the block's Hanford tile is staged in shared memory.
-constexpr int kSlideT = 128;
-
-template <int HC>
-__global__ void __launch_bounds__(128) k_slide_head(const uint16_t *__restrict__ proj, int64_t nw, int W,
-                                                    const int32_t *__restrict__ koff, int n_slides, int n_seg,
-                                                    const int64_t *__restrict__ seg_w0,
-                                                    const float *__restrict__ w2, float b2, float *__restrict__ out,
-                                                    int64_t slide_stride, int logits) {
+// Grid: x = window (fast, so that concurrent blocks share the Livingston tiles in L2), y = T-sample
+// tile, z = group of `spb` offsets; T threads, thread = sample; the block's Hanford tile is staged
+// in shared memory.  T and spb are the launch shape the plan autotuner chooses.
+template <int HC, int T>
+__global__ void __launch_bounds__(T) k_slide_head(const uint16_t *__restrict__ proj, int64_t nw, int W,
+                                                  const int32_t *__restrict__ koff, int n_slides, int spb, int n_seg,
+                                                  const int64_t *__restrict__ seg_w0,
+                                                  const float *__restrict__ w2, float b2, float *__restrict__ out,
+                                                  int64_t slide_stride, int logits) {
     constexpr int NC = HC / 8;                    // 16-byte chunks per sample
-    extern __shared__ uint4 ph_s[];               // [NC][128]
+    extern __shared__ uint4 ph_s[];               // [NC][T]
     __shared__ uint32_t w2h[HC / 2];
     const int64_t w = blockIdx.x;
-    const int t0 = blockIdx.y * kSlideT, t = threadIdx.x;
+    const int t0 = blockIdx.y * T, t = threadIdx.x;
+    const int s_begin = blockIdx.z * spb;
+    const int s_end = min(n_slides, s_begin + spb);
     // the window's segment: Livingston windows wrap within it
     int64_t sw0 = 0, snw = nw;
     if (n_seg > 1) {
@@ -972,11 +975,11 @@ __global__ void __launch_bounds__(128) k_slide_head(const uint16_t *__restrict__
     }
     const uint64_t bstride = (uint64_t)nw * HC * W;   // elements per branch block
     const uint4 *pH = reinterpret_cast<const uint4 *>(proj + (uint64_t)w * HC * W);
-    for (int c = 0; c < NC; ++c) ph_s[c * kSlideT + t] = pH[(uint64_t)c * W + t0 + t];
-    for (int j = t; j < HC / 2; j += kSlideT) w2h[j] = pack_h2(w2[2 * j], w2[2 * j + 1]);
+    for (int c = 0; c < NC; ++c) ph_s[c * T + t] = pH[(uint64_t)c * W + t0 + t];
+    for (int j = t; j < HC / 2; j += T) w2h[j] = pack_h2(w2[2 * j], w2[2 * j + 1]);
     __syncthreads();
     const uint32_t one2 = 0x3C003C00u;            // (1, 1) in FP16x2
-    for (int si = 0; si < n_slides; ++si) {
+    for (int si = s_begin; si < s_end; ++si) {
         int64_t wl = (w - sw0 + koff[si]) % snw;   // koff[si]: slide offset in windows
         if (wl < 0) wl += snw;
         wl += sw0;
@@ -987,7 +990,7 @@ __global__ void __launch_bounds__(128) k_slide_head(const uint16_t *__restrict__
             uint32_t hacc = 0u;
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-                const uint4 a = ph_s[(c + cc) * kSlideT + t];
+                const uint4 a = ph_s[(c + cc) * T + t];
                 const uint4 l = __ldg(pL + (uint64_t)(c + cc) * W + t0 + t);
                 const uint32_t av[4] = {a.x, a.y, a.z, a.w}, lv[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
@@ -1052,11 +1055,34 @@ void plan_reuse(const Dims &d, int W, int stride, bool enable, TcParams &p) {
     if (any) p.reuse_shift = shift;
 }
 
+// Device buffers of one forward geometry besides the handle's weights: the lag rings and the carry
+// buffer of the persistent kernel, the slide projections and the segment / offset tables.  The
+// handle keeps one set for its own calls; a plan owns another, so that later calls on the handle
+// can neither move nor overwrite what its captured graph points at.
+struct TcWork {
+    DevBuf ring, carry, proj, koff, segtab;
+    void release() {
+        ring.release();
+        carry.release();
+        proj.release();
+        koff.release();
+        segtab.release();
+    }
+};
+
+// Launch shape of the slide heads: samples per block (64, 128 or 256) and offsets per block
+// (0: all offsets in one block).
+struct SlideShape {
+    int tile = 128;
+    int spb = 0;
+};
+
 struct TcState {
     int variant = -1;            // 0: (R, S, Hc) = (32, 32, 32); 1: (64, 128, 256)
     bool f8 = false;             // FP8 E4M3 dilated convolutions (else BF16)
     std::vector<float> amax;     // FP8: calibrated max |x_l| per [model][branch][layer][channel]
-    DevBuf img, pblob, ring, zeros, err, slides, proj, koff, carry, segtab;
+    DevBuf img, pblob, zeros, err, slides;
+    TcWork work;                 // buffers of the handle's own forward calls
     uint64_t img_stride = 0, pblob_stride = 0;
     int sms = 0;
     std::vector<float> b2_host;   // b_h2 per model (slide heads take it by value)
@@ -1223,33 +1249,56 @@ cudaError_t set_tc_attr() {
     cudaError_t e = cudaFuncSetAttribute(k_branch_tc<R, S, HC, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)TcShape<R, S, HC, F8>::SMEM);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_slide_head<HC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((HC / 8) * kSlideT * 16));
+    e = cudaFuncSetAttribute(k_slide_head<HC, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (HC / 8) * 64 * 16);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_slide_head<HC, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (HC / 8) * 128 * 16);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_slide_head<HC, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (HC / 8) * 256 * 16);
 }
 
+// Everything one forward needs on the device, prepared by setup_tc (buffers grown, tables
+// uploaded) and launched by issue_tc, which only enqueues kernels (so that it can be captured
+// into a CUDA graph).
+struct TcLaunch {
+    TcParams p;
+    int grid_max = 0;            // CTAs of the zero-lag launch (all models)
+    int grid_slide = 0;          // CTAs of the per-model projection launches
+    int64_t nw = 0;
+    int n_slides = 0;
+    const int32_t *dsl = nullptr;
+    const int64_t *d_w0 = nullptr;
+    float *out = nullptr;
+    bool logits = false;
+    uint16_t *proj = nullptr;
+    SlideShape shape;
+};
+
 template <int R, int S, int HC, bool F8>
-gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL, const Segments &sg, int W,
-                     int stride, const int32_t *slides_host, int n_slides, float *out, bool logits, cudaStream_t st) {
+gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const float *sL, const Segments &sg,
+                    int W, int stride, const int32_t *slides_host, int n_slides, float *out, bool logits,
+                    cudaStream_t st, TcLaunch &L) {
     using Sh = TcShape<R, S, HC, F8>;
     const Dims &d = m->dims;
     const int64_t nw = sg.total_windows();
+    L.nw = nw;
     if (nw <= 0) return GWE_OK;
     uint64_t ring_rows = 0;
     for (int l = 0; l < d.L; ++l) ring_rows += (uint64_t)1 << (l % d.lps);
     const uint64_t ring_cta = (2 * ring_rows * Sh::XROW + 255) & ~uint64_t(255);
     const int64_t max_jobs = (int64_t)d.n_models * nw;
     const int grid_max = (int)std::min<int64_t>(s.sms, max_jobs);
-    TcParams p;
+    TcParams &p = L.p;
     plan_reuse(d, W, stride, g_reuse.load() != 0, p);
     const uint64_t n_rings = p.reuse_shift > 0 ? 2 : 1;
-    GWE_CUDA_TRY(s.ring.ensure(n_rings * ring_cta * grid_max));
+    GWE_CUDA_TRY(wk.ring.ensure(n_rings * ring_cta * grid_max));
     // small host tables go up with cudaMemcpyAsync from pageable memory, which stages them before
     // returning; the slide offsets stay raw (they wrap within each window's segment on the device)
     const int32_t *dsl = nullptr;
     if (n_slides > 0) {
-        GWE_CUDA_TRY(s.koff.ensure(sizeof(int32_t) * n_slides));
-        GWE_CUDA_TRY(cudaMemcpyAsync(s.koff.ptr, slides_host, sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
-        dsl = s.koff.as<int32_t>();
+        GWE_CUDA_TRY(wk.koff.ensure(sizeof(int32_t) * n_slides));
+        GWE_CUDA_TRY(cudaMemcpyAsync(wk.koff.ptr, slides_host, sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
+        dsl = wk.koff.as<int32_t>();
     }
     const int n_seg = (int)sg.s0.size();
     const int64_t *d_w0 = nullptr, *d_s0 = nullptr;
@@ -1260,9 +1309,9 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
             tab[g + 1] = tab[g] + sg.nw[g];
             tab[n_seg + 1 + g] = sg.s0[g];
         }
-        GWE_CUDA_TRY(s.segtab.ensure(sizeof(int64_t) * tab.size()));
-        GWE_CUDA_TRY(cudaMemcpyAsync(s.segtab.ptr, tab.data(), sizeof(int64_t) * tab.size(), cudaMemcpyHostToDevice, st));
-        d_w0 = s.segtab.as<int64_t>();
+        GWE_CUDA_TRY(wk.segtab.ensure(sizeof(int64_t) * tab.size()));
+        GWE_CUDA_TRY(cudaMemcpyAsync(wk.segtab.ptr, tab.data(), sizeof(int64_t) * tab.size(), cudaMemcpyHostToDevice, st));
+        d_w0 = wk.segtab.as<int64_t>();
         d_s0 = d_w0 + n_seg + 1;
     }
     p.wimg = s.img.as<uint8_t>();
@@ -1281,7 +1330,7 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     p.n_models = d.n_models;
     p.out = out;
     p.logits = logits ? 1 : 0;
-    p.ring = s.ring.as<uint8_t>();
+    p.ring = wk.ring.as<uint8_t>();
     p.ring_cta_bytes = n_rings * ring_cta;
     p.ring_pp = n_rings > 1 ? ring_cta : 0;
     p.zeros = s.zeros.as<uint8_t>();
@@ -1296,43 +1345,87 @@ gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL,
     if (p.reuse_shift > 0) {
         const int ntr = W / kTile - p.reuse_shift;
         p.carry_cta_floats = (uint64_t)2 * ntr * (R / 2 + S / 2) * 256;
-        GWE_CUDA_TRY(s.carry.ensure(sizeof(float) * p.carry_cta_floats * grid_max));
-        p.carry = s.carry.as<float>();
+        GWE_CUDA_TRY(wk.carry.ensure(sizeof(float) * p.carry_cta_floats * grid_max));
+        p.carry = wk.carry.as<float>();
     }
-    if (n_slides == 0) {
+    L.grid_max = grid_max;
+    L.grid_slide = (int)std::min<int64_t>(s.sms, nw);
+    L.n_slides = n_slides;
+    L.dsl = dsl;
+    L.d_w0 = d_w0;
+    L.out = out;
+    L.logits = logits;
+    if (n_slides > 0) {
+        // Time slides: per model, one branch pass storing the projections, then the slide heads.
+        const uint64_t proj_elems = 2ull * (uint64_t)nw * HC * W;
+        GWE_CUDA_TRY(wk.proj.ensure(proj_elems * sizeof(uint16_t)));
+        L.proj = wk.proj.as<uint16_t>();
+    }
+    return GWE_OK;
+}
+
+template <int HC, int T>
+void launch_slide_head(const TcLaunch &L, const float *w2, float b2, float *out, cudaStream_t st) {
+    const int spb = L.shape.spb > 0 ? L.shape.spb : L.n_slides;
+    dim3 g2((unsigned)L.nw, (unsigned)(L.p.W / T), (unsigned)((L.n_slides + spb - 1) / spb));
+    k_slide_head<HC, T><<<g2, T, (HC / 8) * T * 16, st>>>(L.proj, L.nw, L.p.W, L.dsl, L.n_slides, spb, L.p.n_seg,
+                                                          L.d_w0, w2, b2, out, (int64_t)L.p.n_models * L.nw * L.p.W,
+                                                          L.logits ? 1 : 0);
+}
+
+// the slide heads of model mi (projections already in L.proj)
+template <int HC>
+gwe_status issue_slide_heads(gwe_model *m, TcState &s, const TcLaunch &L, int mi, cudaStream_t st) {
+    const Dims &d = m->dims;
+    const float *w2 = m->w32.as<float>() + (int64_t)mi * d.P + off_wh2(d);
+    const float b2 = s.b2_host[mi];
+    float *out = L.out + (int64_t)mi * L.nw * L.p.W;
+    ProfScope prof("k_slide_head", st);
+    switch (L.shape.tile) {
+        case 64: launch_slide_head<HC, 64>(L, w2, b2, out, st); break;
+        case 256: launch_slide_head<HC, 256>(L, w2, b2, out, st); break;
+        default: launch_slide_head<HC, 128>(L, w2, b2, out, st); break;
+    }
+    note_launch();
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
+template <int R, int S, int HC, bool F8>
+gwe_status issue_tc(gwe_model *m, TcState &s, const TcLaunch &L, cudaStream_t st) {
+    using Sh = TcShape<R, S, HC, F8>;
+    if (L.nw <= 0) return GWE_OK;
+    if (L.n_slides == 0) {
         ProfScope prof("k_branch_tc", st);
-        k_branch_tc<R, S, HC, F8><<<grid_max, kThreads, Sh::SMEM, st>>>(p);
+        k_branch_tc<R, S, HC, F8><<<L.grid_max, kThreads, Sh::SMEM, st>>>(L.p);
         note_launch();
         GWE_CUDA_TRY(cudaGetLastError());
         return GWE_OK;
     }
-    // Time slides: per model, one branch pass storing the projections, then the slide heads.
-    const uint64_t proj_elems = 2ull * (uint64_t)nw * HC * W;
-    GWE_CUDA_TRY(s.proj.ensure(proj_elems * sizeof(uint16_t)));
-    const int grid = (int)std::min<int64_t>(s.sms, nw);
-    for (int mi = 0; mi < d.n_models; ++mi) {
-        TcParams q = p;
+    for (int mi = 0; mi < m->dims.n_models; ++mi) {
+        TcParams q = L.p;
         q.model0 = mi;
         q.n_models = 1;
-        q.proj = s.proj.as<uint16_t>();
+        q.proj = L.proj;
         {
             ProfScope prof("k_branch_tc", st);
-            k_branch_tc<R, S, HC, F8><<<grid, kThreads, Sh::SMEM, st>>>(q);
-            note_launch();
-        }
-        const float *w2 = m->w32.as<float>() + (int64_t)mi * d.P + off_wh2(d);
-        const float b2 = s.b2_host[mi];
-        dim3 g2((unsigned)nw, (unsigned)(W / kSlideT));
-        {
-            ProfScope prof("k_slide_head", st);
-            k_slide_head<HC><<<g2, kSlideT, (HC / 8) * kSlideT * 16, st>>>(
-                s.proj.as<uint16_t>(), nw, W, dsl, n_slides, p.n_seg, d_w0, w2, b2, out + (int64_t)mi * nw * W,
-                (int64_t)d.n_models * nw * W, logits ? 1 : 0);
+            k_branch_tc<R, S, HC, F8><<<L.grid_slide, kThreads, Sh::SMEM, st>>>(q);
             note_launch();
         }
         GWE_CUDA_TRY(cudaGetLastError());
+        gwe_status r = issue_slide_heads<HC>(m, s, L, mi, st);
+        if (r != GWE_OK) return r;
     }
     return GWE_OK;
+}
+
+template <int R, int S, int HC, bool F8>
+gwe_status launch_tc(gwe_model *m, TcState &s, const float *sH, const float *sL, const Segments &sg, int W,
+                     int stride, const int32_t *slides_host, int n_slides, float *out, bool logits, cudaStream_t st) {
+    TcLaunch L;
+    gwe_status r = setup_tc<R, S, HC, F8>(m, s, s.work, sH, sL, sg, W, stride, slides_host, n_slides, out, logits, st, L);
+    if (r != GWE_OK) return r;
+    return issue_tc<R, S, HC, F8>(m, s, L, st);
 }
 
 // compile-time shape of one instantiation of the tensor-core kernel
@@ -1503,14 +1596,10 @@ void tc_release(gwe_model *m) {
     if (!s) return;
     s->img.release();
     s->pblob.release();
-    s->ring.release();
     s->zeros.release();
     s->err.release();
     s->slides.release();
-    s->proj.release();
-    s->koff.release();
-    s->carry.release();
-    s->segtab.release();
+    s->work.release();
     delete s;
     m->tc = nullptr;
 }
@@ -1693,4 +1782,245 @@ extern "C" gwe_status gwe_forward_static(gwe_model *m, const float *strain_H, co
         return launch_tc_static<T::R, T::S, T::HC, T::F8>(m, *s, scratch, strain_H, strain_L, nw, window, stride,
                                                           out_prob, status, cs);
     });
+}
+
+// ============================================================================ forward plans
+// A plan fixes one batched forward (science segments x time slides on given device buffers),
+// optionally autotunes the launch shape of the slide heads on those buffers, and captures every
+// launch of the forward into one CUDA graph; an execution is one graph launch.
+namespace gwe {
+namespace {
+
+struct PlanImpl {
+    gwe_model *model = nullptr;
+    TcWork work;                  // the plan's own rings, carry, projections and tables
+    TcLaunch L;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n_kernels = 0;            // kernels in the graph
+    double tuned_ms = 0.0, default_ms = 0.0;
+    ~PlanImpl() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        work.release();
+    }
+};
+
+// autotuned slide-head shapes per geometry, shared by the plans of a process
+struct ShapeKey {
+    int hc, W, n_slides, n_seg;
+    int64_t nw;
+    bool operator<(const ShapeKey &o) const {
+        return std::tie(hc, W, n_slides, n_seg, nw) < std::tie(o.hc, o.W, o.n_slides, o.n_seg, o.nw);
+    }
+};
+struct ShapeVal {
+    SlideShape shape;
+    double tuned_ms, default_ms;
+};
+std::mutex g_shape_mu;
+std::map<ShapeKey, ShapeVal> g_shapes;
+
+// Times every candidate shape of model 0's slide heads (projections computed first) with CUDA
+// events on `st` and keeps the fastest: samples per block 64 / 128 / 256 (those dividing the
+// window) x all offsets per block or a quarter of them per block (more, smaller blocks).
+template <int R, int S, int HC, bool F8>
+gwe_status autotune_slides(gwe_model *m, TcState &s, PlanImpl &P, cudaStream_t st) {
+    using Sh = TcShape<R, S, HC, F8>;
+    TcLaunch &L = P.L;
+    const ShapeKey key{HC, L.p.W, L.n_slides, L.p.n_seg, L.nw};
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        auto it = g_shapes.find(key);
+        if (it != g_shapes.end()) {
+            L.shape = it->second.shape;
+            P.tuned_ms = it->second.tuned_ms;
+            P.default_ms = it->second.default_ms;
+            return GWE_OK;
+        }
+    }
+    ProfSuspend quiet;
+    TcParams q = L.p;
+    q.model0 = 0;
+    q.n_models = 1;
+    q.proj = L.proj;
+    k_branch_tc<R, S, HC, F8><<<L.grid_slide, kThreads, Sh::SMEM, st>>>(q);
+    GWE_CUDA_TRY(cudaGetLastError());
+    std::vector<SlideShape> cands;
+    const int quarter = std::max(1, (L.n_slides + 3) / 4);
+    for (int tile : {64, 128, 256}) {
+        if (L.p.W % tile) continue;
+        cands.push_back(SlideShape{tile, 0});
+        if (quarter < L.n_slides) cands.push_back(SlideShape{tile, quarter});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GWE_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        GWE_CUDA_TRY(ce);
+    }
+    double best = 1e300, dflt = 0.0;
+    SlideShape best_shape;
+    gwe_status r = GWE_OK;
+    for (const SlideShape &c : cands) {
+        L.shape = c;
+        double t_min = 1e300;
+        for (int rep = 0; rep < 3 && r == GWE_OK; ++rep) {
+            ce = cudaEventRecord(e0, st);
+            if (ce == cudaSuccess) r = issue_slide_heads<HC>(m, s, L, 0, st);
+            if (ce == cudaSuccess && r == GWE_OK) ce = cudaEventRecord(e1, st);
+            if (ce == cudaSuccess && r == GWE_OK) ce = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (ce == cudaSuccess && r == GWE_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce != cudaSuccess) {
+                set_error(std::string("slide-head autotuning: ") + cudaGetErrorString(ce));
+                r = GWE_ERR_CUDA;
+            }
+            if (rep > 0) t_min = std::min(t_min, (double)ms);   // the first run warms up
+        }
+        if (r != GWE_OK) break;
+        if (c.tile == 128 && c.spb == 0) dflt = t_min;
+        if (t_min < best) {
+            best = t_min;
+            best_shape = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != GWE_OK) return r;
+    L.shape = best_shape;
+    P.tuned_ms = best;
+    P.default_ms = dflt;
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shapes[key] = ShapeVal{best_shape, best, dflt};
+    return GWE_OK;
+}
+
+template <int R, int S, int HC, bool F8>
+gwe_status plan_build(gwe_model *m, TcState &s, PlanImpl &P, const float *sH, const float *sL, const Segments &sg,
+                      int W, int stride, const int32_t *slides, int n_slides, float *out, int flags, cudaStream_t st) {
+    gwe_status r = setup_tc<R, S, HC, F8>(m, s, P.work, sH, sL, sg, W, stride, slides, n_slides, out, false, st, P.L);
+    if (r != GWE_OK) return r;
+    P.L.shape = SlideShape();
+    if ((flags & GWE_PLAN_AUTOTUNE) && n_slides > 0 && P.L.nw > 0) {
+        r = autotune_slides<R, S, HC, F8>(m, s, P, st);
+        if (r != GWE_OK) return r;
+    }
+    // the tables went up from pageable memory and the tuning ran on `st`: finish both first
+    GWE_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaStream_t cs = nullptr;
+    GWE_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const int64_t before = gwe_launch_count();
+    cudaGraph_t g = nullptr;
+    cudaError_t ce;
+    {
+        ProfSuspend quiet;
+        ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            r = issue_tc<R, S, HC, F8>(m, s, P.L, cs);
+            const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+            if (ce == cudaSuccess) ce = ee;
+        }
+    }
+    P.n_kernels = (int)(gwe_launch_count() - before);
+    note_launch(-P.n_kernels);     // captured, not launched
+    cudaStreamDestroy(cs);
+    if (r != GWE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        set_error(std::string("gwe_plan_create: stream capture failed: ") + cudaGetErrorString(ce));
+        return GWE_ERR_CUDA;
+    }
+    P.graph = g;
+    GWE_CUDA_TRY(cudaGraphInstantiate(&P.exec, P.graph, 0));
+    return GWE_OK;
+}
+
+}  // namespace
+}  // namespace gwe
+
+struct gwe_plan {
+    gwe::PlanImpl *impl;
+};
+
+extern "C" gwe_status gwe_plan_create(gwe_model *m, const float *strain_H, const float *strain_L,
+                                      const int64_t *seg_start, const int64_t *seg_len, int n_segments, int window,
+                                      int stride, const int32_t *slides, int n_slides, float *out_prob, int flags,
+                                      void *stream, gwe_plan **out) {
+    clear_error();
+    GWE_ARG_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    GWE_ARG_CHECK(strain_H != nullptr && strain_L != nullptr && out_prob != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(seg_start != nullptr && seg_len != nullptr && n_segments > 0, "no segments");
+    GWE_ARG_CHECK(window > 0 && stride > 0 && stride <= window, "bad window/stride");
+    GWE_ARG_CHECK(n_slides >= 0 && (n_slides == 0 || slides != nullptr), "slides is NULL with n_slides > 0");
+    GWE_ARG_CHECK((flags & ~GWE_PLAN_AUTOTUNE) == 0, "unknown flags");
+    Segments sg;
+    for (int g = 0; g < n_segments; ++g) {
+        GWE_ARG_CHECK(seg_start[g] >= 0 && seg_len[g] >= 0, "negative segment start or length");
+        sg.s0.push_back(seg_start[g]);
+        sg.nw.push_back(seg_len[g] >= window ? (seg_len[g] - window) / stride + 1 : 0);
+    }
+    GWE_ARG_CHECK(sg.total_windows() > 0, "the segments hold no window");
+    if (m->precision != GWE_BF16 && m->precision != GWE_FP8) {
+        set_error("gwe_plan_create: plans use the tensor-core path (GWE_BF16 or GWE_FP8 handles)");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
+    if (!s || s->variant < 0) {
+        set_error("gwe_plan_create: tensor-core path not prepared");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    if (window % kTile != 0) {
+        set_error("gwe_plan_create: window must be a multiple of 128");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    gwe::PlanImpl *P = new gwe::PlanImpl();
+    P->model = m;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    gwe_status r = tc_dispatch(*s, [&](auto t) {
+        using T = decltype(t);
+        return gwe::plan_build<T::R, T::S, T::HC, T::F8>(m, *s, *P, strain_H, strain_L, sg, window, stride, slides,
+                                                         n_slides, out_prob, flags, st);
+    });
+    if (r != GWE_OK) {
+        delete P;
+        return r;
+    }
+    *out = new gwe_plan{P};
+    return GWE_OK;
+}
+
+extern "C" gwe_status gwe_plan_execute(gwe_plan *plan, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(plan != nullptr && plan->impl != nullptr, "plan is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ProfScope prof("gwe_plan", st);
+    GWE_CUDA_TRY(cudaGraphLaunch(plan->impl->exec, st));
+    note_launch(plan->impl->n_kernels);
+    return GWE_OK;
+}
+
+extern "C" gwe_status gwe_plan_shape(const gwe_plan *plan, int *slide_tile, int *slides_per_block, int *n_kernels,
+                                     double *tuned_ms, double *default_ms) {
+    clear_error();
+    GWE_ARG_CHECK(plan != nullptr && plan->impl != nullptr, "plan is NULL");
+    const gwe::PlanImpl &P = *plan->impl;
+    if (slide_tile) *slide_tile = P.L.shape.tile;
+    if (slides_per_block) *slides_per_block = P.L.shape.spb > 0 ? P.L.shape.spb : P.L.n_slides;
+    if (n_kernels) *n_kernels = P.n_kernels;
+    if (tuned_ms) *tuned_ms = P.tuned_ms;
+    if (default_ms) *default_ms = P.default_ms;
+    return GWE_OK;
+}
+
+extern "C" void gwe_plan_destroy(gwe_plan *plan) {
+    if (!plan) return;
+    delete plan->impl;
+    delete plan;
 }

@@ -65,6 +65,13 @@ struct ProfScope {
     ~ProfScope();
 };
 
+// While alive, ProfScope records nothing on this thread (used around stream captures, where an
+// event record would become part of the captured graph).
+struct ProfSuspend {
+    ProfSuspend();
+    ~ProfSuspend();
+};
+
 // Counts the library's kernel launches (read with gwe_launch_count).
 void note_launch(int n = 1);
 

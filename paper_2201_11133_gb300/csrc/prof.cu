@@ -46,14 +46,18 @@ void drain(Entry &e) {
 }
 
 std::atomic<long long> g_launches{0};
+thread_local int tl_suspend = 0;    // > 0 while a stream capture is being recorded on this thread
 
 }  // namespace
+
+ProfSuspend::ProfSuspend() { ++tl_suspend; }
+ProfSuspend::~ProfSuspend() { --tl_suspend; }
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char *name, cudaStream_t s) : slot(-1), st(s) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_on) return;
+    if (!g_on || tl_suspend > 0) return;
     cudaEvent_t b, e;
     if (cudaEventCreate(&b) != cudaSuccess) return;
     if (cudaEventCreate(&e) != cudaSuccess) {
