@@ -262,6 +262,117 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def lognormal_segments(total: int, seed: int = 2024, median_s: float = 1200.0, sigma: float = 1.0,
+                       lo_s: float = 60.0, hi_s: float = 14400.0, gap_max_s: float = 60.0):
+    """Science segments with lognormal lengths (median 20 min, clipped to 60 s .. 4 h) and gaps of up
+    to a minute, laid out from sample 0 until `total` samples are used (the last one cut)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    starts, lens, pos = [], [], 0
+    while pos < total:
+        ln = int(np.clip(rng.lognormal(np.log(median_s), sigma), lo_s, hi_s) * FS)
+        ln = min(ln, total - pos)
+        if ln >= WINDOW:
+            starts.append(pos)
+            lens.append(ln)
+        pos += ln + int(rng.uniform(0, gap_max_s) * FS)
+    return np.array(starts, dtype=np.int64), np.array(lens, dtype=np.int64)
+
+
+def batched_slides(gwe, cfg, wb, Hw, Lw, n, thr, minutes, dist, dev, stream, world):
+    """Segments cut from the whitened hour (lognormal lengths, gaps between them) x 64 offsets of
+    1..64 s, FP8 ensemble, one autotuned CUDA-graph plan per step, then triggers per segment."""
+    import torch
+    from paper_2201_11133_gb300 import multi
+    starts, lens = lognormal_segments(min(n, int(minutes * 60) * FS))
+    nws = gwe.segment_windows(lens, WINDOW, STRIDE)
+    k_sl = 64
+    offs = [2 * (i + 1) for i in range(k_sl)]
+    m8 = gwe.Model(cfg, wb, PREC_NAMES["fp8"])
+    out = torch.empty((k_sl, cfg["n_models"], int(nws.sum()), WINDOW), dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    plan = gwe.gwe_plan_create(m8.handle, Hw, Lw, starts, lens, WINDOW, STRIDE, offs, out, gwe.GWE_PLAN_AUTOTUNE,
+                               stream=stream)
+    t_create = time.perf_counter() - t0
+    shape = gwe.gwe_plan_shape(plan)
+
+    def step():
+        gwe.gwe_plan_execute(plan, stream=stream)
+        return gwe.gwe_triggers_segments(out, cfg["n_models"], k_sl, lens, WINDOW, STRIDE, thr, 2048.0, 2048,
+                                         flags=0, stream=stream)[0]
+
+    step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ts, tf = [], []
+    for _ in range(2):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        gwe.gwe_plan_execute(plan, stream=stream)
+        e1.record(stream)
+        recs = gwe.gwe_triggers_segments(out, cfg["n_models"], k_sl, lens, WINDOW, STRIDE, thr, 2048.0, 2048,
+                                         flags=0, stream=stream)[0]
+        e2.record(stream)
+        e2.synchronize()
+        ts.append(e0.elapsed_time(e2))
+        tf.append(e0.elapsed_time(e1))
+    gwe.gwe_sync(m8.handle)
+    t_step = multi.max_over_ranks(sum(ts) / len(ts), dist, dev)
+    t_fwd = multi.max_over_ranks(sum(tf) / len(tf), dist, dev)
+    strain_s = float(lens.sum()) / FS
+    res = {"segments": int(len(lens)), "strain_s": strain_s, "windows": int(nws.sum()), "offsets": k_sl,
+           "precision": "fp8", "ms_per_step": t_step, "forward_graph_ms": t_fwd,
+           "physical_strain_s_per_s": world * strain_s / (t_step / 1000.0),
+           "effective_strain_s_per_s": world * strain_s * k_sl / (t_step / 1000.0),
+           "ensemble_triggers": int(np.sum(recs["model"] == -1)) if len(recs) else 0,
+           "plan": {"graph_kernels": shape["n_kernels"], "slide_tile": shape["slide_tile"],
+                    "slides_per_block": shape["slides_per_block"], "slide_heads_ms_tuned": shape["tuned_ms"],
+                    "slide_heads_ms_default": shape["default_ms"], "create_s": t_create},
+           "segment_lengths_s": {"min": float(lens.min()) / FS, "median": float(np.median(lens)) / FS,
+                                 "max": float(lens.max()) / FS},
+           "note": "lognormal segment lengths (median 20 min, clipped 60 s..4 h) cut from the whitened hour; "
+                   "one graph launch per step (all models, branch passes + slide heads), then triggers per "
+                   "segment on every (offset, model) series"}
+    gwe.gwe_plan_destroy(plan)
+    del out
+    m8.close()
+    return res
+
+
+def stream_search(gwe, cfg, wb, sh, sl, thr, hours, dist, dev, stream, world):
+    """FP16 raw strain (x 1e21) in pinned host memory, `hours` long (the hour repeated), searched in
+    chunks of 7151 windows (+16 windows of context and 4 s of whitening guard per side: 1 h spans):
+    H2D copies, conversion, whitening, ensemble forward and triggers, for BF16 and FP8."""
+    import torch
+    from paper_2201_11133_gb300 import multi
+    reps = max(1, int(round(hours)))
+    hH = torch.from_numpy(np.tile(sh, reps).astype(np.float16)).pin_memory()
+    hL = torch.from_numpy(np.tile(sl, reps).astype(np.float16)).pin_memory()
+    n_all = int(hH.numel())
+    res = {"hours": n_all / FS / 3600.0, "input": "fp16 x 1e21, pinned host memory", "chunk_windows": 7151,
+           "margin_windows": 16, "guard_samples": 16384, "h2d_bytes": int(hH.nbytes + hL.nbytes)}
+    for pname in ("bf16", "fp8"):
+        m = gwe.Model(cfg, wb, PREC_NAMES[pname])
+        sr = gwe.gwe_search_create(m.handle, window=WINDOW, stride=STRIDE, chunk_windows=7151, margin_windows=16,
+                                   guard_samples=16384, fs=float(FS), welch_seg=WELCH_SEG,
+                                   input_dtype=gwe.GWE_INPUT_F16, input_scale=1.0, height_thr=thr,
+                                   min_width=2048.0, coinc=2048, trigger_flags=0)
+        gwe.gwe_search_run(sr, hH[:WINDOW * 8], hL[:WINDOW * 8], WINDOW * 8, stream=stream)   # warm the plans
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        recs = gwe.gwe_search_run(sr, hH, hL, n_all, stream=stream)
+        torch.cuda.synchronize()
+        t = multi.max_over_ranks(time.perf_counter() - t0, dist, dev)
+        rate = world * n_all / FS / t
+        res[pname] = {"seconds": t, "strain_s_per_s": rate, "ensemble_triggers": int(np.sum(recs["model"] == -1)),
+                      "month_seconds_extrapolated": 30 * 86400 / (rate / world)}
+        gwe.gwe_search_destroy(sr)
+        m.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,6 +388,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--slides", type=int, default=64,
                     help="also time the time-slide background pass with this many Livingston offsets (0: skip)")
+    ap.add_argument("--batched-minutes", type=float, default=60.0,
+                    help="science segments (lognormal lengths) totalling this many minutes x 64 offsets through a "
+                         "graph plan in FP8 (0: skip)")
+    ap.add_argument("--stream-hours", type=float, default=3.0,
+                    help="stream this many hours of FP16 strain from pinned host memory through the chunked "
+                         "search (0: skip)")
     ap.add_argument("--compare-minutes", type=float, default=6.0,
                     help="time the other precisions' forward steps too (FP8 on the whole workload, FP32 on "
                          "this many minutes of it); 0: skip")
@@ -433,6 +550,15 @@ def main():
                               "slide heads per offset, triggers on every (offset, model) series"}
         del out_sl
 
+    # many uneven science segments x 64 offsets, FP8, through one autotuned CUDA-graph plan
+    batched = None
+    if args.batched_minutes > 0:
+        batched = batched_slides(gwe, cfg, wb, Hw, Lw, n, thr, args.batched_minutes, dist, dev, stream, world)
+    # month-scale streaming: FP16 strain in pinned host memory, chunked whitening + forward + triggers
+    streaming = None
+    if args.stream_hours > 0:
+        streaming = stream_search(gwe, cfg, wb, sh, sl, thr, args.stream_hours, dist, dev, stream, world)
+
     # the same step in the other precisions (FP32: the plain SIMT path the speed-ups are quoted against)
     precisions = None
     if args.compare_minutes > 0:
@@ -542,6 +668,8 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "time_slides": slides_res,
+        "batched_slides": batched,
+        "streaming": streaming,
         "precisions": precisions,
         "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                     for k, v in prof.items()},

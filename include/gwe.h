@@ -378,6 +378,70 @@ gwe_status gwe_triggers_segments(const float *prob, int n_models, int n_slides, 
                                  int64_t coinc, int flags, gwe_trigger *out, int32_t *out_segment, int64_t cap,
                                  int64_t *n_out, void *stream);
 
+/* Input sample types of gwe_search_run. */
+#define GWE_INPUT_F32 0
+#define GWE_INPUT_F16 1
+
+/* Parameters of a streaming search (gwe_search_create). */
+typedef struct {
+    int window, stride;        /* window and stride in samples (paper: 4096, 2048) */
+    int chunk_windows;         /* windows per chunk core */
+    int margin_windows;        /* windows of context computed on each side of a core */
+    int64_t guard_samples;     /* raw samples whitened beyond the margins on each side */
+    double fs;                 /* sample rate, Hz */
+    int welch_seg;             /* Welch segment length (power of two; 16384 = 4 s at 4096 Hz) */
+    int input_dtype;           /* GWE_INPUT_F32 or GWE_INPUT_F16 */
+    float input_scale;         /* samples are multiplied by this after conversion to FP32 */
+    float height_thr;          /* peak height threshold (as gwe_triggers) */
+    double min_width;          /* minimum peak width in samples (as gwe_triggers) */
+    int64_t coinc;             /* coincidence span in samples (as gwe_triggers) */
+    int trigger_flags;         /* 0 or GWE_TRIG_PER_MODEL */
+} gwe_search_config;
+
+/* Opaque streaming search (gwe_search_create). */
+typedef struct gwe_search gwe_search;
+
+/*
+ * Streaming search over one long stream of raw two-detector strain (section
+ * "Computational Efficiency": a month of Hanford and Livingston data searched
+ * by the ensemble; section "Materials and Methods", paragraph "Data
+ * preparation": whitening with PSDs estimated from the data).  The stream's
+ * windows (window w = samples [w*stride, w*stride + window)) are cut into
+ * chunks of chunk_windows windows (the cores).  Each chunk computes the
+ * windows of its core plus margin_windows windows on each side, on a span of
+ * raw samples that reaches guard_samples further on each side (clipped to the
+ * stream): the span is converted to FP32 (times input_scale), whitened as
+ * gwe_whiten does with the span as its segment (PSD and standard deviation of
+ * the span), run through the handle's ensemble forward, and peak finding and
+ * ensemble coincidence (as gwe_triggers) run on the stitched series of the
+ * span's windows.  A record is kept when its index lies in the core's part of
+ * the stream's stitched series (window 0 gives samples [0, window), window w
+ * its last stride samples): the cores partition the series, so each trigger
+ * comes from one chunk.  Peaks whose bases or half-height crossings reach
+ * beyond a span can differ from peak finding on the whole series; the margins
+ * bound that.  The model handle must not be used by other calls meanwhile.
+ *   cfg     parameters; validated here (GWE_ERR_ARG).
+ */
+gwe_status gwe_search_create(gwe_model *model, const gwe_search_config *cfg, gwe_search **out);
+
+/*
+ * Run the search over n_samples samples per detector.
+ *   strain_H/L   the raw strain, input_dtype elements: device memory
+ *                (host_input = 0), or host memory (host_input = 1; pinned
+ *                memory lets the copy of the next chunk's span overlap the
+ *                current chunk's work, which runs on `stream`).
+ *   out, cap     host array of records, index in the stream's stitched
+ *                series, slide 0; ordered by chunk, then as gwe_triggers.
+ *   n_out        total number of records (GWE_ERR_CAPACITY if above cap).
+ * Synchronous (returns after the last chunk).  GWE_ERR_ARG when a chunk's
+ * span is shorter than welch_seg.
+ */
+gwe_status gwe_search_run(gwe_search *search, const void *strain_H, const void *strain_L, int64_t n_samples,
+                          int host_input, gwe_trigger *out, int64_t cap, int64_t *n_out, void *stream);
+
+/* Release a search. */
+void gwe_search_destroy(gwe_search *search);
+
 /*
  * Whitening front end (paper section "Materials and Methods", paragraph "Data
  * preparation": the strain is whitened with power spectral densities

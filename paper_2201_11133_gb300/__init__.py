@@ -23,12 +23,14 @@ __all__ = [
     "gwe_model_destroy",
     "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
     "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static",
-    "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
+    "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE",
+    "gwe_search_create", "gwe_search_run", "gwe_search_destroy", "GWE_INPUT_F32", "GWE_INPUT_F16", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
 
 GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
 GWE_TRIG_PER_MODEL = 1
 GWE_PLAN_AUTOTUNE = 1
+GWE_INPUT_F32, GWE_INPUT_F16 = 0, 1
 _STATUS = {0: "GWE_OK", 1: "GWE_ERR_ARG", 2: "GWE_ERR_CUDA", 3: "GWE_ERR_OOM", 4: "GWE_ERR_TIMEOUT",
            5: "GWE_ERR_UNSUPPORTED", 6: "GWE_ERR_CAPACITY"}
 
@@ -51,6 +53,14 @@ class _Config(ctypes.Structure):
 class _Trigger(ctypes.Structure):
     _fields_ = [("index", ctypes.c_int64), ("slide", ctypes.c_int32), ("model", ctypes.c_int32),
                 ("height", ctypes.c_double), ("prominence", ctypes.c_double), ("width", ctypes.c_double)]
+
+
+class _SearchConfig(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int), ("stride", ctypes.c_int), ("chunk_windows", ctypes.c_int),
+                ("margin_windows", ctypes.c_int), ("guard_samples", ctypes.c_int64), ("fs", ctypes.c_double),
+                ("welch_seg", ctypes.c_int), ("input_dtype", ctypes.c_int), ("input_scale", ctypes.c_float),
+                ("height_thr", ctypes.c_float), ("min_width", ctypes.c_double), ("coinc", ctypes.c_int64),
+                ("trigger_flags", ctypes.c_int)]
 
 
 TRIGGER_DTYPE = np.dtype([("index", np.int64), ("slide", np.int32), ("model", np.int32),
@@ -98,6 +108,9 @@ def load():
             "gwe_plan_execute": (I, [P, P]),
             "gwe_plan_shape": (I, [P, P, P, P, P, P]),
             "gwe_plan_destroy": (None, [P]),
+            "gwe_search_create": (I, [P, P, P]),
+            "gwe_search_run": (I, [P, P, P, I64, I, P, I64, P, P]),
+            "gwe_search_destroy": (None, [P]),
             "gwe_profile_enable": (I, [I]),
             "gwe_profile_read": (I, [I, P, I, P, P]),
             "gwe_last_error": (ctypes.c_char_p, []),
@@ -330,6 +343,44 @@ def gwe_plan_shape(plan: int) -> dict:
 def gwe_plan_destroy(plan: int) -> None:
     if plan:
         load().gwe_plan_destroy(plan)
+
+
+def gwe_search_create(model: int, window: int = 4096, stride: int = 2048, chunk_windows: int = 7151,
+                      margin_windows: int = 16, guard_samples: int = 16384, fs: float = 4096.0, welch_seg: int = 16384,
+                      input_dtype: int = GWE_INPUT_F32, input_scale: float = 1.0, height_thr: float = 0.5,
+                      min_width: float = 2048.0, coinc: int = 2048, trigger_flags: int = 0) -> int:
+    """Streaming search over a long raw two-detector stream (see include/gwe.h); returns the handle."""
+    c = _SearchConfig(int(window), int(stride), int(chunk_windows), int(margin_windows), int(guard_samples),
+                      float(fs), int(welch_seg), int(input_dtype), float(input_scale), float(height_thr),
+                      float(min_width), int(coinc), int(trigger_flags))
+    h = ctypes.c_void_p()
+    _check(load().gwe_search_create(model, ctypes.byref(c), ctypes.byref(h)), "gwe_search_create")
+    return h.value
+
+
+def gwe_search_run(search: int, strain_H, strain_L, n_samples: int, cap: int = 1 << 20, stream=None) -> np.ndarray:
+    """Records (TRIGGER_DTYPE) of the whole stream.  strain_H/L: CUDA tensors (device input) or host
+    tensors / numpy arrays (host input; pin them for overlapped copies)."""
+    def ptr(x):
+        if hasattr(x, "is_cuda"):
+            if not x.is_contiguous():
+                raise ValueError("expected a contiguous tensor")
+            return x.data_ptr(), bool(x.is_cuda)
+        a = np.ascontiguousarray(x)
+        return a.ctypes.data, False
+    (ph, dh), (pl, dl) = ptr(strain_H), ptr(strain_L)
+    if dh != dl:
+        raise ValueError("strain_H and strain_L must both be on the device or both on the host")
+    out = np.zeros(max(1, int(cap)), dtype=TRIGGER_DTYPE)
+    n_out = ctypes.c_int64(0)
+    _check(load().gwe_search_run(search, ph, pl, int(n_samples), 0 if dh else 1, out.ctypes.data, int(cap),
+                                 ctypes.byref(n_out), _stream(stream)), "gwe_search_run")
+    return out[:n_out.value].copy()
+
+
+def gwe_search_destroy(search: int) -> None:
+    if search:
+        load().gwe_search_destroy(search)
 
 
 def gwe_set_cross_window_reuse(enable: bool) -> None:
