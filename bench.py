@@ -373,6 +373,54 @@ def stream_search(gwe, cfg, wb, sh, sl, thr, hours, dist, dev, stream, world):
     return res
 
 
+def training_step(gwe, cfg, B, dist, dev, stream, world):
+    """Forward logits, dL/dlogit of the mean BCE, and the backward pass (weight and input gradients,
+    per-stack recomputation) of one member on B windows of 2 x 4096 samples, half with chirps."""
+    import torch
+    from paper_2201_11133_gb300 import multi
+    cfg1 = dict(cfg, n_models=1)
+    wb = workload.init_weights(cfg1, seed=3000)
+    xh, xl, y = workload.training_batch(B=B, W=WINDOW, seed=2000)
+    m = gwe.Model(cfg1, wb, PREC_NAMES["fp32"])
+    XH, XL, Y = (torch.from_numpy(a).to(dev) for a in (xh, xl, y))
+    lg = torch.empty((1, B, WINDOW), dtype=torch.float32, device=dev)
+    gw = torch.empty(gwe.gwe_param_count(cfg1), dtype=torch.float32, device=dev)
+    gH = torch.empty((B, WINDOW), dtype=torch.float32, device=dev)
+    gL = torch.empty_like(gH)
+
+    def step():
+        gwe.gwe_forward_logits(m.handle, XH, XL, B, WINDOW, lg, stream)
+        dlg = (torch.sigmoid(lg[0]) - Y) / float(B * WINDOW)      # mean-BCE gradient on the logits
+        gwe.gwe_backward(m.handle, 0, XH, XL, B, WINDOW, dlg, gw, gH, gL, stream)
+
+    step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    gwe.gwe_profile_enable(True)
+    ts = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    prof = gwe.gwe_profile_read()
+    gwe.gwe_profile_enable(False)
+    t = multi.max_over_ranks(sum(ts) / len(ts), dist, dev)
+    fwd = B * WINDOW * flops_per_sample(cfg1)
+    res = {"batch": B, "window": WINDOW, "layers": workload.n_layers(cfg1), "precision": "fp32 (SIMT)",
+           "ms_per_step": t, "windows_per_s": world * B / (t / 1000.0),
+           "tflop_per_step_algorithmic": 3 * fwd / 1e12,
+           "achieved_tflops": 3 * fwd / (t / 1000.0) / 1e12,
+           "kernels": {k: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2} for k, v in prof.items()},
+           "note": "algorithmic FLOPs = forward + 2x forward for the backward; the per-stack recomputation "
+                   "of the forward is executed on top"}
+    m.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,6 +442,9 @@ def main():
     ap.add_argument("--stream-hours", type=float, default=3.0,
                     help="stream this many hours of FP16 strain from pinned host memory through the chunked "
                          "search (0: skip)")
+    ap.add_argument("--train-batch", type=int, default=256,
+                    help="time one training step (forward logits, BCE gradient, hand-written backward) of one "
+                         "30-layer model on this many windows (0: skip)")
     ap.add_argument("--compare-minutes", type=float, default=6.0,
                     help="time the other precisions' forward steps too (FP8 on the whole workload, FP32 on "
                          "this many minutes of it); 0: skip")
@@ -559,6 +610,11 @@ def main():
     if args.stream_hours > 0:
         streaming = stream_search(gwe, cfg, wb, sh, sl, thr, args.stream_hours, dist, dev, stream, world)
 
+    # one training step of one 30-layer member (forward logits + BCE gradient + backward)
+    train = None
+    if args.train_batch > 0:
+        train = training_step(gwe, cfg, args.train_batch, dist, dev, stream, world)
+
     # the same step in the other precisions (FP32: the plain SIMT path the speed-ups are quoted against)
     precisions = None
     if args.compare_minutes > 0:
@@ -670,6 +726,7 @@ def main():
         "time_slides": slides_res,
         "batched_slides": batched,
         "streaming": streaming,
+        "training": train,
         "precisions": precisions,
         "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                     for k, v in prof.items()},
