@@ -791,14 +791,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             }
                         }
                     }
-                    if (!warp_wait(B_RS + b, ph_rs & 1, 31) ||
-                        !warp_wait(B_BIAS + 4 * b + 2 + (g & 1), (g >> 1) & 1, 37)) { ok = false; break; }
+                    // residual: x_{l+1} = (x_l + b_res) + W_res z  (FP32).  The bias is added while the
+                    // residual MMAs run, so that only the TMEM load and one add follow their completion.
+                    if (!warp_wait(B_BIAS + 4 * b + 2 + (g & 1), (g >> 1) & 1, 37)) { ok = false; break; }
+                    const uint32_t rslot = sb + 2 * Sh::CB_BYTES + (g & 1) * Sh::RB_BYTES;
+                    if (l + 1 < L) {
+                        const uint32_t bres = rslot + c0 * 4;
+#pragma unroll
+                        for (int k4 = 0; k4 < RH / 4; ++k4) {
+                            const uint4 bb = lds128(bres + 16 * k4);
+                            x[4 * k4 + 0] += __uint_as_float(bb.x);
+                            x[4 * k4 + 1] += __uint_as_float(bb.y);
+                            x[4 * k4 + 2] += __uint_as_float(bb.z);
+                            x[4 * k4 + 3] += __uint_as_float(bb.w);
+                        }
+                    }
+                    if (!warp_wait(B_RS + b, ph_rs & 1, 31)) { ok = false; break; }
                     ++ph_rs;
                     tc_fence_after();
                     if (l + 1 < L) {
-                        // residual: x_{l+1} = x_l + (W_res z) + b_res  (FP32)
-                        const uint32_t rslot = sb + 2 * Sh::CB_BYTES + (g & 1) * Sh::RB_BYTES;
-                        const uint32_t bres = rslot + c0 * 4;
                         uint32_t rr[RH];
                         if constexpr (RH == 32) {
                             tmem_ld32(t_conv + R + c0, rr);
@@ -807,13 +818,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         }
                         tmem_ld_wait();
 #pragma unroll
-                        for (int k4 = 0; k4 < RH / 4; ++k4) {
-                            const uint4 bb = lds128(bres + 16 * k4);
-                            x[4 * k4 + 0] += __uint_as_float(rr[4 * k4 + 0]) + __uint_as_float(bb.x);
-                            x[4 * k4 + 1] += __uint_as_float(rr[4 * k4 + 1]) + __uint_as_float(bb.y);
-                            x[4 * k4 + 2] += __uint_as_float(rr[4 * k4 + 2]) + __uint_as_float(bb.z);
-                            x[4 * k4 + 3] += __uint_as_float(rr[4 * k4 + 3]) + __uint_as_float(bb.w);
-                        }
+                        for (int k = 0; k < RH; ++k) x[k] += __uint_as_float(rr[k]);
                         store_x(nullptr, rslot + (R + c0) * 4);
                         fence_proxy_async_smem();
                         tc_fence_before();
