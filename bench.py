@@ -375,49 +375,55 @@ def stream_search(gwe, cfg, wb, sh, sl, thr, hours, dist, dev, stream, world):
 
 def training_step(gwe, cfg, B, dist, dev, stream, world):
     """Forward logits, dL/dlogit of the mean BCE, and the backward pass (weight and input gradients,
-    per-stack recomputation) of one member on B windows of 2 x 4096 samples, half with chirps."""
+    per-stack recomputation) of one member on B windows of 2 x 4096 samples, half with chirps: with
+    a BF16 handle (tensor-core forward and backward, FP32 accumulation) and with an FP32 handle
+    (the FP32 SIMT kernels)."""
     import torch
     from paper_2201_11133_gb300 import multi
     cfg1 = dict(cfg, n_models=1)
     wb = workload.init_weights(cfg1, seed=3000)
     xh, xl, y = workload.training_batch(B=B, W=WINDOW, seed=2000)
-    m = gwe.Model(cfg1, wb, PREC_NAMES["fp32"])
     XH, XL, Y = (torch.from_numpy(a).to(dev) for a in (xh, xl, y))
-    lg = torch.empty((1, B, WINDOW), dtype=torch.float32, device=dev)
-    gw = torch.empty(gwe.gwe_param_count(cfg1), dtype=torch.float32, device=dev)
-    gH = torch.empty((B, WINDOW), dtype=torch.float32, device=dev)
-    gL = torch.empty_like(gH)
-
-    def step():
-        gwe.gwe_forward_logits(m.handle, XH, XL, B, WINDOW, lg, stream)
-        dlg = (torch.sigmoid(lg[0]) - Y) / float(B * WINDOW)      # mean-BCE gradient on the logits
-        gwe.gwe_backward(m.handle, 0, XH, XL, B, WINDOW, dlg, gw, gH, gL, stream)
-
-    step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    gwe.gwe_profile_enable(True)
-    ts = []
-    for _ in range(2):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    prof = gwe.gwe_profile_read()
-    gwe.gwe_profile_enable(False)
-    t = multi.max_over_ranks(sum(ts) / len(ts), dist, dev)
     fwd = B * WINDOW * flops_per_sample(cfg1)
-    res = {"batch": B, "window": WINDOW, "layers": workload.n_layers(cfg1), "precision": "fp32 (SIMT)",
-           "ms_per_step": t, "windows_per_s": world * B / (t / 1000.0),
+    res = {"batch": B, "window": WINDOW, "layers": workload.n_layers(cfg1),
            "tflop_per_step_algorithmic": 3 * fwd / 1e12,
-           "achieved_tflops": 3 * fwd / (t / 1000.0) / 1e12,
-           "kernels": {k: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2} for k, v in prof.items()},
            "note": "algorithmic FLOPs = forward + 2x forward for the backward; the per-stack recomputation "
                    "of the forward is executed on top"}
-    m.close()
+    for pname in ("bf16", "fp32"):
+        m = gwe.Model(cfg1, wb, PREC_NAMES[pname])
+        lg = torch.empty((1, B, WINDOW), dtype=torch.float32, device=dev)
+        gw = torch.empty(gwe.gwe_param_count(cfg1), dtype=torch.float32, device=dev)
+        gH = torch.empty((B, WINDOW), dtype=torch.float32, device=dev)
+        gL = torch.empty_like(gH)
+
+        def step():
+            gwe.gwe_forward_logits(m.handle, XH, XL, B, WINDOW, lg, stream)
+            dlg = (torch.sigmoid(lg[0]) - Y) / float(B * WINDOW)      # mean-BCE gradient on the logits
+            gwe.gwe_backward(m.handle, 0, XH, XL, B, WINDOW, dlg, gw, gH, gL, stream)
+
+        step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        gwe.gwe_profile_enable(True)
+        ts = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        prof = gwe.gwe_profile_read()
+        gwe.gwe_profile_enable(False)
+        t = multi.max_over_ranks(sum(ts) / len(ts), dist, dev)
+        res[pname] = {"path": "tensor cores (BF16 operands, FP32 accumulation)" if pname == "bf16" else "FP32 SIMT",
+                      "ms_per_step": t, "windows_per_s": world * B / (t / 1000.0),
+                      "achieved_tflops": 3 * fwd / (t / 1000.0) / 1e12,
+                      "kernels": {k: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2}
+                                  for k, v in prof.items()}}
+        m.close()
+    res["speedup_bf16_vs_fp32"] = res["fp32"]["ms_per_step"] / res["bf16"]["ms_per_step"]
     return res
 
 

@@ -190,12 +190,19 @@ gwe_status gwe_forward_logits(gwe_model *model, const float *x_H, const float *x
  *   grad_H, grad_L device FP32 [batch][window] dLoss/dstrain, or NULL.
  * The forward keeps only each stack's input and the final skip sums; the
  * backward recomputes one stack at a time from its input (per-stack
- * recomputation) and walks it backwards.  FP32 arithmetic on the FP32 weights
- * (for every handle precision); weight gradients are reduced with atomic
- * additions, so their summation order is not fixed.  Windows are processed in
- * chunks of 16; the workspace (about 0.3 GB per chunk for the 30-layer R = 64
- * model) is owned by the handle.  GWE_ERR_UNSUPPORTED for channel counts the
- * FP32 kernels do not cover.
+ * recomputation) and walks it backwards.  An FP32 handle runs FP32 SIMT
+ * kernels on the FP32 weights (windows in chunks of 16, about 0.3 GB of
+ * workspace per chunk for the 30-layer R = 64 model).  A GWE_BF16 or GWE_FP8
+ * handle runs every contraction (recomputed forward, dz, dgrad, weight
+ * gradients) as a BF16 tensor-core GEMM with FP32 accumulation on BF16 copies
+ * of the FP32 weights, keeps dL/dx, the residual stream and the skip sums in
+ * FP32, and uses the FP32 kernels for the head, the biases and the input
+ * projection (windows in chunks of 64, about 8 GB of workspace per chunk);
+ * its gradients differ from the FP32 ones by the BF16 rounding of the
+ * operands.  Weight gradients are reduced with atomic additions, so their
+ * summation order is not fixed.  The workspace is owned by the handle.
+ * GWE_ERR_UNSUPPORTED for channel counts the kernels do not cover;
+ * GWE_ERR_TIMEOUT if a device-side wait of the tensor-core kernels gave up.
  */
 gwe_status gwe_backward(gwe_model *model, int model_index, const float *x_H, const float *x_L, int batch,
                         int window, const float *dlogit, float *grad_weights, float *grad_H, float *grad_L,

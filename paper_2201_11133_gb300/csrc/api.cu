@@ -137,6 +137,7 @@ gwe_status gwe_model_set_weights(gwe_model *m, const float *hb) {
     const size_t bytes = (size_t)m->dims.P * m->dims.n_models * sizeof(float);
     GWE_CUDA_TRY(m->w32.ensure(bytes));
     GWE_CUDA_TRY(cudaMemcpy(m->w32.ptr, hb, bytes, cudaMemcpyHostToDevice));
+    ++m->wstamp;
     gwe_status st = fp32_prepare(m, hb);
     if (st != GWE_OK && m->precision == GWE_FP32) return st;
     if (m->precision == GWE_BF16 || m->precision == GWE_FP8) {
@@ -188,6 +189,7 @@ void gwe_model_destroy(gwe_model *m) {
     if (!m) return;
     tc_release(m);
     fp32_backward_release(m);
+    tc_backward_release(m->bwd_tc);
     m->w32.release();
     m->f32.buf.release();
     m->ws.x0.release();
@@ -265,6 +267,12 @@ gwe_status gwe_backward(gwe_model *m, int model_index, const float *xH, const fl
     GWE_ARG_CHECK(xH != nullptr && xL != nullptr && dlogit != nullptr && grad_w != nullptr, "NULL buffer");
     GWE_ARG_CHECK(batch > 0 && window > 0, "batch and window must be positive");
     GWE_ARG_CHECK((int64_t)batch * window < ((int64_t)1 << 31), "batch * window too large");
+    if (m->precision != GWE_FP32 && tc_backward_supported(m->dims)) {
+        int sms = 0;
+        GWE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+        return tc_backward(m, m->bwd_tc, model_index, xH, xL, batch, window, dlogit, grad_w, grad_H, grad_L, sms,
+                           as_stream(stream));
+    }
     return fp32_backward(m, model_index, xH, xL, batch, window, dlogit, grad_w, grad_H, grad_L, as_stream(stream));
 }
 

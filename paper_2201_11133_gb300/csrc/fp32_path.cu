@@ -872,6 +872,92 @@ void fp32_backward_release(gwe_model *m) {
     m->bwd = nullptr;
 }
 
+// Pieces of the backward pass shared with the tensor-core backward (bwd_tc.cu): the head, the
+// bias sums, the input projection and its backward.  Arrays hold both branches, branch 1 after
+// branch 0 (rb rows each).
+gwe_status fp32_input_proj(gwe_model *m, int mi, const float *sH, const float *sL, int64_t rb, float *x0,
+                           cudaStream_t st) {
+    const Dims &d = m->dims;
+    const float *blob = m->w32.as<float>() + (int64_t)mi * d.P;
+    const int64_t n = 2 * rb * d.R;
+    k_input_proj<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sH, sL, blob, d.Pb, d.R, rb, x0);
+    note_launch();
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
+gwe_status fp32_head_backward(gwe_model *m, int mi, const float *skip, int64_t rb, int W, int C, const float *dlogit,
+                              float *dskip, float *gw, cudaStream_t st) {
+    const Dims &d = m->dims;
+    const int S = d.S, Hc = d.Hc;
+    BwdWs *w = reinterpret_cast<BwdWs *>(m->bwd);
+    if (!w) {
+        w = new BwdWs();
+        m->bwd = w;
+    }
+    GWE_CUDA_TRY(w->ru.ensure(sizeof(float) * rb * Hc));
+    GWE_CUDA_TRY(w->du.ensure(sizeof(float) * rb * Hc));
+    float *ru = w->ru.as<float>(), *du = w->du.as<float>();
+    const float *blob = m->w32.as<float>() + (int64_t)mi * d.P;
+    const Fp32Weights &f = m->f32;
+    const float *head = f.buf.as<float>() + (int64_t)mi * f.model_stride + f.head_off;
+    BRows p{};
+    p.nsrc = 2;
+    p.s[0] = src(skip, S, 0, 1, head, Hc, S);
+    p.s[1] = src(skip + rb * S, S, 0, 1, head + (int64_t)S * Hc, Hc, S);
+    p.N = Hc; p.W = W; p.C = C;
+    p.Y = du; p.ldy = Hc;
+    p.aux0 = blob + off_bh1(d); p.aux1 = blob + off_wh2(d); p.aux2 = dlogit;
+    p.out1 = ru;
+    launch_rows<EP_HEAD_U>(p, 1, st);
+    BRows q{};
+    q.nsrc = 1;
+    q.s[0] = src(du, Hc, 0, 0, blob + off_wh1(d), 2 * S, Hc);
+    q.N = 2 * S; q.W = W; q.C = C;
+    q.aux0 = skip; q.out1 = dskip; q.aux_boff = rb * S;
+    launch_rows<EP_HEAD_DH>(q, 1, st);
+    float *g1 = gw + off_wh1(d);
+    BWg p1 = wg(du, Hc, Hc, 0, skip, S, S, 0, 0, g1, 2 * S, 0, gw + off_bh1(d), 0, W, C);
+    p1.xrelu = 1;
+    launch_wgrad(p1, 1, st);
+    BWg p2 = wg(du, Hc, Hc, 0, skip + rb * S, S, S, 0, 0, g1 + S, 2 * S, 0, nullptr, 0, W, C);
+    p2.xrelu = 1;
+    launch_wgrad(p2, 1, st);
+    launch_wgrad(wg(ru, Hc, Hc, 0, dlogit, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, C), 1, st);
+    launch_wgrad(wg(dlogit, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W, C), 1, st);
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
+gwe_status fp32_bias_grad(const float *G, int ldg, int N, int64_t g_boff, float *db, int64_t db_boff, int W, int C,
+                          int nbranch, cudaStream_t st) {
+    launch_wgrad(wg(G, ldg, N, g_boff, nullptr, 0, 0, 0, 0, nullptr, 0, 0, db, db_boff, W, C), nbranch, st);
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
+gwe_status fp32_input_backward(gwe_model *m, int mi, const float *dx0, int64_t rb, const float *sH, const float *sL,
+                               int W, int C, float *gw, float *gH, float *gL, cudaStream_t st) {
+    const Dims &d = m->dims;
+    const int R = d.R;
+    const float *blob = m->w32.as<float>() + (int64_t)mi * d.P;
+    launch_wgrad(wg(dx0, R, R, 0, sH, 1, 1, 0, 0, gw + off_branch(d, 0), 1, 0, gw + off_branch(d, 0) + R, 0, W, C), 1,
+                 st);
+    launch_wgrad(wg(dx0 + rb * R, R, R, 0, sL, 1, 1, 0, 0, gw + off_branch(d, 1), 1, 0, gw + off_branch(d, 1) + R, 0,
+                    W, C), 1, st);
+    const unsigned nb = (unsigned)((rb + 7) / 8);
+    if (gH) {
+        k_dstrain<<<nb, 256, 0, st>>>(dx0, blob + off_branch(d, 0), R, rb, gH);
+        note_launch();
+    }
+    if (gL) {
+        k_dstrain<<<nb, 256, 0, st>>>(dx0 + rb * R, blob + off_branch(d, 1), R, rb, gL);
+        note_launch();
+    }
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
 gwe_status fp32_backward(gwe_model *m, int mi, const float *xH, const float *xL, int batch, int W,
                          const float *dlogit, float *gw, float *gH, float *gL, cudaStream_t st) {
     const Dims &d = m->dims;

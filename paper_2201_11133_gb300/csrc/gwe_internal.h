@@ -115,6 +115,8 @@ struct gwe_model {
     gwe::Fp32Weights f32;         // FP32 kernel layout
     void *tc = nullptr;           // tensor-core path state (opaque, branch_tc.cu)
     void *bwd = nullptr;          // backward workspace (opaque, fp32_path.cu)
+    void *bwd_tc = nullptr;       // tensor-core backward state (opaque, bwd_tc.cu)
+    uint64_t wstamp = 0;          // incremented whenever the weights change
     gwe::Workspace ws;
 };
 
@@ -133,6 +135,12 @@ struct Segments {
 
 // fp32_path.cu
 gwe_status fp32_prepare(gwe_model *m, const float *host_blob);
+// bwd_tc.cu: backward of one member with BF16 tensor-core GEMMs (FP32 accumulation)
+bool tc_backward_supported(const Dims &d);
+gwe_status tc_backward(gwe_model *m, void *&state, int model_index, const float *xH, const float *xL, int batch,
+                       int W, const float *dlogit, float *grad_w, float *grad_H, float *grad_L, int sms,
+                       cudaStream_t st);
+void tc_backward_release(void *&state);
 // Forward of all models over one segment; writes probabilities (or logits).
 gwe_status fp32_forward(gwe_model *m, const float *sH, const float *sL, const Segments &sg, int window,
                         int stride, const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st);

@@ -1,0 +1,119 @@
+"""The tensor-core backward (BF16 operands, FP32 accumulation, per-stack
+recomputation) against the oracle's BF16 reading of the backward
+(oracle/bf16_backward.py: FP64 arithmetic with the operands of every
+contraction rounded to BF16, the reading the kernels implement) and, for the
+record, against the exact FP64 gradient and the FP32 backward.
+
+Tolerances.  On these random-init networks the gradient is sensitive to any
+perturbation of the forward at the 1e-7 level (ReLU masks of the head and
+rounding boundaries flip), so the kernels' FP32 accumulation order moves them
+about as far from the BF16 reading as the reading is from exact arithmetic
+(~2e-2 relative on the 30-layer model).  The pins are therefore: the kernels'
+distance from the exact gradient (relative L2, weights and strain) is at most
+twice the BF16 reading's, plus 1e-3; the cosine with the exact gradient is at
+least 0.99; and on a 1 s training batch with chirps and labels the gradient is
+within 1e-2 (largest entry) and cosine 0.999 of the FP32 backward's."""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _grads(cfg, wb, xh, xl, dlogit, prec):
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    dev = require_gpu()
+    m = gwe.Model(cfg, wb, prec)
+    B, W = xh.shape
+    P = gwe.gwe_param_count(cfg)
+    gw = torch.empty(P, dtype=torch.float32, device=dev)
+    gh = torch.empty((B, W), dtype=torch.float32, device=dev)
+    gl = torch.empty((B, W), dtype=torch.float32, device=dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    gwe.gwe_backward(m.handle, 0, t(xh), t(xl), B, W, t(dlogit), gw, gh, gl)
+    m.sync()
+    out = gw.cpu().numpy().astype(np.float64), gh.cpu().numpy().astype(np.float64), gl.cpu().numpy().astype(np.float64)
+    m.close()
+    return out
+
+
+def _rel(got, ref):
+    return np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30)
+
+
+def _cos(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+@pytest.mark.parametrize("name,W,B", [("small", 512, 3), ("ensemble", 384, 2), ("ensemble", 1024, 1)])
+def test_tc_backward_as_accurate_as_bf16_arithmetic(name, W, B):
+    import paper_2201_11133_gb300 as gwe
+    from oracle import bf16_backward as ob
+    cfg = workload.config(name, n_models=1)
+    wb = workload.init_weights(cfg, seed=3400, bias_std=0.1)
+    rng = np.random.default_rng(5)
+    xh = rng.standard_normal((B, W)).astype(np.float32)
+    xl = rng.standard_normal((B, W)).astype(np.float32)
+    dlogit = (rng.standard_normal((B, W)) / (B * W)).astype(np.float32)
+    gw, gh, gl = _grads(cfg, wb, xh, xl, dlogit, gwe.GWE_BF16)
+    qw, qh, ql = ob.backward(cfg, workload.param_offsets(cfg), wb[0], xh, xl, dlogit)
+    rw, rh, rl = oracle.backward(cfg, wb[0].astype(np.float64), xh, xl, dlogit.astype(np.float64))
+    l2 = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    for got, q, ref, what in ((gw, qw, rw, "weights"), (gh, qh, rh, "strain_H"), (gl, ql, rl, "strain_L")):
+        e_gpu, e_q = l2(got, ref), l2(q, ref)
+        print(f"{name} W={W} B={B} {what}: rel L2 vs exact: kernels {e_gpu:.2e}, BF16 reading {e_q:.2e}; "
+              f"kernels vs reading {l2(got, q):.2e}; cos vs exact {_cos(got, ref):.5f}")
+        assert e_gpu <= 2.0 * e_q + 1e-3, (what, e_gpu, e_q)
+        assert _cos(got, ref) >= 0.99, (what, _cos(got, ref))
+
+
+def test_tc_backward_close_to_fp32_backward_full_window():
+    """A 1 s window batch of the 30-layer model with chirps and per-sample BCE labels: the tensor-core
+    gradient against the FP32 SIMT gradient of the same weights."""
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    cfg = workload.config("ensemble", n_models=1)
+    wb = workload.init_weights(cfg, seed=3000)
+    xh, xl, y = workload.training_batch(B=6, W=4096, seed=2024)
+    dev = require_gpu()
+    m = gwe.Model(cfg, wb, gwe.GWE_FP32)
+    lg = m.logits(torch.from_numpy(xh).to(dev), torch.from_numpy(xl).to(dev))[0]
+    dl = ((torch.sigmoid(lg) - torch.from_numpy(y).to(dev)) / float(y.size)).cpu().numpy()
+    m.close()
+    g32, h32, l32 = _grads(cfg, wb, xh, xl, dl, gwe.GWE_FP32)
+    g16, h16, l16 = _grads(cfg, wb, xh, xl, dl, gwe.GWE_BF16)
+    e_w, e_h = _rel(g16, g32), _rel(h16, h32)
+    print(f"full window: rel err vs FP32 weights {e_w:.2e} strain {e_h:.2e} cos {_cos(g16, g32):.6f}")
+    assert e_w <= 1e-2 and _cos(g16, g32) >= 0.999
+
+
+def test_tc_backward_training_steps_lower_the_loss():
+    """torch autograd through a BF16 handle (tensor-core forward logits, tensor-core backward): a few
+    SGD steps on a batch with chirps lower the BCE loss."""
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    dev = require_gpu()
+    cfg = workload.config("small", n_models=1)
+    wb = workload.init_weights(cfg, seed=3700, bias_std=0.1)
+    xh, xl, y = workload.training_batch(B=8, W=1024, seed=79, merger_range=(256, 1023))
+    m = gwe.Model(cfg, wb, gwe.GWE_BF16)
+    w = torch.from_numpy(wb[0].copy()).to(dev).requires_grad_(True)
+    H = torch.from_numpy(xh).to(dev)
+    Lt = torch.from_numpy(xl).to(dev)
+    Y = torch.from_numpy(y).to(dev)
+    opt = torch.optim.SGD([w], lr=0.5)
+    losses = []
+    for _ in range(6):
+        opt.zero_grad()
+        lg = gwe.gwe_logits_autograd(m, w, H, Lt)
+        loss = torch.nn.functional.binary_cross_entropy_with_logits(lg, Y)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.item()))
+    assert losses[-1] < losses[0], losses
+    m.close()
