@@ -99,8 +99,6 @@ __device__ __forceinline__ uint32_t tmem_cols_for(int n) {
     return c;
 }
 
-__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
-
 // 8 BF16 values of row `row` (window-relative t) from segment s at chunk c, zero outside the window
 __device__ __forceinline__ uint4 seg_load(const RowSeg &s, int b, int64_t row, int W, int c) {
     const int64_t w = row / W;
@@ -111,6 +109,24 @@ __device__ __forceinline__ uint4 seg_load(const RowSeg &s, int b, int64_t row, i
 }
 
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
+
+// 16-byte global -> shared copy in flight until cp_async_wait_all; zero-filled when !valid
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// address of 8 BF16 values of row `row` of segment s at chunk c, and whether they lie in the window
+__device__ __forceinline__ const __nv_bfloat16 *seg_addr(const RowSeg &s, int b, int64_t row, int W, int c,
+                                                          bool &valid) {
+    const int64_t w = row / W;
+    const int t = (int)(row - w * W) + s.shift;
+    valid = t >= 0 && t < W;
+    return valid ? s.p + b * s.boff + (w * W + t) * (int64_t)s.ld + 8 * c : s.p;
+}
 
 // 16 consecutive values of one row (16-byte aligned): FP32 loads and stores, BF16 stores
 __device__ __forceinline__ void ld16_f32(const float *src, float (&v)[16]) {
@@ -147,7 +163,7 @@ __global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
     __shared__ uint64_t bar[2];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int KC = p.K / 8;                                   // 16-byte chunks per row
     const uint32_t a_bytes = (uint32_t)kRows * p.K * 2;   // B image follows the A tile
     uint8_t *sA = smem, *sB = smem + a_bytes;
@@ -173,21 +189,23 @@ __global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
         const int64_t r0 = (tile - (int64_t)b * tpb) * kRows;
         // the branch's B image (once per branch change; every earlier MMA has completed here)
         if (b != cur_b) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(p.bimg + b * p.bimg_boff);
+            const uint8_t *src = p.bimg + b * p.bimg_boff;
             const int n16 = p.bn * p.K * 2 / 16;
-            for (int i = tid; i < n16; i += 128) reinterpret_cast<uint4 *>(sB)[i] = __ldg(src + i);
+            for (int i = tid; i < n16; i += 128) cp_async16(smem_u32(sB + 16 * i), src + 16 * i, true);
             cur_b = b;
         }
-        // A tile: thread = row, chunk-column layout
+        // A tile: thread = row, chunk-column layout; every copy of the tile in flight at once
         const int64_t row = r0 + tid;
         int c = 0;
         for (int si = 0; si < p.nseg; ++si) {
             const RowSeg &s = p.seg[si];
             for (int cc = 0; cc < s.C / 8; ++cc, ++c) {
-                const uint4 v = row < p.rows ? seg_load(s, b, row, p.W, cc) : make_uint4(0, 0, 0, 0);
-                *reinterpret_cast<uint4 *>(sA + (size_t)c * kRows * 16 + tid * 16) = v;
+                bool valid = false;
+                const __nv_bfloat16 *src = row < p.rows ? seg_addr(s, b, row, p.W, cc, valid) : s.p;
+                cp_async16(smem_u32(sA + (size_t)c * kRows * 16 + tid * 16), src, valid && row < p.rows);
             }
         }
+        cp_async_wait_all();
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -364,22 +382,33 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
         // G^T: element (m, k = tid) at chunk k / 8, row m, position k % 8
         const uint32_t kofs = (uint32_t)(tid >> 3) * 128 * 16 + (uint32_t)(tid & 7) * 2;
         const __nv_bfloat16 *g = p.G + b * p.g_boff + row * p.ldg;
-        for (int m0 = 0; m0 < p.M; m0 += 8) {
-            uint4 v = live ? __ldg(reinterpret_cast<const uint4 *>(g + m0)) : make_uint4(0, 0, 0, 0);
-            const uint16_t *e = reinterpret_cast<const uint16_t *>(&v);
+        {
+            uint4 v[16];                      // M <= 128: at most 16 chunks, all loads issued first
 #pragma unroll
-            for (int i = 0; i < 8; ++i) *reinterpret_cast<uint16_t *>(sA + kofs + (m0 + i) * 16) = e[i];
+            for (int q = 0; q < 16; ++q)
+                v[q] = (live && 8 * q < p.M) ? __ldg(reinterpret_cast<const uint4 *>(g + 8 * q)) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                if (8 * q >= p.M) break;
+                const uint16_t *e = reinterpret_cast<const uint16_t *>(&v[q]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) *reinterpret_cast<uint16_t *>(sA + kofs + (8 * q + i) * 16) = e[i];
+            }
         }
         // X^T: element (n, k = tid) at chunk k / 8, row n, position k % 8
         const uint32_t kofsb = (uint32_t)(tid >> 3) * N * 16 + (uint32_t)(tid & 7) * 2;
-        int n0 = 0;
-        for (int si = 0; si < p.nxs; ++si) {
-            const RowSeg &s = p.xs[si];
-            for (int cc = 0; cc < s.C / 8; ++cc, n0 += 8) {
-                uint4 v = live ? seg_load(s, b, row, p.W, cc) : make_uint4(0, 0, 0, 0);
-                const uint16_t *e = reinterpret_cast<const uint16_t *>(&v);
+        {
+            uint4 v[N / 8];                   // all X chunks of the row, loads issued first
+            const int c0 = p.xs[0].C / 8;     // chunks of the first segment; the rest from the second
 #pragma unroll
-                for (int i = 0; i < 8; ++i) *reinterpret_cast<uint16_t *>(sB + kofsb + (n0 + i) * 16) = e[i];
+            for (int k = 0; k < N / 8; ++k)
+                v[k] = live ? (k < c0 ? seg_load(p.xs[0], b, row, p.W, k) : seg_load(p.xs[1], b, row, p.W, k - c0))
+                            : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int k = 0; k < N / 8; ++k) {
+                const uint16_t *e = reinterpret_cast<const uint16_t *>(&v[k]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) *reinterpret_cast<uint16_t *>(sB + kofsb + (8 * k + i) * 16) = e[i];
             }
         }
         fence_proxy_async_smem();
