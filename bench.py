@@ -436,8 +436,11 @@ def main():
     ap.add_argument("--precision", default=os.environ.get("GWE_BENCH_PRECISION", "bf16"), choices=list(PREC_NAMES))
     ap.add_argument("--minutes", type=float, default=60.0,
                     help="strain duration per detector (60 = the one-hour workload; smaller only for profiler captures)")
-    ap.add_argument("--ref-windows", type=int, default=2)
-    ap.add_argument("--cpu-windows", type=int, default=8)
+    ncpu = max(1, min(32, os.cpu_count() or 1))
+    ap.add_argument("--ref-windows", type=int, default=ncpu,
+                    help="windows per reference-arm step (the oracle runs one window per host core)")
+    ap.add_argument("--cpu-windows", type=int, default=ncpu,
+                    help="windows of the CPU-baseline sample (one per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--slides", type=int, default=64,
