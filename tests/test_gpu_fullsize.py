@@ -1,0 +1,132 @@
+"""Full-size parity: the one-hour, two-detector, 4-model 30-layer workload in the
+launch configuration the benchmark times (device whitening of the raw coloured
+strain, one persistent forward launch over all 7199 windows with cross-window
+reuse, device triggers), checked on outputs the oracle computes directly:
+
+* probabilities of sampled windows (first and last windows, windows at the
+  boundaries of the persistent kernel's per-CTA window ranges, where the reuse
+  carry restarts, and windows spread over the hour) against the FP64 network
+  on the same whitened inputs, within 1.5e-2: the BF16 rounding of the
+  convolution operands alone (an FP64 evaluation of the network with both
+  conv operands rounded to BF16 and everything else exact) reaches ~1e-2 on
+  windows of this workload, so the 1e-2 bound of the small-input tests is met
+  there with little margin (up to 1.03e-2 measured on one sampled window of
+  the hour);
+* the trigger records of the whole hour against the oracle's peak finding and
+  coincidence on the same probabilities (bit-exact);
+* 64 one-second time slides over the hour: sampled (offset, window) pairs
+  against the FP64 network on the explicitly paired windows (same bound)."""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from gpu_util import require_gpu, sigmoid
+
+pytestmark = pytest.mark.gpu
+
+FS, W, STRIDE, N = 4096, 4096, 2048, 3600 * 4096
+
+
+@pytest.fixture(scope="module")
+def hour():
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    dev = require_gpu()
+    cfg = workload.config("ensemble")
+    wb = workload.init_weights(cfg, seed=3000)
+    sh, sl, _ = workload.coloured_stream(N, seed=1000, n_inj=200, snr_range=(6.0, 20.0), mc_range=(5.0, 30.0))
+    H = torch.from_numpy(sh).to(dev)
+    L = torch.from_numpy(sl).to(dev)
+    Hw, Lw = torch.empty_like(H), torch.empty_like(L)
+    gwe.gwe_whiten(H, N, float(FS), 16384, Hw)
+    gwe.gwe_whiten(L, N, float(FS), 16384, Lw)
+    m = gwe.Model(cfg, wb, gwe.GWE_BF16)
+    yield dict(gwe=gwe, cfg=cfg, wb=wb, m=m, Hw=Hw, Lw=Lw, hw=Hw.cpu().numpy(), lw=Lw.cpu().numpy(), dev=dev)
+    m.close()
+
+
+def _range_starts(n_jobs, grid):
+    q, rm = divmod(n_jobs, grid)
+    return [c * q + min(c, rm) for c in range(grid)]
+
+
+TOL = 1.5e-2
+
+
+def test_hour_forward_sampled_windows(hour):
+    import torch
+    gwe, cfg, wb, m = hour["gwe"], hour["cfg"], hour["wb"], hour["m"]
+    nw = gwe.gwe_n_windows(N, W, STRIDE)
+    assert nw == 7199
+    out = torch.empty((1, cfg["n_models"], nw, W), dtype=torch.float32, device=hour["dev"])
+    gwe.gwe_forward(m.handle, hour["Hw"], hour["Lw"], N, W, STRIDE, None, out)
+    m.sync()
+    sms = torch.cuda.get_device_properties(hour["dev"]).multi_processor_count
+    starts = _range_starts(cfg["n_models"] * nw, min(sms, cfg["n_models"] * nw))
+    worst = 0.0
+    for mi in range(cfg["n_models"]):
+        # windows of model mi where a CTA range starts (no carry) and the one after it (first reuse)
+        bnd = [j - mi * nw for j in starts if mi * nw <= j < (mi + 1) * nw][1:3]
+        ws = sorted({0, 1, nw // 2, nw - 2, nw - 1, *bnd, *[b + 1 for b in bnd if b + 1 < nw]})
+        xh = np.stack([hour["hw"][w * STRIDE:w * STRIDE + W] for w in ws])
+        xl = np.stack([hour["lw"][w * STRIDE:w * STRIDE + W] for w in ws])
+        ref = sigmoid(oracle.forward_windows(cfg, wb[mi], xh, xl))
+        got = out[0, mi, ws].cpu().numpy().astype(np.float64)
+        err = float(np.max(np.abs(got - ref)))
+        worst = max(worst, err)
+        print(f"model {mi}: windows {ws}: max |dprob| {err:.2e}")
+        assert err <= TOL
+    hour["prob"] = out
+    print(f"hour forward sampled max |dprob| {worst:.2e}")
+
+
+def test_hour_triggers_bit_exact(hour):
+    gwe, cfg = hour["gwe"], hour["cfg"]
+    prob = hour.get("prob")
+    if prob is None:
+        pytest.skip("needs the forward of test_hour_forward_sampled_windows")
+    nw = prob.shape[2]
+    thr = float(np.quantile(prob[0, 0, :, ::97].cpu().numpy(), 0.995))
+    recs = gwe.gwe_triggers(prob, cfg["n_models"], 1, nw, W, STRIDE, thr, 0.0, 2048, flags=gwe.GWE_TRIG_PER_MODEL,
+                            cap=1 << 22)
+    p = prob.cpu().numpy()
+    per_model, ens = oracle.triggers(p, W, STRIDE, thr, 0.0, 2048)
+    for mi in range(cfg["n_models"]):
+        idx, h, pr, wd = per_model[0][mi]
+        mine = recs[recs["model"] == mi]
+        assert len(mine) == len(idx) and len(idx) > 0
+        np.testing.assert_array_equal(mine["index"], idx)
+        np.testing.assert_array_equal(mine["height"], h)
+        np.testing.assert_array_equal(mine["prominence"], pr)
+        np.testing.assert_array_equal(mine["width"], wd)
+    np.testing.assert_array_equal(recs[recs["model"] == -1]["index"], ens[0])
+    print(f"hour triggers: {len(recs)} records, {len(ens[0])} ensemble triggers, bit-exact")
+
+
+def test_hour_time_slides_sampled_pairs(hour):
+    import torch
+    gwe, cfg, wb, m = hour["gwe"], hour["cfg"], hour["wb"], hour["m"]
+    hour.pop("prob", None)
+    torch.cuda.empty_cache()
+    nw = gwe.gwe_n_windows(N, W, STRIDE)
+    offs = [2 * (k + 1) for k in range(64)]
+    out = torch.empty((64, cfg["n_models"], nw, W), dtype=torch.float32, device=hour["dev"])
+    gwe.gwe_forward(m.handle, hour["Hw"], hour["Lw"], N, W, STRIDE, offs, out)
+    m.sync()
+    rng = np.random.default_rng(9)
+    pairs = [(0, 0), (63, nw - 1), (31, nw - 50), (5, 1234), (47, 4000), (12, nw - 3)]
+    for k in range(4):
+        pairs.append((int(rng.integers(0, 64)), int(rng.integers(0, nw))))
+    for mi in range(cfg["n_models"]):
+        ws = [w for _, w in pairs]
+        wl = [(w + offs[si]) % nw for si, w in pairs]
+        xh = np.stack([hour["hw"][w * STRIDE:w * STRIDE + W] for w in ws])
+        xl = np.stack([hour["lw"][w * STRIDE:w * STRIDE + W] for w in wl])
+        ref = sigmoid(oracle.forward_windows(cfg, wb[mi], xh, xl))
+        got = np.stack([out[si, mi, w].cpu().numpy() for si, w in pairs]).astype(np.float64)
+        err = float(np.max(np.abs(got - ref)))
+        print(f"model {mi}: slid pairs max |dprob| {err:.2e}")
+        assert err <= TOL
+    del out
+    torch.cuda.empty_cache()
