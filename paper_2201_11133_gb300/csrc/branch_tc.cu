@@ -984,11 +984,52 @@ __global__ void __launch_bounds__(T) k_slide_head(const uint16_t *__restrict__ p
     for (int j = t; j < HC / 2; j += T) w2h[j] = pack_h2(w2[2 * j], w2[2 * j + 1]);
     __syncthreads();
     const uint32_t one2 = 0x3C003C00u;            // (1, 1) in FP16x2
-    for (int si = s_begin; si < s_end; ++si) {
+    // Livingston window of slide si (wrapping within the segment)
+    auto lwin = [&](int si) -> const uint4 * {
         int64_t wl = (w - sw0 + koff[si]) % snw;   // koff[si]: slide offset in windows
         if (wl < 0) wl += snw;
         wl += sw0;
-        const uint4 *pL = reinterpret_cast<const uint4 *>(proj + bstride + (uint64_t)wl * HC * W);
+        return reinterpret_cast<const uint4 *>(proj + bstride + (uint64_t)wl * HC * W);
+    };
+    auto finish = [&](int si, float acc) {
+        const float lg = acc + b2;
+        out[(uint64_t)si * slide_stride + (uint64_t)w * W + t0 + t] = logits ? lg : 1.f / (1.f + expf(-lg));
+    };
+    // two offsets per pass: one shared-memory read of the Hanford chunk serves both, and the two
+    // Livingston streams give twice the loads in flight (the per-offset arithmetic is unchanged)
+    int si = s_begin;
+    for (; si + 1 < s_end; si += 2) {
+        const uint4 *pL0 = lwin(si), *pL1 = lwin(si + 1);
+        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll 2
+        for (int c = 0; c < NC; c += 2) {
+            uint32_t h0 = 0u, h1 = 0u;
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const uint4 a = ph_s[(c + cc) * T + t];
+                const uint4 l0 = __ldg(pL0 + (uint64_t)(c + cc) * W + t0 + t);
+                const uint4 l1 = __ldg(pL1 + (uint64_t)(c + cc) * W + t0 + t);
+                const uint32_t av[4] = {a.x, a.y, a.z, a.w};
+                const uint32_t lv0[4] = {l0.x, l0.y, l0.z, l0.w}, lv1[4] = {l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t r0, r1;
+                    asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(r0) : "r"(av[q]), "r"(one2), "r"(lv0[q]));
+                    asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(r1) : "r"(av[q]), "r"(one2), "r"(lv1[q]));
+                    h0 = hfma2(r0, w2h[(c + cc) * 4 + q], h0);
+                    h1 = hfma2(r1, w2h[(c + cc) * 4 + q], h1);
+                }
+            }
+            const float2 f0 = __half22float2(*reinterpret_cast<__half2 *>(&h0));
+            const float2 f1 = __half22float2(*reinterpret_cast<__half2 *>(&h1));
+            acc0 += f0.x + f0.y;
+            acc1 += f1.x + f1.y;
+        }
+        finish(si, acc0);
+        finish(si + 1, acc1);
+    }
+    if (si < s_end) {
+        const uint4 *pL = lwin(si);
         float acc = 0.f;
 #pragma unroll 4
         for (int c = 0; c < NC; c += 2) {
@@ -1009,8 +1050,7 @@ __global__ void __launch_bounds__(T) k_slide_head(const uint16_t *__restrict__ p
             const float2 f2 = __half22float2(hh);
             acc += f2.x + f2.y;
         }
-        const float lg = acc + b2;
-        out[(uint64_t)si * slide_stride + (uint64_t)w * W + t0 + t] = logits ? lg : 1.f / (1.f + expf(-lg));
+        finish(si, acc);
     }
 }
 
