@@ -20,6 +20,7 @@
 // staging), accumulate over a range of row tiles in TMEM and add their partial sums atomically.
 // The head, the biases, the input projection and dL/dstrain use the FP32 kernels.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,9 +67,12 @@ struct RowGemm {
     const float *bias;                // per-branch bias of the epilogue (blob), branch 1 at + bias_boff
     const float *bias2;               // EPI_RES with skip: b_skip
     int64_t bias_boff;
-    const float *aux;                 // EPI_RES: x_l; EPI_DZ: a; EPI_DGRAD: dx_{l+1}   (FP32)
+    const float *aux;                 // EPI_RES: x_l; EPI_DGRAD: dx_{l+1}   (FP32)
+    const __half *gate;               // EPI_DZ: [tanh(f) | sigmoid(g)] per row (FP16), written by EPI_CONV
+    __half *gate_out;                 // EPI_CONV: where to write it (or null)
+    int64_t gate_boff;
     int64_t aux_boff;
-    float *o32;                       // EPI_CONV: a (or null); EPI_RES: x_{l+1}; EPI_DZ: da; EPI_DGRAD: dx_l
+    float *o32;                       // EPI_RES: x_{l+1}; EPI_DGRAD: dx_l
     int64_t o32_boff;
     __nv_bfloat16 *o16;               // EPI_CONV: z; EPI_RES: x_{l+1}; EPI_DZ: da; EPI_DGRAD: dx_l
     int64_t o16_boff;
@@ -90,6 +94,8 @@ struct WgGemm {
     float *dW;                        // dW[m][n] at dW + m * ldw + n, branch 1 at + w_boff
     int ldw;
     int64_t w_boff;
+    float *db;                        // or null: db[m] += sum over rows of G[row][m] (column nx of X is 1)
+    int nx;                           // columns of X from the segments (N = nx, or nx + 16 with db)
     int *err;
 };
 
@@ -143,6 +149,29 @@ __device__ __forceinline__ void st16_f32(float *dst, const float (&v)[16]) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         *reinterpret_cast<float4 *>(dst + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+__device__ __forceinline__ void st16_f16(__half *dst, const float (&v)[16]) {
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(dst + 8) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+__device__ __forceinline__ void ld16_f16(const __half *src, float (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(src + 8 * q);
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
+            v[8 * q + 2 * i] = f.x;
+            v[8 * q + 2 * i + 1] = f.y;
+        }
+    }
 }
 __device__ __forceinline__ void st16_bf16(__nv_bfloat16 *dst, const float (&v)[16]) {
     uint32_t w[8];
@@ -239,17 +268,17 @@ __global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
                 tmem_ld16(tl + R + c0, gr);
                 tmem_ld_wait();
                 if (!live) continue;
-                float f[16], g[16], z[16];
+                float th[16], sg[16], z[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    f[j] = __uint_as_float(fr[j]) + __ldg(bc + c0 + j);
-                    g[j] = __uint_as_float(gr[j]) + __ldg(bc + R + c0 + j);
-                    z[j] = tanhf(f[j]) * sigm(g[j]);
+                    th[j] = tanhf(__uint_as_float(fr[j]) + __ldg(bc + c0 + j));
+                    sg[j] = sigm(__uint_as_float(gr[j]) + __ldg(bc + R + c0 + j));
+                    z[j] = th[j] * sg[j];
                 }
-                if (p.o32) {
-                    float *ao = p.o32 + b * p.o32_boff + orow * 2 * R;
-                    st16_f32(ao + c0, f);
-                    st16_f32(ao + R + c0, g);
+                if (p.gate_out) {   // the backward's gate cache: tanh(f), sigmoid(g) in FP16
+                    __half *go = p.gate_out + b * p.gate_boff + orow * 2 * R;
+                    st16_f16(go + c0, th);
+                    st16_f16(go + R + c0, sg);
                 }
                 st16_bf16(p.o16 + b * p.o16_boff + orow * R + c0, z);
             }
@@ -294,21 +323,17 @@ __global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
                 tmem_ld16(tl + c0, dr);
                 tmem_ld_wait();
                 if (!live) continue;
-                const float *a = p.aux + b * p.aux_boff + orow * 2 * R;
-                float f[16], g[16], df[16], dg[16];
-                ld16_f32(a + c0, f);
-                ld16_f32(a + R + c0, g);
+                const __half *gc = p.gate + b * p.gate_boff + orow * 2 * R;
+                float th[16], sg[16], df[16], dg[16];
+                ld16_f16(gc + c0, th);
+                ld16_f16(gc + R + c0, sg);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const float dz = __uint_as_float(dr[j]);
-                    const float th = tanhf(f[j]), sg = sigm(g[j]);
-                    df[j] = dz * sg * (1.f - th * th);
-                    dg[j] = dz * th * sg * (1.f - sg);
+                    df[j] = dz * sg[j] * (1.f - th[j] * th[j]);
+                    dg[j] = dz * th[j] * sg[j] * (1.f - sg[j]);
                 }
-                float *d32 = p.o32 + b * p.o32_boff + orow * 2 * R;
                 __nv_bfloat16 *d16 = p.o16 + b * p.o16_boff + orow * 2 * R;
-                st16_f32(d32 + c0, df);
-                st16_f32(d32 + R + c0, dg);
                 st16_bf16(d16 + c0, df);
                 st16_bf16(d16 + R + c0, dg);
             }
@@ -400,10 +425,13 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
         {
             uint4 v[N / 8];                   // all X chunks of the row, loads issued first
             const int c0 = p.xs[0].C / 8;     // chunks of the first segment; the rest from the second
+            const int cx = p.nx / 8;          // beyond: the ones column (BF16 1.0 at column nx) and zeros
 #pragma unroll
             for (int k = 0; k < N / 8; ++k)
-                v[k] = live ? (k < c0 ? seg_load(p.xs[0], b, row, p.W, k) : seg_load(p.xs[1], b, row, p.W, k - c0))
-                            : make_uint4(0, 0, 0, 0);
+                v[k] = !live ? make_uint4(0, 0, 0, 0)
+                             : (k < c0 ? seg_load(p.xs[0], b, row, p.W, k)
+                                       : (k < cx ? seg_load(p.xs[1], b, row, p.W, k - c0)
+                                                 : make_uint4(k == cx ? 0x3F80u : 0u, 0, 0, 0)));
 #pragma unroll
             for (int k = 0; k < N / 8; ++k) {
                 const uint16_t *e = reinterpret_cast<const uint16_t *>(&v[k]);
@@ -446,7 +474,12 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
             if (m < p.M) {
                 float *dw = p.dW + b * p.w_boff + (int64_t)m * p.ldw + c0;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) atomicAdd(dw + j, __uint_as_float(v[j]));
+                for (int j = 0; j < 16; ++j) {
+                    if (c0 + j < p.nx)
+                        atomicAdd(dw + j, __uint_as_float(v[j]));
+                    else if (c0 + j == p.nx && p.db)
+                        atomicAdd(p.db + b * p.w_boff + m, __uint_as_float(v[j]));
+                }
             }
         }
     }
@@ -459,33 +492,6 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, NCOLS);
-    }
-}
-
-// db[c] += sum over the rows of branch blockIdx.y of G[row][c] (c < C); block = 32 x 8 threads,
-// threads x over columns, y over rows; one atomic add per column and block
-__global__ void __launch_bounds__(256) k_colsum(const float *__restrict__ G, int64_t g_boff, int ld, int C,
-                                                int64_t rows, int64_t rows_per_block, float *__restrict__ db,
-                                                int64_t db_boff) {
-    __shared__ float part[8][33];
-    const int b = blockIdx.y;
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-    const int64_t r1 = r0 + rows_per_block < rows ? r0 + rows_per_block : rows;
-    const float *g = G + b * g_boff;
-    for (int c0 = 0; c0 < C; c0 += 32) {
-        const int c = c0 + threadIdx.x;
-        float acc = 0.f;
-        if (c < C)
-            for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) acc += g[r * ld + c];
-        part[threadIdx.y][threadIdx.x] = acc;
-        __syncthreads();
-        if (threadIdx.y == 0 && c < C) {
-            float t = 0.f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) t += part[k][threadIdx.x];
-            atomicAdd(db + b * db_boff + c, t);
-        }
-        __syncthreads();
     }
 }
 
@@ -508,7 +514,7 @@ struct TcBwd {
     size_t conv_b = 0, rs_b = 0, dz_b = 0, dg_b = 0, layer_b = 0;
     int model = -1;
     uint64_t stamp = 0;
-    DevBuf xsave, skip, dskip32, dskip16, x32, x16, a32, z16, dx32[2], dx16[2], da32, da16, err;
+    DevBuf xsave, skip, dskip32, dskip16, x32, x16, gate16, z16, dx32[2], dx16[2], da16, err;
 };
 
 inline size_t choff(int rows, int n, int k) { return (size_t)(k / 8) * rows * 16 + (size_t)n * 16 + (k % 8) * 2; }
@@ -553,17 +559,6 @@ void build_bwd_images(const Dims &d, const float *blob, TcBwd &t) {
 
 int g_rows_smem_set = 0;
 
-// bias gradients: column sums over the rows of both branches
-gwe_status colsum(const float *G, int64_t g_boff, int ld, int C, int64_t rows, float *db, int64_t db_boff, int sms,
-                  cudaStream_t st) {
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, (rows + 1023) / 1024));
-    const int64_t rpb = (rows + blocks - 1) / blocks;
-    k_colsum<<<dim3((unsigned)blocks, 2), dim3(32, 8), 0, st>>>(G, g_boff, ld, C, rows, rpb, db, db_boff);
-    note_launch();
-    GWE_CUDA_TRY(cudaGetLastError());
-    return GWE_OK;
-}
-
 gwe_status set_attrs() {
     if (g_rows_smem_set) return GWE_OK;
     const int big = 200 * 1024;
@@ -571,9 +566,9 @@ gwe_status set_attrs() {
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_DZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<80>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<144>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     g_rows_smem_set = 1;
     return GWE_OK;
 }
@@ -610,14 +605,21 @@ gwe_status run_wgrad(WgGemm p, int sms, cudaStream_t st) {
     const int64_t want = std::max<int64_t>(1, (int64_t)sms * 2);
     p.tiles_per_cta = (int)std::max<int64_t>(8, (p.tiles + want - 1) / want);
     dim3 grid((unsigned)((p.tiles + p.tiles_per_cta - 1) / p.tiles_per_cta), 2);
-    const size_t smem = (size_t)128 * 128 * 2 + (size_t)p.N * 128 * 2 + 128;
+    // with 256 TMEM columns (N > 128) at most two CTAs may share an SM: ask for at least 80 KB
+    const size_t smem = std::max<size_t>((size_t)128 * 128 * 2 + (size_t)p.N * 128 * 2 + 128,
+                                         p.N > 128 ? 80 * 1024 : 0);
     ProfScope prof("k_tc_wgrad", st);
-    if (p.N == 32)
-        k_tc_wgrad<32><<<grid, 128, smem, st>>>(p);
-    else if (p.N == 64)
-        k_tc_wgrad<64><<<grid, 128, smem, st>>>(p);
-    else
-        k_tc_wgrad<128><<<grid, 128, smem, st>>>(p);
+    // N = nx + 16: the segments' columns, then the ones column for the bias gradient (nx = 32, 64, 128)
+    if (p.N == 48)
+        k_tc_wgrad<48><<<grid, 128, smem, st>>>(p);
+    else if (p.N == 80)
+        k_tc_wgrad<80><<<grid, 128, smem, st>>>(p);
+    else if (p.N == 144)
+        k_tc_wgrad<144><<<grid, 128, smem, st>>>(p);
+    else {
+        set_error("tensor-core backward: unsupported weight-gradient width");
+        return GWE_ERR_UNSUPPORTED;
+    }
     note_launch();
     GWE_CUDA_TRY(cudaGetLastError());
     return GWE_OK;
@@ -633,8 +635,8 @@ bool tc_backward_supported(const Dims &d) {
 void tc_backward_release(void *&state) {
     TcBwd *t = reinterpret_cast<TcBwd *>(state);
     if (!t) return;
-    DevBuf *all[] = {&t->img, &t->xsave, &t->skip, &t->dskip32, &t->dskip16, &t->x32, &t->x16, &t->a32, &t->z16,
-                     &t->dx32[0], &t->dx32[1], &t->dx16[0], &t->dx16[1], &t->da32, &t->da16, &t->err};
+    DevBuf *all[] = {&t->img, &t->xsave, &t->skip, &t->dskip32, &t->dskip16, &t->x32, &t->x16, &t->gate16, &t->z16,
+                     &t->dx32[0], &t->dx32[1], &t->dx16[0], &t->dx16[1], &t->da16, &t->err};
     for (DevBuf *b : all) b->release();
     delete t;
     state = nullptr;
@@ -687,20 +689,20 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
     GWE_CUDA_TRY(t->dskip16.ensure(2 * rows2 * S));
     GWE_CUDA_TRY(t->x32.ensure(sizeof(float) * (lps + 1) * rows2 * R));
     GWE_CUDA_TRY(t->x16.ensure(2 * (lps + 1) * rows2 * R));
-    GWE_CUDA_TRY(t->a32.ensure(sizeof(float) * lps * rows2 * 2 * R));
+    GWE_CUDA_TRY(t->gate16.ensure(2 * lps * rows2 * 2 * R));
     GWE_CUDA_TRY(t->z16.ensure(2 * lps * rows2 * R));
     for (int i = 0; i < 2; ++i) {
         GWE_CUDA_TRY(t->dx32[i].ensure(sizeof(float) * rows2 * R));
         GWE_CUDA_TRY(t->dx16[i].ensure(2 * rows2 * R));
     }
-    GWE_CUDA_TRY(t->da32.ensure(sizeof(float) * rows2 * 2 * R));
     GWE_CUDA_TRY(t->da16.ensure(2 * rows2 * 2 * R));
     GWE_CUDA_TRY(cudaMemsetAsync(gw, 0, sizeof(float) * d.P, st));
     const int64_t Pb = d.Pb;
     int *err = t->err.as<int>();
     const uint8_t *img = t->img.as<uint8_t>();
     auto limg = [&](int l, int b) { return img + t->layer_b * ((size_t)l * 2 + b); };
-    float *x32 = t->x32.as<float>(), *a32 = t->a32.as<float>(), *xsave = t->xsave.as<float>();
+    float *x32 = t->x32.as<float>(), *xsave = t->xsave.as<float>();
+    __half *gate16 = t->gate16.as<__half>();
     __nv_bfloat16 *x16 = t->x16.as<__nv_bfloat16>(), *z16 = t->z16.as<__nv_bfloat16>();
 
     for (int c0 = 0; c0 < batch; c0 += C) {
@@ -710,7 +712,7 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
         const float *sH = xH + (int64_t)c0 * W, *sL = xL + (int64_t)c0 * W;
         // one layer's forward: conv (a optional) then res (+ skip when skip_mode >= 0)
         auto layer_fwd = [&](int l, float *xin32, __nv_bfloat16 *xin16, float *xout32, __nv_bfloat16 *xout16,
-                             float *aout, __nv_bfloat16 *zout, int skip_mode) -> gwe_status {
+                             __half *gout, __nv_bfloat16 *zout, int skip_mode) -> gwe_status {
             const int dl = 1 << (l % lps);
             RowGemm p{};
             p.seg[0] = seg(xin16, xo, R, R, -dl);
@@ -727,8 +729,8 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
             p.R = R;
             p.bias = blob + off_bconv(d, 0, l);
             p.bias_boff = Pb;
-            p.o32 = aout;
-            p.o32_boff = rb * 2 * R;
+            p.gate_out = gout;
+            p.gate_boff = rb * 2 * R;
             p.o16 = zout;
             p.o16_boff = xo;
             gwe_status e = run_rows<EPI_CONV>(p, sms, st);
@@ -797,14 +799,14 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
                 const int l = k * lps + j;
                 r = layer_fwd(l, x32 + (size_t)j * rows2 * R, x16 + (size_t)j * rows2 * R,
                               x32 + (size_t)(j + 1) * rows2 * R, x16 + (size_t)(j + 1) * rows2 * R,
-                              a32 + (size_t)j * rows2 * 2 * R, z16 + (size_t)j * rows2 * R, -1);
+                              gate16 + (size_t)j * rows2 * 2 * R, z16 + (size_t)j * rows2 * R, -1);
                 if (r != GWE_OK) return r;
             }
             for (int j = lps - 1; j >= 0; --j) {
                 const int l = k * lps + j, dl = 1 << j;
                 const __nv_bfloat16 *xl16 = x16 + (size_t)j * rows2 * R;
                 const __nv_bfloat16 *zl16 = z16 + (size_t)j * rows2 * R;
-                const float *al = a32 + (size_t)j * rows2 * 2 * R;
+                const __half *gl = gate16 + (size_t)j * rows2 * 2 * R;
                 float *dxh32 = t->dx32[hi].as<float>(), *dxl32 = t->dx32[hi ^ 1].as<float>();
                 __nv_bfloat16 *dxh16 = t->dx16[hi].as<__nv_bfloat16>(), *dxl16 = t->dx16[hi ^ 1].as<__nv_bfloat16>();
                 // dz = [dx_{l+1} | dskip] . [W_res | W_skip], gate backward -> da
@@ -822,10 +824,8 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
                     p.nbranch = 2;
                     p.err = err;
                     p.R = R;
-                    p.aux = al;
-                    p.aux_boff = rb * 2 * R;
-                    p.o32 = t->da32.as<float>();
-                    p.o32_boff = rb * 2 * R;
+                    p.gate = gl;
+                    p.gate_boff = rb * 2 * R;
                     p.o16 = t->da16.as<__nv_bfloat16>();
                     p.o16_boff = rb * 2 * R;
                     r = run_rows<EPI_DZ>(p, sms, st);
@@ -841,7 +841,9 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
                     g.xs[0] = seg(xl16, xo, R, R, -dl);
                     g.xs[1] = seg(xl16, xo, R, R, 0);
                     g.nxs = 2;
-                    g.N = 2 * R;
+                    g.nx = 2 * R;
+                    g.N = 2 * R + 16;
+                    g.db = gw + off_bconv(d, 0, l);
                     g.rows = rb;
                     g.W = W;
                     g.dW = gw + off_wconv(d, 0, l);
@@ -857,8 +859,10 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
                     gr.M = R;
                     gr.xs[0] = seg(zl16, xo, R, R, 0);
                     gr.nxs = 1;
-                    gr.N = R;
+                    gr.nx = R;
+                    gr.N = R + 16;
                     gr.dW = gw + off_wres(d, 0, l);
+                    gr.db = gw + off_bres(d, 0, l);
                     gr.ldw = R;
                     r = run_wgrad(gr, sms, st);
                     if (r != GWE_OK) return r;
@@ -868,12 +872,8 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
                     gs.ldg = S;
                     gs.M = S;
                     gs.dW = gw + off_wskip(d, 0, l);
+                    gs.db = gw + off_bskip(d, 0, l);
                     r = run_wgrad(gs, sms, st);
-                    if (r != GWE_OK) return r;
-                    r = colsum(t->da32.as<float>(), rb * 2 * R, 2 * R, 2 * R, rb, gw + off_bconv(d, 0, l), Pb, sms, st);
-                    if (r == GWE_OK) r = colsum(dxh32, xo, R, R, rb, gw + off_bres(d, 0, l), Pb, sms, st);
-                    if (r == GWE_OK)
-                        r = colsum(t->dskip32.as<float>(), rb * S, S, S, rb, gw + off_bskip(d, 0, l), Pb, sms, st);
                     if (r != GWE_OK) return r;
                 }
                 // dx_l = dx_{l+1} + [da(t) | da(t + d)] . [W1 ; W0]

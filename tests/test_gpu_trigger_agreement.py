@@ -14,7 +14,8 @@ from gpu_util import require_gpu
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-2
+TOL = 1e-2       # BF16 probability tolerance
+TOL_FP8 = 3e-2   # FP8 probability tolerance (the 8-layer model's FP8 error is 2.9e-2)
 
 
 def _match(a, b, radius=256):
@@ -32,8 +33,8 @@ def _match(a, b, radius=256):
     return hits
 
 
-@pytest.mark.parametrize("q", [0.5, 0.8])
-def test_trigger_agreement(q):
+@pytest.mark.parametrize("q,prec", [(0.5, "bf16"), (0.8, "bf16"), (0.5, "fp8"), (0.8, "fp8")])
+def test_trigger_agreement(q, prec):
     """Random-init models give jagged probability series (median prominence ~0.15), so the
     threshold sweep uses quantiles of the oracle's probabilities and no width cut."""
     import torch
@@ -48,27 +49,28 @@ def test_trigger_agreement(q):
     thr = float(np.quantile(ref, q))
     coinc = 2048
     per_model, ens = oracle.triggers(ref, W, stride, thr, 0.0, coinc)
-    m = gwe.Model(cfg, wb, gwe.GWE_BF16)
+    tol = TOL if prec == "bf16" else TOL_FP8
+    m = gwe.Model(cfg, wb, gwe.GWE_BF16 if prec == "bf16" else gwe.GWE_FP8)
     prob = m.forward(torch.from_numpy(sh).to(dev), torch.from_numpy(sl).to(dev), W, stride)
     m.sync()
     recs = gwe.gwe_triggers(prob, 4, 1, prob.shape[2], W, stride, thr, 0.0, coinc)
     for mi in range(4):
         idx, h, pr, _ = per_model[0][mi]
-        solid = idx[(pr >= 0.05) & (np.abs(h - thr) > TOL)]
+        solid = idx[(pr >= 0.05) & (np.abs(h - thr) > tol)]
         got_m = recs[recs["model"] == mi]["index"]
         if len(solid):
             recall = _match(solid, got_m) / len(solid)
-            print(f"q {q} model {mi}: {len(idx)} oracle peaks, {len(solid)} solid, recall {recall:.5f}")
+            print(f"{prec} q {q} model {mi}: {len(idx)} oracle peaks, {len(solid)} solid, recall {recall:.5f}")
             assert recall >= 0.999
     got = recs[recs["model"] == -1]["index"]
     idx0, h0, pr0, _ = per_model[0][0]
     info = {int(i): (hh, pp) for i, hh, pp in zip(idx0, h0, pr0)}
-    marginal = {int(i) for i in ens[0] if abs(info[int(i)][0] - thr) <= TOL or info[int(i)][1] < 0.05}
+    marginal = {int(i) for i in ens[0] if abs(info[int(i)][0] - thr) <= tol or info[int(i)][1] < 0.05}
     solid_e = [int(i) for i in ens[0] if int(i) not in marginal]
     hits = _match(solid_e, got)
     union = len(solid_e) + len(got) - _match(got, ens[0])
     jacc = hits / max(1, len(solid_e))
-    print(f"q {q}: {len(ens[0])} oracle ensemble triggers ({len(marginal)} marginal), device {len(got)}, "
+    print(f"{prec} q {q}: {len(ens[0])} oracle ensemble triggers ({len(marginal)} marginal), device {len(got)}, "
           f"solid recall {jacc:.5f}")
     assert len(solid_e) > 0
     assert jacc >= 0.999
