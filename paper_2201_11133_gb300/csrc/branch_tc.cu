@@ -191,6 +191,12 @@ struct TcParams {
     // skipped; those rows are the previous window's, at the same ring offsets (the shift is a
     // multiple of every dilation), and are read from the previous job's ring.
     int reuse_shift;
+    // Training save mode (save_x != NULL, one model, no reuse): the input of every stack, x_l for
+    // l % lps == 0, FP32 [stack][branch][window][W][R], and the skip sum with its biases before the
+    // head's ReLU, FP32 [branch][window][W][S]: what the backward's per-stack recomputation starts
+    // from.
+    float *save_x;
+    float *save_skip;
     float *carry;              // per CTA: [branch][tile < NT - reuse_shift][(RH + SH) / 4][256 threads] float4
     uint64_t carry_cta_floats;
     int8_t lstar[64];
@@ -281,7 +287,9 @@ __device__ __forceinline__ Job decode_job(const TcParams &p, int64_t j) {
     return q;
 }
 
-template <int R, int S, int HC, bool F8>
+// SAVE: training save mode (stack inputs and skip sums stored; BF16 only), a separate instantiation
+// so that the inference kernels carry none of its code
+template <int R, int S, int HC, bool F8, bool SAVE = false>
 __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
     using Sh = TcShape<R, S, HC, F8>;
     constexpr int RH = R / 2;          // channels per epilogue thread (half of a row)
@@ -735,6 +743,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 for (int l = l0; l < L; ++l, ++g) {
                     const int d = 1 << (l % lps);
                     const int n = d < kTile ? d : kTile;
+                    if (SAVE && l % lps == 0) {
+                        // stack input x_l of this thread's row and channels
+                        float4 *dx = reinterpret_cast<float4 *>(
+                            p.save_x + ((((int64_t)(l / lps) * 2 + b) * p.nw + jb.w) * p.W + t0 + r) * R + c0);
+#pragma unroll
+                        for (int k4 = 0; k4 < RH / 4; ++k4)
+                            dx[k4] = make_float4(x[4 * k4], x[4 * k4 + 1], x[4 * k4 + 2], x[4 * k4 + 3]);
+                    }
                     if (!warp_wait(B_CONV + b, ph_conv & 1, 30) ||
                         !warp_wait(B_BIAS + 4 * b + (g & 1), (g >> 1) & 1, 36)) { ok = false; break; }
                     ++ph_conv;
@@ -867,11 +883,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4) {
                         const float4 bs = __ldg(bsk4 + 4 * cc + k4);
-                        h[4 * k4 + 0] = fmaxf(__uint_as_float(sr[4 * k4 + 0]) + bs.x, 0.f);
-                        h[4 * k4 + 1] = fmaxf(__uint_as_float(sr[4 * k4 + 1]) + bs.y, 0.f);
-                        h[4 * k4 + 2] = fmaxf(__uint_as_float(sr[4 * k4 + 2]) + bs.z, 0.f);
-                        h[4 * k4 + 3] = fmaxf(__uint_as_float(sr[4 * k4 + 3]) + bs.w, 0.f);
+                        h[4 * k4 + 0] = __uint_as_float(sr[4 * k4 + 0]) + bs.x;
+                        h[4 * k4 + 1] = __uint_as_float(sr[4 * k4 + 1]) + bs.y;
+                        h[4 * k4 + 2] = __uint_as_float(sr[4 * k4 + 2]) + bs.z;
+                        h[4 * k4 + 3] = __uint_as_float(sr[4 * k4 + 3]) + bs.w;
                     }
+                    if constexpr (SAVE) {
+                        float4 *ds = reinterpret_cast<float4 *>(
+                            p.save_skip + (((int64_t)b * p.nw + jb.w) * p.W + t0 + r) * S + ch);
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4)
+                            ds[k4] = make_float4(h[4 * k4], h[4 * k4 + 1], h[4 * k4 + 2], h[4 * k4 + 3]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) h[k] = fmaxf(h[k], 0.f);
                     sts128(st + (ch / 8) * (kTile * 16) + r * 16,
                            make_uint4(pack_h2(h[0], h[1]), pack_h2(h[2], h[3]), pack_h2(h[4], h[5]), pack_h2(h[6], h[7])));
                     sts128(st + (ch / 8 + 1) * (kTile * 16) + r * 16,
@@ -1294,6 +1319,11 @@ cudaError_t set_tc_attr() {
     cudaError_t e = cudaFuncSetAttribute(k_branch_tc<R, S, HC, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)TcShape<R, S, HC, F8>::SMEM);
     if (e != cudaSuccess) return e;
+    if (!F8) {
+        e = cudaFuncSetAttribute(k_branch_tc<R, S, HC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TcShape<R, S, HC, false>::SMEM);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(k_slide_head<HC, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (HC / 8) * 64 * 16);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_slide_head<HC, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (HC / 8) * 128 * 16);
@@ -1385,6 +1415,8 @@ gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const
     p.err = s.err.as<int>();
     p.model0 = 0;
     p.proj = nullptr;
+    p.save_x = nullptr;
+    p.save_skip = nullptr;
     p.wait_ns = g_wait_ns;
     p.dbg_drop = g_dbg_drop;
     if (p.reuse_shift > 0) {
@@ -1666,6 +1698,46 @@ gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, const Segm
     });
 }
 
+bool tc_save_supported(gwe_model *m, int W) {
+    const TcState *s = reinterpret_cast<const TcState *>(m->tc);
+    return s && s->variant >= 0 && !s->f8 && W % kTile == 0 && W >= kTile;
+}
+
+gwe_status tc_forward_save(gwe_model *m, int mi, const float *xH, const float *xL, int nwin, int W, float *logits,
+                           float *save_x, float *save_skip, cudaStream_t st) {
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
+    if (!s || s->variant < 0 || s->f8 || W % kTile != 0 || nwin <= 0 || mi < 0 || mi >= m->dims.n_models) {
+        set_error("training save forward: needs a BF16 tensor-core handle and a window that is a multiple of 128");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    Segments sg;
+    sg.s0.push_back(0);
+    sg.nw.push_back(nwin);
+    return tc_dispatch(*s, [&](auto t) -> gwe_status {
+        using T = decltype(t);
+        using Sh = TcShape<T::R, T::S, T::HC, false>;
+        TcLaunch L;
+        // windows back to back (stride = W): no cross-window reuse, every layer of every tile runs
+        gwe_status r = setup_tc<T::R, T::S, T::HC, false>(m, *s, s->work, xH, xL, sg, W, W, nullptr, 0, logits, true,
+                                                          st, L);
+        if (r != GWE_OK) return r;
+        if (L.p.reuse_shift != 0) {
+            set_error("training save forward: cross-window reuse must be off");
+            return GWE_ERR_UNSUPPORTED;
+        }
+        L.p.model0 = mi;
+        L.p.n_models = 1;
+        L.p.save_x = save_x;
+        L.p.save_skip = save_skip;
+        const int grid = (int)std::min<int64_t>(s->sms, nwin);
+        ProfScope prof("k_branch_tc", st);
+        k_branch_tc<T::R, T::S, T::HC, false, true><<<grid, kThreads, Sh::SMEM, st>>>(L.p);
+        note_launch();
+        GWE_CUDA_TRY(cudaGetLastError());
+        return GWE_OK;
+    });
+}
+
 void set_cross_window_reuse(int enable) { g_reuse.store(enable ? 1 : 0); }
 
 gwe_status debug_config(int drop, double wait_seconds) {
@@ -1783,6 +1855,8 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.err = err;
     p.model0 = 0;
     p.proj = nullptr;
+    p.save_x = nullptr;
+    p.save_skip = nullptr;
     p.wait_ns = g_wait_ns;
     p.dbg_drop = g_dbg_drop;
     plan_reuse(d, W, stride, false, p);   // no carry buffer in the fixed scratch

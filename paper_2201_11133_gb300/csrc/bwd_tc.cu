@@ -18,7 +18,9 @@
 // layer's B image in shared memory; the MMA accumulates in TMEM and the epilogue (thread = row)
 // applies the fused step.  Weight-gradient GEMMs stage G^T and X^T tiles (transposed while
 // staging), accumulate over a range of row tiles in TMEM and add their partial sums atomically.
-// The head, the biases, the input projection and dL/dstrain use the FP32 kernels.
+// The stack inputs and skip sums that the per-stack recomputation starts from come, for BF16
+// handles, from the fused forward kernel (one launch per chunk, training save mode); otherwise from
+// a forward pass of row GEMMs.  The head, the input projection and dL/dstrain use the FP32 kernels.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -105,15 +107,6 @@ __device__ __forceinline__ uint32_t tmem_cols_for(int n) {
     return c;
 }
 
-// 8 BF16 values of row `row` (window-relative t) from segment s at chunk c, zero outside the window
-__device__ __forceinline__ uint4 seg_load(const RowSeg &s, int b, int64_t row, int W, int c) {
-    const int64_t w = row / W;
-    const int t = (int)(row - w * W) + s.shift;
-    if (t < 0 || t >= W) return make_uint4(0, 0, 0, 0);
-    const __nv_bfloat16 *src = s.p + b * s.boff + (w * W + t) * (int64_t)s.ld + 8 * c;
-    return __ldg(reinterpret_cast<const uint4 *>(src));
-}
-
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
 
 // 16-byte global -> shared copy in flight until cp_async_wait_all; zero-filled when !valid
@@ -123,6 +116,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool v
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // address of 8 BF16 values of row `row` of segment s at chunk c, and whether they lie in the window
@@ -134,17 +132,7 @@ __device__ __forceinline__ const __nv_bfloat16 *seg_addr(const RowSeg &s, int b,
     return valid ? s.p + b * s.boff + (w * W + t) * (int64_t)s.ld + 8 * c : s.p;
 }
 
-// 16 consecutive values of one row (16-byte aligned): FP32 loads and stores, BF16 stores
-__device__ __forceinline__ void ld16_f32(const float *src, float (&v)[16]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float4 t = *reinterpret_cast<const float4 *>(src + 4 * q);
-        v[4 * q] = t.x;
-        v[4 * q + 1] = t.y;
-        v[4 * q + 2] = t.z;
-        v[4 * q + 3] = t.w;
-    }
-}
+// 16 consecutive values of one row (16-byte aligned): FP32, FP16 and BF16 stores
 __device__ __forceinline__ void st16_f32(float *dst, const float (&v)[16]) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -160,19 +148,6 @@ __device__ __forceinline__ void st16_f16(__half *dst, const float (&v)[16]) {
     *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
     *reinterpret_cast<uint4 *>(dst + 8) = make_uint4(w[4], w[5], w[6], w[7]);
 }
-__device__ __forceinline__ void ld16_f16(const __half *src, float (&v)[16]) {
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const uint4 t = *reinterpret_cast<const uint4 *>(src + 8 * q);
-        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
-            v[8 * q + 2 * i] = f.x;
-            v[8 * q + 2 * i + 1] = f.y;
-        }
-    }
-}
 __device__ __forceinline__ void st16_bf16(__nv_bfloat16 *dst, const float (&v)[16]) {
     uint32_t w[8];
 #pragma unroll
@@ -185,14 +160,20 @@ __device__ __forceinline__ void st16_bf16(__nv_bfloat16 *dst, const float (&v)[1
 }
 
 // D = A . B^T over the row tiles of both branches, fused epilogue EPI.
+// 256 threads: thread (r = tid % 128, h = tid / 128) owns row r of the tile and half h of the
+// epilogue's channels (TMEM lanes of warp w: 32 (w % 4) ..).  Per tile the epilogue's global
+// operands are loaded into registers before the MMA is waited for, and the next tile's A copies
+// (and B image, at a branch change) are issued as soon as the MMA has read shared memory, so that
+// they are in flight while the epilogue runs.
 template <int EPI>
-__global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
+__global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ uint64_t bar[2];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int r = tid & 127, h = tid >> 7;
     const int KC = p.K / 8;                                   // 16-byte chunks per row
     const uint32_t a_bytes = (uint32_t)kRows * p.K * 2;   // B image follows the A tile
     uint8_t *sA = smem, *sB = smem + a_bytes;
@@ -210,28 +191,58 @@ __global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
     const uint32_t tmem = tslot;
     const int64_t tpb = (p.rows + kRows - 1) / kRows;         // tiles per branch
     int cur_b = -1;
-    uint32_t ph = 0;
-    bool ok = true;
-    const uint32_t idesc = idesc_f16(128, p.N, 1);
-    for (int64_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+    // cp.async copies of one tile: B image at a branch change, A tile in chunk-column layout
+    // (chunks 2j and 2j + 1 of row tid / 2 by threads tid & ~1 and tid | 1, so that a lane pair
+    // reads one 32-byte sector; window boundaries zero-filled)
+    auto issue_tile = [&](int64_t tile) {
         const int b = (int)(tile / tpb);
         const int64_t r0 = (tile - (int64_t)b * tpb) * kRows;
-        // the branch's B image (once per branch change; every earlier MMA has completed here)
         if (b != cur_b) {
             const uint8_t *src = p.bimg + b * p.bimg_boff;
             const int n16 = p.bn * p.K * 2 / 16;
-            for (int i = tid; i < n16; i += 128) cp_async16(smem_u32(sB + 16 * i), src + 16 * i, true);
+            for (int i = tid; i < n16; i += 256) cp_async16(smem_u32(sB + 16 * i), src + 16 * i, true);
             cur_b = b;
         }
-        // A tile: thread = row, chunk-column layout; every copy of the tile in flight at once
-        const int64_t row = r0 + tid;
+        const int cr = tid >> 1, par = tid & 1;
+        const int64_t row = r0 + cr;
         int c = 0;
         for (int si = 0; si < p.nseg; ++si) {
             const RowSeg &s = p.seg[si];
             for (int cc = 0; cc < s.C / 8; ++cc, ++c) {
+                if ((c & 1) != par) continue;
                 bool valid = false;
                 const __nv_bfloat16 *src = row < p.rows ? seg_addr(s, b, row, p.W, cc, valid) : s.p;
-                cp_async16(smem_u32(sA + (size_t)c * kRows * 16 + tid * 16), src, valid && row < p.rows);
+                cp_async16(smem_u32(sA + (size_t)c * kRows * 16 + cr * 16), src, valid && row < p.rows);
+            }
+        }
+    };
+    if (blockIdx.x < p.n_tiles) issue_tile(blockIdx.x);
+    uint32_t ph = 0;
+    bool ok = true;
+    const uint32_t idesc = idesc_f16(128, p.N, 1);
+    const int R = p.R, hr = R / 2, ch0 = h * hr;   // this thread's channels [ch0, ch0 + hr), hr <= 32
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    for (int64_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+        const int b = (int)(tile / tpb);
+        const int64_t row = (tile - (int64_t)b * tpb) * kRows + r;
+        const bool live = row < p.rows;
+        // the epilogue's global operands, in flight during the A copies and the MMA
+        float4 pa[8];                                         // EPI_RES, EPI_DGRAD: aux[row][ch0 ..]
+        uint4 pg[8];                                          // EPI_DZ: tanh(f), then sigmoid(g), [ch0 ..]
+        if (EPI == EPI_RES || EPI == EPI_DGRAD) {
+            const float *src = p.aux + b * p.aux_boff + row * R + ch0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                pa[q] = (live && 4 * q < hr) ? __ldg(reinterpret_cast<const float4 *>(src + 4 * q))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (EPI == EPI_DZ) {
+            const __half *src = p.gate + b * p.gate_boff + row * 2 * R + ch0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool in = live && 8 * q < hr;
+                pg[q] = in ? __ldg(reinterpret_cast<const uint4 *>(src + 8 * q)) : make_uint4(0, 0, 0, 0);
+                pg[4 + q] = in ? __ldg(reinterpret_cast<const uint4 *>(src + R + 8 * q)) : make_uint4(0, 0, 0, 0);
             }
         }
         cp_async_wait_all();
@@ -255,14 +266,14 @@ __global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
             break;
         }
         tc_fence_after();
-        // epilogue: thread = row (TMEM lane = warp * 32 + lane = tid)
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-        const bool live = row < p.rows;
-        const int64_t orow = row;
+        // the MMA has read the A tile and the B image: the next tile's copies may overwrite them
+        if (tile + gridDim.x < p.n_tiles) issue_tile(tile + gridDim.x);
         if (EPI == EPI_CONV) {
-            const int R = p.R;
             const float *bc = p.bias + b * p.bias_boff;
-            for (int c0 = 0; c0 < R; c0 += 16) {
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (16 * g >= hr) break;
+                const int c0 = ch0 + 16 * g;
                 uint32_t fr[16], gr[16];
                 tmem_ld16(tl + c0, fr);
                 tmem_ld16(tl + R + c0, gr);
@@ -276,86 +287,125 @@ __global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
                     z[j] = th[j] * sg[j];
                 }
                 if (p.gate_out) {   // the backward's gate cache: tanh(f), sigmoid(g) in FP16
-                    __half *go = p.gate_out + b * p.gate_boff + orow * 2 * R;
+                    __half *go = p.gate_out + b * p.gate_boff + row * 2 * R;
                     st16_f16(go + c0, th);
                     st16_f16(go + R + c0, sg);
                 }
-                st16_bf16(p.o16 + b * p.o16_boff + orow * R + c0, z);
+                st16_bf16(p.o16 + b * p.o16_boff + row * R + c0, z);
             }
         } else if (EPI == EPI_RES) {
-            const int R = p.R;
             const float *br = p.bias + b * p.bias_boff;
-            for (int c0 = 0; c0 < R; c0 += 16) {
+            const int S = p.N - R, hs = S / 2, s0 = h * hs;   // skip channels [s0, s0 + hs), hs <= 64
+            float *so = S > 0 ? p.skip + b * p.skip_boff + row * S + s0 : nullptr;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (16 * g >= hr) break;
+                const int c0 = ch0 + 16 * g;
                 uint32_t rr[16];
                 tmem_ld16(tl + c0, rr);
                 tmem_ld_wait();
                 if (!live) continue;
                 float v[16];
-                ld16_f32(p.aux + b * p.aux_boff + orow * R + c0, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(rr[j]) + __ldg(br + c0 + j);
-                st16_f32(p.o32 + b * p.o32_boff + orow * R + c0, v);
-                st16_bf16(p.o16 + b * p.o16_boff + orow * R + c0, v);
-            }
-            const int S = p.N - R;
-            const float *bs = p.bias2 ? p.bias2 + b * p.bias_boff : nullptr;
-            for (int c0 = 0; c0 < S; c0 += 16) {
-                uint32_t qr[16];
-                tmem_ld16(tl + R + c0, qr);
-                tmem_ld_wait();
-                if (!live) continue;
-                float *so = p.skip + b * p.skip_boff + orow * S + c0;
-                float v[16];
-                if (p.skip_init) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
-                } else {
-                    ld16_f32(so, v);
+                for (int q = 0; q < 4; ++q) {
+                    v[4 * q] = pa[4 * g + q].x;
+                    v[4 * q + 1] = pa[4 * g + q].y;
+                    v[4 * q + 2] = pa[4 * g + q].z;
+                    v[4 * q + 3] = pa[4 * g + q].w;
                 }
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(qr[j]) + __ldg(bs + c0 + j);
-                st16_f32(so, v);
+                for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(rr[j]) + __ldg(br + c0 + j);
+                st16_f32(p.o32 + b * p.o32_boff + row * R + c0, v);
+                st16_bf16(p.o16 + b * p.o16_boff + row * R + c0, v);
+            }
+            const float *bs = p.bias2 ? p.bias2 + b * p.bias_boff : nullptr;
+            // the skip sums of this thread's half, all loads in flight together
+            float4 ps[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                ps[q] = (live && S > 0 && !p.skip_init && 4 * q < hs) ? *reinterpret_cast<const float4 *>(so + 4 * q)
+                                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (16 * g >= hs) break;
+                uint32_t qr[16];
+                tmem_ld16(tl + R + s0 + 16 * g, qr);
+                tmem_ld_wait();
+                if (!live) continue;
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v[4 * q] = ps[4 * g + q].x;
+                    v[4 * q + 1] = ps[4 * g + q].y;
+                    v[4 * q + 2] = ps[4 * g + q].z;
+                    v[4 * q + 3] = ps[4 * g + q].w;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(qr[j]) + __ldg(bs + s0 + 16 * g + j);
+                st16_f32(so + 16 * g, v);
             }
         } else if (EPI == EPI_DZ) {
-            const int R = p.R;
-            for (int c0 = 0; c0 < R; c0 += 16) {
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (16 * g >= hr) break;
+                const int c0 = ch0 + 16 * g;
                 uint32_t dr[16];
                 tmem_ld16(tl + c0, dr);
                 tmem_ld_wait();
                 if (!live) continue;
-                const __half *gc = p.gate + b * p.gate_boff + orow * 2 * R;
                 float th[16], sg[16], df[16], dg[16];
-                ld16_f16(gc + c0, th);
-                ld16_f16(gc + R + c0, sg);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint32_t wt[4] = {pg[2 * g + q].x, pg[2 * g + q].y, pg[2 * g + q].z, pg[2 * g + q].w};
+                    const uint32_t ws[4] = {pg[4 + 2 * g + q].x, pg[4 + 2 * g + q].y, pg[4 + 2 * g + q].z,
+                                            pg[4 + 2 * g + q].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 ft = __half22float2(*reinterpret_cast<const __half2 *>(&wt[i]));
+                        const float2 fs = __half22float2(*reinterpret_cast<const __half2 *>(&ws[i]));
+                        th[8 * q + 2 * i] = ft.x;
+                        th[8 * q + 2 * i + 1] = ft.y;
+                        sg[8 * q + 2 * i] = fs.x;
+                        sg[8 * q + 2 * i + 1] = fs.y;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const float dz = __uint_as_float(dr[j]);
                     df[j] = dz * sg[j] * (1.f - th[j] * th[j]);
                     dg[j] = dz * th[j] * sg[j] * (1.f - sg[j]);
                 }
-                __nv_bfloat16 *d16 = p.o16 + b * p.o16_boff + orow * 2 * R;
+                __nv_bfloat16 *d16 = p.o16 + b * p.o16_boff + row * 2 * R;
                 st16_bf16(d16 + c0, df);
                 st16_bf16(d16 + R + c0, dg);
             }
         } else {   // EPI_DGRAD
-            const int R = p.R;
-            for (int c0 = 0; c0 < R; c0 += 16) {
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (16 * g >= hr) break;
+                const int c0 = ch0 + 16 * g;
                 uint32_t dr[16];
                 tmem_ld16(tl + c0, dr);
                 tmem_ld_wait();
                 if (!live) continue;
                 float v[16];
-                ld16_f32(p.aux + b * p.aux_boff + orow * R + c0, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(dr[j]);
-                st16_f32(p.o32 + b * p.o32_boff + orow * R + c0, v);
-                st16_bf16(p.o16 + b * p.o16_boff + orow * R + c0, v);
+                for (int q = 0; q < 4; ++q) {
+                    v[4 * q] = pa[4 * g + q].x + __uint_as_float(dr[4 * q]);
+                    v[4 * q + 1] = pa[4 * g + q].y + __uint_as_float(dr[4 * q + 1]);
+                    v[4 * q + 2] = pa[4 * g + q].z + __uint_as_float(dr[4 * q + 2]);
+                    v[4 * q + 3] = pa[4 * g + q].w + __uint_as_float(dr[4 * q + 3]);
+                }
+                st16_f32(p.o32 + b * p.o32_boff + row * R + c0, v);
+                st16_bf16(p.o16 + b * p.o16_boff + row * R + c0, v);
             }
         }
-        // every thread's TMEM reads and shared-memory use of this tile end before the next tile
+        // every thread's TMEM reads of this tile end before the next tile's MMA
         tc_fence_before();
         __syncthreads();
     }
+    // copies issued for a tile that an aborted loop never reached complete before the CTA exits
+    cp_async_wait_all();
     // no MMA of this thread may be in flight when TMEM is released
     if (tid == 0) {
         mma_commit(&bar[1]);
@@ -370,26 +420,37 @@ __global__ void __launch_bounds__(128) k_tc_rows(const RowGemm p) {
 }
 
 // dW += G^T X over the row tiles [blockIdx.x * tiles_per_cta, ...) of branch blockIdx.y.
+// Both operands are MN-major: rows of G and X are copied unchanged (8 channels per 16 bytes),
+// element (mn, k) of a stage at (mn / 8) * 2048 + k * 16 + (mn % 8) * 2, i.e. 8-channel groups
+// 2048 bytes apart and 8-row K groups 128 bytes apart.  In the descriptor of a non-swizzled
+// MN-major operand the stride byte offset is the step between 8-channel groups and the leading
+// byte offset the step between 8-row K groups.  Two stages: the copies of tile i + 1 are in flight while
+// the MMAs of tile i run.  Channels M..127 of A are zero; columns nx..N-1 of B are [1, 0, ...],
+// so that column nx of D is the column sum of G (the bias gradient).
 template <int N>
 __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
+    constexpr uint32_t A_BYTES = 16 * 2048, B_BYTES = (N / 8) * 2048, STAGE = A_BYTES + B_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t bar[3];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     constexpr uint32_t NCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
     const int tid = threadIdx.x, warp = tid >> 5;
-    uint8_t *sA = smem;                       // G^T: [128 rows = channels][K = 128 rows of the tile]
-    uint8_t *sB = smem + 128 * 128 * 2;       // X^T: [N][128]
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int i = 0; i < 3; ++i) mbar_init(&bar[i], 1);
         abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(&tslot, NCOLS);
-    // rows M..127 of G^T stay zero for every tile
-    for (int i = tid; i < 128 * 128 * 2 / 16; i += 128) reinterpret_cast<uint4 *>(sA)[i] = make_uint4(0, 0, 0, 0);
+    // constant parts of both stages (row k = tid): A channel groups >= M / 8 zero, B groups from
+    // nx / 8 on: 1.0 at column nx, zeros after it
+    for (int s = 0; s < 2; ++s) {
+        uint8_t *a = smem + s * STAGE, *bb = a + A_BYTES;
+        for (int mi = p.M / 8; mi < 16; ++mi) *reinterpret_cast<uint4 *>(a + mi * 2048 + tid * 16) = make_uint4(0, 0, 0, 0);
+        for (int ni = p.nx / 8; ni < N / 8; ++ni)
+            *reinterpret_cast<uint4 *>(bb + ni * 2048 + tid * 16) = make_uint4(ni == p.nx / 8 ? 0x3F80u : 0u, 0, 0, 0);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -397,72 +458,73 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
     const int b = blockIdx.y;
     const int64_t t_begin = (int64_t)blockIdx.x * p.tiles_per_cta;
     const int64_t t_end = std::min<int64_t>(p.tiles, t_begin + p.tiles_per_cta);
-    const uint32_t idesc = idesc_f16(128, N, 1);
-    uint32_t ph = 0;
-    int issued = 0;
+    const int64_t n = t_end - t_begin;
+    // copies of one tile into stage s: rows tid / 2 and tid / 2 + 64, channel groups of parity tid & 1
+    auto issue = [&](int64_t tile, int s) {
+        uint8_t *a = smem + s * STAGE, *bb = a + A_BYTES;
+        const int par = tid & 1;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int k = (tid >> 1) + 64 * pass;
+            const int64_t row = tile * kRows + k;
+            const bool live = row < p.rows;
+            const __nv_bfloat16 *g = p.G + b * p.g_boff + (live ? row : 0) * p.ldg;
+            for (int mi = par; mi < p.M / 8; mi += 2) cp_async16(smem_u32(a + mi * 2048 + k * 16), g + 8 * mi, live);
+            int ni = 0;
+            for (int si = 0; si < p.nxs; ++si) {
+                const RowSeg &sg = p.xs[si];
+                bool valid = false;
+                const __nv_bfloat16 *x0 = live ? seg_addr(sg, b, row, p.W, 0, valid) : sg.p;
+                for (int cc = 0; cc < sg.C / 8; ++cc, ++ni) {
+                    if ((ni & 1) != par) continue;
+                    cp_async16(smem_u32(bb + ni * 2048 + k * 16), valid ? x0 + 8 * cc : sg.p, valid);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    const uint32_t idesc = idesc_f16(128, N, 1) | (1u << 15) | (1u << 16);   // A and B MN-major
+    if (n > 0) issue(t_begin, 0);
+    if (n > 1) issue(t_begin + 1, 1);
     bool ok = true;
-    for (int64_t tile = t_begin; tile < t_end; ++tile) {
-        const int64_t row = tile * kRows + tid;   // thread = row of the tile = K index of the MMA
-        const bool live = row < p.rows;
-        // G^T: element (m, k = tid) at chunk k / 8, row m, position k % 8
-        const uint32_t kofs = (uint32_t)(tid >> 3) * 128 * 16 + (uint32_t)(tid & 7) * 2;
-        const __nv_bfloat16 *g = p.G + b * p.g_boff + row * p.ldg;
-        {
-            uint4 v[16];                      // M <= 128: at most 16 chunks, all loads issued first
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-                v[q] = (live && 8 * q < p.M) ? __ldg(reinterpret_cast<const uint4 *>(g + 8 * q)) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                if (8 * q >= p.M) break;
-                const uint16_t *e = reinterpret_cast<const uint16_t *>(&v[q]);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) *reinterpret_cast<uint16_t *>(sA + kofs + (8 * q + i) * 16) = e[i];
-            }
-        }
-        // X^T: element (n, k = tid) at chunk k / 8, row n, position k % 8
-        const uint32_t kofsb = (uint32_t)(tid >> 3) * N * 16 + (uint32_t)(tid & 7) * 2;
-        {
-            uint4 v[N / 8];                   // all X chunks of the row, loads issued first
-            const int c0 = p.xs[0].C / 8;     // chunks of the first segment; the rest from the second
-            const int cx = p.nx / 8;          // beyond: the ones column (BF16 1.0 at column nx) and zeros
-#pragma unroll
-            for (int k = 0; k < N / 8; ++k)
-                v[k] = !live ? make_uint4(0, 0, 0, 0)
-                             : (k < c0 ? seg_load(p.xs[0], b, row, p.W, k)
-                                       : (k < cx ? seg_load(p.xs[1], b, row, p.W, k - c0)
-                                                 : make_uint4(k == cx ? 0x3F80u : 0u, 0, 0, 0)));
-#pragma unroll
-            for (int k = 0; k < N / 8; ++k) {
-                const uint16_t *e = reinterpret_cast<const uint16_t *>(&v[k]);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) *reinterpret_cast<uint16_t *>(sB + kofsb + (8 * k + i) * 16) = e[i];
-            }
-        }
+    for (int64_t i = 0; i < n; ++i) {
+        const int s = (int)(i & 1);
+        if (i + 1 < n)
+            cp_async_wait_group<1>();
+        else
+            cp_async_wait_group<0>();
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            const uint32_t a0 = smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
             for (int ks = 0; ks < 8; ++ks) {
-                const uint64_t ad = sdesc(a0 + ks * 2 * 128 * 16, 128 * 16, 128);
-                const uint64_t bd = sdesc(b0 + ks * 2 * N * 16, N * 16, 128);
-                mma_f16(tmem, ad, bd, idesc, (issued > 0 || ks > 0) ? 1u : 0u);
+                const uint64_t ad = sdesc(a0 + ks * 256, 128, 2048);
+                const uint64_t bd = sdesc(b0 + ks * 256, 128, 2048);
+                mma_f16(tmem, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
             }
-            mma_commit(&bar[0]);
+            mma_commit(&bar[s]);
         }
-        ++issued;
-        // the tile's shared memory is rewritten by the next tile: wait for the MMAs to read it
-        const bool w_ok = mbar_wait(&bar[0], ph & 1, &abort_flag, p.err, 80, kWaitNs);
-        ++ph;
-        if (__syncthreads_or(!w_ok)) {
-            ok = false;
-            break;
+        if (i + 2 < n) {
+            // stage s takes tile i + 2 once the MMAs of tile i have read it
+            const bool w_ok = mbar_wait(&bar[s], (uint32_t)(i >> 1) & 1, &abort_flag, p.err, 80, kWaitNs);
+            if (__syncthreads_or(!w_ok)) {
+                ok = false;
+                break;
+            }
+            issue(t_begin + i + 2, s);
         }
     }
-    if (ok && issued > 0) {
+    cp_async_wait_all();
+    // every MMA of the CTA has completed (and written D) once this commit arrives
+    bool d_ok = true;
+    if (tid == 0) {
+        mma_commit(&bar[2]);
+        d_ok = mbar_wait_drain(&bar[2], 0, p.err, 81, kWaitNs);
+    }
+    if (__syncthreads_or(!d_ok)) ok = false;
+    if (ok && n > 0) {
         tc_fence_after();
         // D[m][n] in TMEM lane m: warps whose lanes hold m < M add their rows
         const int m = tid;
@@ -482,10 +544,6 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
                 }
             }
         }
-    }
-    if (tid == 0) {
-        mma_commit(&bar[1]);
-        mbar_wait_drain(&bar[1], 0, p.err, 81, kWaitNs);
     }
     tc_fence_before();
     __syncthreads();
@@ -593,7 +651,7 @@ gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
     const size_t smem = std::max<size_t>((size_t)kRows * p.K * 2 + (size_t)p.bn * p.K * 2 + 128, 80 * 1024);
     const int grid = (int)std::min<int64_t>(p.n_tiles, (int64_t)sms * (smem <= 100 * 1024 ? 2 : 1));
     ProfScope prof("k_tc_rows", st);
-    k_tc_rows<EPI><<<grid, 128, smem, st>>>(p);
+    k_tc_rows<EPI><<<grid, 256, smem, st>>>(p);
     note_launch();
     GWE_CUDA_TRY(cudaGetLastError());
     return GWE_OK;
@@ -601,13 +659,14 @@ gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
 
 gwe_status run_wgrad(WgGemm p, int sms, cudaStream_t st) {
     p.tiles = (p.rows + kRows - 1) / kRows;
-    // about four CTAs per SM over both branches, at least 8 tiles each
-    const int64_t want = std::max<int64_t>(1, (int64_t)sms * 2);
-    p.tiles_per_cta = (int)std::max<int64_t>(8, (p.tiles + want - 1) / want);
+    // two stages of [G^T: 128 x 128 | X^T: N x 128] BF16; one CTA per SM when they exceed half of
+    // the shared memory (this also keeps two 256-column TMEM allocations off one SM), else two
+    const size_t smem = 2 * ((size_t)128 * 128 * 2 + (size_t)p.N * 128 * 2) + 128;
+    const int per_sm = smem > 113 * 1024 ? 1 : 2;
+    // one wave over both branches, contiguous tile ranges (fewer partial sums to add atomically)
+    const int64_t per_branch = std::max<int64_t>(1, (int64_t)sms * per_sm / 2);
+    p.tiles_per_cta = (int)std::max<int64_t>(1, (p.tiles + per_branch - 1) / per_branch);
     dim3 grid((unsigned)((p.tiles + p.tiles_per_cta - 1) / p.tiles_per_cta), 2);
-    // with 256 TMEM columns (N > 128) at most two CTAs may share an SM: ask for at least 80 KB
-    const size_t smem = std::max<size_t>((size_t)128 * 128 * 2 + (size_t)p.N * 128 * 2 + 128,
-                                         p.N > 128 ? 80 * 1024 : 0);
     ProfScope prof("k_tc_wgrad", st);
     // N = nx + 16: the segments' columns, then the ones column for the bias gradient (nx = 32, 64, 128)
     if (p.N == 48)
@@ -628,8 +687,8 @@ gwe_status run_wgrad(WgGemm p, int sms, cudaStream_t st) {
 }  // namespace
 
 bool tc_backward_supported(const Dims &d) {
-    return d.k == 2 && d.R % 16 == 0 && d.S % 16 == 0 && 2 * d.R <= 128 && d.R + d.S <= 256 && d.S <= 128 &&
-           d.R >= 16;
+    // row-GEMM epilogues split the channels between two threads in groups of 16
+    return d.k == 2 && d.R % 32 == 0 && d.S % 32 == 0 && 2 * d.R <= 128 && d.R + d.S <= 256 && d.S <= 128;
 }
 
 void tc_backward_release(void *&state) {
@@ -679,7 +738,10 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
         t->model = mi;
         t->stamp = stamp;
     }
-    const int C = std::min(batch, 64);                       // windows per chunk
+    const int C = std::min(batch, 128);                      // windows per chunk
+    // BF16 handles: the fused forward kernel stores the stack inputs and skip sums; otherwise a
+    // forward pass of row GEMMs computes them
+    const bool fused_save = m->precision == GWE_BF16 && tc_save_supported(m, W);
     const size_t rows = (size_t)C * W, rows2 = 2 * rows;
     GWE_CUDA_TRY(t->err.ensure(256));
     GWE_CUDA_TRY(cudaMemsetAsync(t->err.ptr, 0, sizeof(int), st));
@@ -710,6 +772,7 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
         const int64_t rb = (int64_t)Cc * W;          // rows per branch
         const int64_t xo = rb * R;                   // branch offset of [row][R] arrays (this chunk)
         const float *sH = xH + (int64_t)c0 * W, *sL = xL + (int64_t)c0 * W;
+        const int64_t xs_stride = 2 * rb * R;        // stack stride of xsave (this chunk)
         // one layer's forward: conv (a optional) then res (+ skip when skip_mode >= 0)
         auto layer_fwd = [&](int l, float *xin32, __nv_bfloat16 *xin16, float *xout32, __nv_bfloat16 *xout16,
                              __half *gout, __nv_bfloat16 *zout, int skip_mode) -> gwe_status {
@@ -763,7 +826,10 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
             return run_rows<EPI_RES>(q, sms, st);
         };
         // ---- forward keeping each stack's input and the skip sums
-        {
+        if (fused_save) {
+            r = tc_forward_save(m, mi, sH, sL, Cc, W, t->dskip32.as<float>(), xsave, t->skip.as<float>(), st);
+            if (r != GWE_OK) return r;
+        } else {
             float *xa32 = x32, *xb32 = x32 + rows2 * R;
             __nv_bfloat16 *xa16 = x16, *xb16 = x16 + rows2 * R;
             r = fp32_input_proj(m, mi, sH, sL, rb, xa32, st);
@@ -772,7 +838,7 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
             note_launch();
             for (int l = 0; l < L; ++l) {
                 if (l % lps == 0)
-                    GWE_CUDA_TRY(cudaMemcpyAsync(xsave + (size_t)(l / lps) * rows2 * R, xa32, sizeof(float) * 2 * rb * R,
+                    GWE_CUDA_TRY(cudaMemcpyAsync(xsave + (size_t)(l / lps) * xs_stride, xa32, sizeof(float) * 2 * rb * R,
                                                  cudaMemcpyDeviceToDevice, st));
                 r = layer_fwd(l, xa32, xa16, xb32, xb16, nullptr, z16, l == 0 ? 1 : 0);
                 if (r != GWE_OK) return r;
@@ -791,7 +857,7 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
         GWE_CUDA_TRY(cudaMemsetAsync(t->dx32[hi].ptr, 0, sizeof(float) * 2 * rb * R, st));
         GWE_CUDA_TRY(cudaMemsetAsync(t->dx16[hi].ptr, 0, 2 * 2 * rb * R, st));
         for (int k = stacks - 1; k >= 0; --k) {
-            GWE_CUDA_TRY(cudaMemcpyAsync(x32, xsave + (size_t)k * rows2 * R, sizeof(float) * 2 * rb * R,
+            GWE_CUDA_TRY(cudaMemcpyAsync(x32, xsave + (size_t)k * xs_stride, sizeof(float) * 2 * rb * R,
                                          cudaMemcpyDeviceToDevice, st));
             k_f32_to_bf16<<<1024, 256, 0, st>>>(x32, x16, 2 * rb * R);
             note_launch();
@@ -907,7 +973,11 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
                                 gL ? gL + (int64_t)c0 * W : nullptr, st);
         if (r != GWE_OK) return r;
     }
-    // a device-side wait that gave up leaves its site in the error word
+    // a device-side wait that gave up leaves its site in the error word (the fused forward's in its own)
+    if (fused_save) {
+        r = tc_check(m, st);
+        if (r != GWE_OK) return r;
+    }
     int e = 0;
     GWE_CUDA_TRY(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GWE_CUDA_TRY(cudaStreamSynchronize(st));

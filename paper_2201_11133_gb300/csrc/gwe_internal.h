@@ -169,6 +169,13 @@ void tc_release(gwe_model *m);
 gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, const Segments &sg, int window, int stride,
                       const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st);
 bool tc_supported(const Dims &d);
+// whether tc_forward_save can run for this handle and window length
+bool tc_save_supported(gwe_model *m, int W);
+// Fused forward of member mi over nwin back-to-back windows of W samples that also stores every
+// stack's input x (FP32 [stack][branch][window][W][R]) and the pre-ReLU skip sum (FP32
+// [branch][window][W][S]); logits go to `logits` ([nwin][W]).
+gwe_status tc_forward_save(gwe_model *m, int mi, const float *xH, const float *xL, int nwin, int W, float *logits,
+                           float *save_x, float *save_skip, cudaStream_t st);
 
 // whiten.cu: Welch PSD (FP64 accumulation) and spectral whitening of one detector's strain
 gwe_status whiten_run(const float *x, int64_t n, double fs, int seg, float *out, cudaStream_t st);
