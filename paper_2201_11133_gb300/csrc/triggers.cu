@@ -10,17 +10,21 @@
 //
 // Steps (all kernels, ordered so that results come out sorted by series and
 // index without a sort):
-//   1. per 256-sample block of every series: max, min, first and last argmin
-//      (lets the long prominence and width walks skip whole blocks);
+//   1. a summary tree per series (256-sample blocks, then nodes of 32 nodes):
+//      max, min, first and last argmin, so that the prominence and width
+//      walks pass long stretches in a few steps;
 //   2. candidate count per 8192-sample chunk -> exclusive scan -> ordered write
 //      of every local maximum (plateau midpoint) whose height passes;
-//   3. per candidate: prominence and width at half prominence in FP64 with the
-//      same operation order as the definition (no contraction), keep flag;
+//   3. per candidate: prominence and width at half prominence in FP64 with
+//      the same operation order as the definition (no contraction), keep
+//      flag; one thread per candidate over a shared-memory window around its
+//      chunk, one warp on the summary tree for the few whose walks leave it;
 //   4. ordered compaction of kept peaks; per-series start offsets;
 //   5. per model-0 peak: coincidence test against the other models' peaks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -30,6 +34,7 @@ namespace gwe {
 namespace {
 
 constexpr int kBS = 256;       // samples per statistics block
+constexpr int kFan = 32;       // children per node of the summary tree above the blocks
 constexpr int kCH = 8192;      // samples per candidate chunk
 constexpr int kT = 256;        // threads per block
 
@@ -39,7 +44,8 @@ struct Series {
     int W, stride;
     __device__ __forceinline__ float at(int64_t g) const {
         if (g < W) return base[g];
-        const int64_t w = (g - W) / stride + 1;
+        const uint64_t r = (uint64_t)(g - W);
+        const int64_t w = (r < 0x100000000ull ? (int64_t)((uint32_t)r / (uint32_t)stride) : (int64_t)(r / (uint64_t)stride)) + 1;
         return base[w * W + (g - w * stride)];
     }
 };
@@ -114,19 +120,20 @@ __global__ void k_stats(Geo g, float *bmax, float *bmin, int64_t *amin_lo, int64
 }
 
 // local maximum test at a left edge i; returns the peak index (plateau midpoint) or -1
-__device__ __forceinline__ int64_t peak_at(const Series &v, int64_t i, double thr) {
+// thr: the height threshold (a float, so the float comparison is the definition's)
+__device__ __forceinline__ int64_t peak_at(const Series &v, int64_t i, float thr) {
     if (i < 1 || i > v.n - 2) return -1;
     const float xi = v.at(i);
     if (!(v.at(i - 1) < xi)) return -1;
     int64_t ia = i + 1;
     while (ia < v.n - 1 && v.at(ia) == xi) ++ia;
     if (!(v.at(ia) < xi)) return -1;
-    if (!((double)xi >= thr)) return -1;
+    if (!(xi >= thr)) return -1;
     return (i + (ia - 1)) / 2;
 }
 
 // 2. candidates: mode 0 counts per chunk, mode 1 writes in order
-__global__ void k_cand(Geo g, double thr, int mode, int64_t *counts, const int64_t *offsets, int64_t *cand_idx,
+__global__ void k_cand(Geo g, float thr, int mode, int64_t *counts, const int64_t *offsets, int64_t *cand_idx,
                        int *cand_ser, int64_t nchunk) {
     __shared__ int sh[kT / 32 + 1];
     const int s = blockIdx.y;
@@ -171,115 +178,440 @@ __global__ void k_scan(const int64_t *in, int64_t *out, int64_t n) {
     if (threadIdx.x == 0) out[n] = carry;
 }
 
-// 3. prominence and width of one candidate
-__global__ void k_eval(Geo g, int64_t ncand, const int64_t *cand_idx, const int *cand_ser, const float *bmax,
-                       const float *bmin, const int64_t *amin_lo, const int64_t *amin_hi, double min_width,
-                       int *keep, double *o_h, double *o_pr, double *o_wd) {
-    const int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci >= ncand) return;
-    const int s = cand_ser[ci];
-    const int64_t p = cand_idx[ci];
+// 1b. statistics of the next tree level: node j summarises nodes [32 j, 32 j + 32) of the level
+// below (one thread per node)
+__global__ void k_stats_up(int64_t cnt_lo, int64_t cnt, int n_series, const float *bmax, const float *bmin,
+                           const int64_t *alo, const int64_t *ahi, float *smax, float *smin, int64_t *slo,
+                           int64_t *shi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt * n_series) return;
+    const int s = (int)(i / cnt);
+    const int64_t j = i - (int64_t)s * cnt;
+    const int64_t b0 = (int64_t)s * cnt_lo + j * kFan, b1 = (int64_t)s * cnt_lo + min((j + 1) * kFan, cnt_lo);
+    float mx = -INFINITY, mn = INFINITY;
+    int64_t lo = INT64_MAX, hi = -1;
+    for (int64_t b = b0; b < b1; ++b) {
+        mx = fmaxf(mx, bmax[b]);
+        const float m = bmin[b];
+        if (m < mn) { mn = m; lo = alo[b]; hi = ahi[b]; }
+        else if (m == mn) { hi = ahi[b]; }
+    }
+    smax[i] = mx; smin[i] = mn; slo[i] = lo; shi[i] = hi;
+}
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// (value, lane) minimum over the warp; ties go to the lower lane
+__device__ __forceinline__ void warp_argmin(float &m, int &l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float om = __shfl_xor_sync(kFull, m, o);
+        const int ol = __shfl_xor_sync(kFull, l, o);
+        if (om < m || (om == m && ol < l)) { m = om; l = ol; }
+    }
+}
+
+// Summary tree of the series: level 1 = blocks of kBS samples, level l + 1 = nodes of kFan level-l
+// nodes, up to the first level with at most kFan nodes.  Per node: max, min, first and last argmin.
+constexpr int kMaxLv = 8;
+struct Tree {
+    const float *MX[kMaxLv], *MN[kMaxLv];      // [series][cnt[l]] (index 0 unused)
+    const int64_t *AL[kMaxLv], *AH[kMaxLv];
+    int64_t cnt[kMaxLv];
+    int top;
+};
+// one series' view of the tree (level l node j of series s at [s * cnt[l] + j]); the tree stays
+// in the kernel's parameter space
+struct STree {
+    const Tree &t;
+    int64_t s;
+    int top;
+    __device__ __forceinline__ float mx(int l, int64_t j) const { return t.MX[l][s * t.cnt[l] + j]; }
+    __device__ __forceinline__ float mn(int l, int64_t j) const { return t.MN[l][s * t.cnt[l] + j]; }
+    __device__ __forceinline__ int64_t al(int l, int64_t j) const { return t.AL[l][s * t.cnt[l] + j]; }
+    __device__ __forceinline__ int64_t ah(int l, int64_t j) const { return t.AH[l][s * t.cnt[l] + j]; }
+    __device__ __forceinline__ int64_t cnt(int l) const { return t.cnt[l]; }
+};
+__device__ __forceinline__ int64_t span_of(int l) { return (int64_t)kBS << (5 * (l - 1)); }
+
+// The walks below give the same results as walking sample by sample (the definition).  A warp
+// examines up to 32 consecutive samples or nodes per step (lane 0 nearest the peak): it climbs the
+// tree through the siblings of the nodes that hold the peak, takes whole nodes from their summaries
+// while the walk would pass all of them, and descends into the first node it would not pass.
+
+// Prominence base on the left of peak p: minimum of the samples from p down to the first sample
+// above xp (exclusive); on ties the largest index (the first met walking down).
+__device__ void prom_left(const Series &v, const STree &u, int64_t p, float xp, int lane, float &lmin, int64_t &lb) {
+    lmin = xp;
+    lb = p;
+    auto samples = [&](int64_t hi, int64_t lo) -> bool {
+        for (int64_t base = hi; base >= lo; base -= 32) {
+            const int64_t k = base - lane;
+            const bool in = k >= lo;
+            const float x = in ? v.at(k) : 0.f;
+            const unsigned up = __ballot_sync(kFull, in && x > xp);
+            const int nl = up ? __ffs(up) - 1 : 32;
+            float m = (in && lane < nl) ? x : INFINITY;
+            int l = lane;
+            warp_argmin(m, l);
+            if (m < lmin) { lmin = m; lb = base - l; }
+            if (up) return true;
+        }
+        return false;
+    };
+    // nodes [lo, hi] of level lv, downwards; true once a sample above xp is met
+    auto nodes = [&](int lv, int64_t hi, int64_t lo) -> bool {
+        for (int64_t base = hi; base >= lo; base -= 32) {
+            const int64_t j = base - lane;
+            const bool in = j >= lo;
+            const unsigned up = __ballot_sync(kFull, in && u.mx(lv, in ? j : lo) > xp);
+            const int nl = up ? __ffs(up) - 1 : 32;
+            float m = (in && lane < nl) ? u.mn(lv, j) : INFINITY;
+            int l = lane;
+            warp_argmin(m, l);
+            if (m < lmin) { lmin = m; lb = u.ah(lv, base - l); }
+            if (up) {
+                // descend into node base - nl: its children from the top, down to the first one
+                // above xp, then that block's samples
+                int64_t nd = base - nl;
+                for (int c = lv - 1; c >= 1; --c) {
+                    const int64_t clo = nd * kFan, chi = min(clo + kFan, u.cnt(c)) - 1;
+                    const int64_t jj = chi - lane;
+                    const bool cin = jj >= clo;
+                    const unsigned cup = __ballot_sync(kFull, cin && u.mx(c, cin ? jj : clo) > xp);
+                    const int cn = cup ? __ffs(cup) - 1 : 32;
+                    float cm = (cin && lane < cn) ? u.mn(c, jj) : INFINITY;
+                    int cl = lane;
+                    warp_argmin(cm, cl);
+                    if (cm < lmin) { lmin = cm; lb = u.ah(c, chi - cl); }
+                    nd = chi - cn;
+                }
+                return samples(nd * kBS + kBS - 1, nd * kBS);
+            }
+        }
+        return false;
+    };
+    int64_t c = p / kBS;
+    if (samples(p, c * kBS)) return;
+    for (int lv = 1; lv <= u.top; ++lv, c /= kFan)
+        if (nodes(lv, c - 1, lv == u.top ? 0 : (c / kFan) * kFan)) return;
+}
+
+// mirrored: samples from p up to the first sample above xp; on ties the smallest index
+__device__ void prom_right(const Series &v, const STree &u, int64_t p, float xp, int lane, float &rmin,
+                           int64_t &rb) {
+    rmin = xp;
+    rb = p;
+    auto samples = [&](int64_t lo, int64_t hi) -> bool {
+        for (int64_t base = lo; base <= hi; base += 32) {
+            const int64_t k = base + lane;
+            const bool in = k <= hi;
+            const float x = in ? v.at(k) : 0.f;
+            const unsigned up = __ballot_sync(kFull, in && x > xp);
+            const int nl = up ? __ffs(up) - 1 : 32;
+            float m = (in && lane < nl) ? x : INFINITY;
+            int l = lane;
+            warp_argmin(m, l);
+            if (m < rmin) { rmin = m; rb = base + l; }
+            if (up) return true;
+        }
+        return false;
+    };
+    auto nodes = [&](int lv, int64_t lo, int64_t hi) -> bool {
+        for (int64_t base = lo; base <= hi; base += 32) {
+            const int64_t j = base + lane;
+            const bool in = j <= hi;
+            const unsigned up = __ballot_sync(kFull, in && u.mx(lv, in ? j : hi) > xp);
+            const int nl = up ? __ffs(up) - 1 : 32;
+            float m = (in && lane < nl) ? u.mn(lv, j) : INFINITY;
+            int l = lane;
+            warp_argmin(m, l);
+            if (m < rmin) { rmin = m; rb = u.al(lv, base + l); }
+            if (up) {
+                int64_t nd = base + nl;
+                for (int c = lv - 1; c >= 1; --c) {
+                    const int64_t clo = nd * kFan, chi = min(clo + kFan, u.cnt(c)) - 1;
+                    const int64_t jj = clo + lane;
+                    const bool cin = jj <= chi;
+                    const unsigned cup = __ballot_sync(kFull, cin && u.mx(c, cin ? jj : chi) > xp);
+                    const int cn = cup ? __ffs(cup) - 1 : 32;
+                    float cm = (cin && lane < cn) ? u.mn(c, jj) : INFINITY;
+                    int cl = lane;
+                    warp_argmin(cm, cl);
+                    if (cm < rmin) { rmin = cm; rb = u.al(c, clo + cl); }
+                    nd = clo + cn;
+                }
+                return samples(nd * kBS, min(nd * kBS + kBS, v.n) - 1);
+            }
+        }
+        return false;
+    };
+    int64_t c = p / kBS;
+    if (samples(p, min((c + 1) * kBS, v.n) - 1)) return;
+    for (int lv = 1; lv <= u.top; ++lv, c /= kFan)
+        if (nodes(lv, c + 1, lv == u.top ? u.cnt(lv) - 1 : min((c / kFan + 1) * kFan, u.cnt(lv)) - 1)) return;
+}
+
+// Width walk on the left: the first k from p downwards with k <= lb or !(h < x[k]).  A node is
+// passed when it lies above lb and all its samples are above h.
+__device__ int64_t width_left(const Series &v, const STree &u, int64_t p, int64_t lb, double h, int lane) {
+    int64_t k = lb;
+    auto samples = [&](int64_t hi, int64_t lo) -> bool {   // lo >= lb
+        for (int64_t base = hi; base >= lo; base -= 32) {
+            const int64_t kk = base - lane;
+            const bool in = kk >= lo;
+            const bool stop = in && (kk <= lb || !(h < (double)v.at(kk)));
+            const unsigned st = __ballot_sync(kFull, stop);
+            if (st) { k = base - (__ffs(st) - 1); return true; }
+        }
+        return false;
+    };
+    auto passes = [&](int lv, int64_t j) -> bool { return j * span_of(lv) > lb && h < (double)u.mn(lv, j); };
+    auto nodes = [&](int lv, int64_t hi, int64_t lo) -> bool {
+        for (int64_t base = hi; base >= lo; base -= 32) {
+            const int64_t j = base - lane;
+            const unsigned st = __ballot_sync(kFull, j >= lo && !passes(lv, j));
+            if (st) {
+                int64_t nd = base - (__ffs(st) - 1);
+                for (int c = lv - 1; c >= 1; --c) {
+                    const int64_t clo = nd * kFan, chi = min(clo + kFan, u.cnt(c)) - 1;
+                    const int64_t jj = chi - lane;
+                    const unsigned cst = __ballot_sync(kFull, jj >= clo && !passes(c, jj));
+                    nd = chi - (__ffs(cst) - 1);
+                }
+                return samples(nd * kBS + kBS - 1, max(nd * kBS, lb));
+            }
+        }
+        return false;
+    };
+    int64_t c = p / kBS;
+    if (samples(p, max(c * kBS, lb))) return k;
+    for (int lv = 1; lv <= u.top; ++lv, c /= kFan)
+        if (nodes(lv, c - 1, lv == u.top ? 0 : (c / kFan) * kFan)) return k;
+    return k;
+}
+
+// Width walk on the right: the first k from p upwards with k >= rb or !(h < x[k]).
+__device__ int64_t width_right(const Series &v, const STree &u, int64_t p, int64_t rb, double h, int lane) {
+    int64_t k = rb;
+    auto samples = [&](int64_t lo, int64_t hi) -> bool {   // hi <= rb
+        for (int64_t base = lo; base <= hi; base += 32) {
+            const int64_t kk = base + lane;
+            const bool in = kk <= hi;
+            const bool stop = in && (kk >= rb || !(h < (double)v.at(kk)));
+            const unsigned st = __ballot_sync(kFull, stop);
+            if (st) { k = base + (__ffs(st) - 1); return true; }
+        }
+        return false;
+    };
+    auto passes = [&](int lv, int64_t j) -> bool {
+        return (j + 1) * span_of(lv) - 1 < rb && h < (double)u.mn(lv, j);
+    };
+    auto nodes = [&](int lv, int64_t lo, int64_t hi) -> bool {
+        for (int64_t base = lo; base <= hi; base += 32) {
+            const int64_t j = base + lane;
+            const unsigned st = __ballot_sync(kFull, j <= hi && !passes(lv, j));
+            if (st) {
+                int64_t nd = base + (__ffs(st) - 1);
+                for (int c = lv - 1; c >= 1; --c) {
+                    const int64_t clo = nd * kFan, chi = min(clo + kFan, u.cnt(c)) - 1;
+                    const int64_t jj = clo + lane;
+                    const unsigned cst = __ballot_sync(kFull, jj <= chi && !passes(c, jj));
+                    nd = clo + (__ffs(cst) - 1);
+                }
+                return samples(nd * kBS, min(nd * kBS + kBS - 1, rb));
+            }
+        }
+        return false;
+    };
+    int64_t c = p / kBS;
+    if (samples(p, min(c * kBS + kBS - 1, rb))) return k;
+    for (int lv = 1; lv <= u.top; ++lv, c /= kFan)
+        if (nodes(lv, c + 1, lv == u.top ? u.cnt(lv) - 1 : min((c / kFan + 1) * kFan, u.cnt(lv)) - 1)) return k;
+    return k;
+}
+
+// 3b. prominence and width of the candidates whose walks leave the shared-memory window of
+// k_eval_local (list[0 .. *count)), one warp each, on the summary tree
+__global__ void k_eval_tree(Geo g, const int64_t *list, const int64_t *count, const int64_t *cand_idx,
+                            const int *cand_ser, const Tree t, double min_width, int *keep, double *o_h, double *o_pr,
+                            double *o_wd) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nlong = *count;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nlong; wi += nwarps) {
+        const int64_t ci = list[wi];
+        const int s = cand_ser[ci];
+        const int64_t p = cand_idx[ci];
+        const Series v = g.series(s);
+        const STree u{t, (int64_t)s, t.top};
+        const float xp = v.at(p);
+        float lmin, rmin;
+        int64_t lb, rb;
+        prom_left(v, u, p, xp, lane, lmin, lb);
+        prom_right(v, u, p, xp, lane, rmin, rb);
+        const double dxp = (double)xp;
+        const double base = (double)lmin > (double)rmin ? (double)lmin : (double)rmin;
+        const double pr = __dsub_rn(dxp, base);
+        const double h = __dsub_rn(dxp, __dmul_rn(pr, 0.5));
+        // width at half prominence, interpolated between the samples on either side of h
+        int64_t k = width_left(v, u, p, lb, h, lane);
+        double lip = (double)k;
+        {
+            const double xk = (double)v.at(k);
+            if (xk < h) lip = __dadd_rn(lip, __ddiv_rn(__dsub_rn(h, xk), __dsub_rn((double)v.at(k + 1), xk)));
+        }
+        k = width_right(v, u, p, rb, h, lane);
+        double rip = (double)k;
+        {
+            const double xk = (double)v.at(k);
+            if (xk < h) rip = __dsub_rn(rip, __ddiv_rn(__dsub_rn(h, xk), __dsub_rn((double)v.at(k - 1), xk)));
+        }
+        if (lane == 0) {
+            const double wd = __dsub_rn(rip, lip);
+            keep[ci] = (wd >= min_width) ? 1 : 0;
+            o_h[ci] = dxp;
+            o_pr[ci] = pr;
+            o_wd[ci] = wd;
+        }
+    }
+}
+
+// order-preserving unsigned key of a float (-0 taken as +0): a < b  <=>  fkey(a) < fkey(b)
+__device__ __forceinline__ unsigned fkey(float x) {
+    const unsigned u = __float_as_uint(x + 0.0f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// 3a. prominence and width of the candidates of one kCH-sample chunk (blockIdx.x) of series
+// blockIdx.y over the chunk and kHalo samples on either side held in shared memory, one warp per
+// candidate, 32 samples per step (lane 0 nearest the peak), with the results of the definition's
+// sample-by-sample walks: the running minimum changes only at a strictly smaller sample, and the
+// width test h < (double)x is x > hf with hf the largest float <= h.  A candidate whose
+// prominence walk reaches the edge of the window (not the end of the series) goes to the list for
+// k_eval_tree.
+constexpr int kHalo = 2048;
+__global__ void __launch_bounds__(kT) k_eval_local(Geo g, int64_t nchunk, const int64_t *offsets,
+                                                     const int64_t *cand_idx, double min_width, int64_t mw_int,
+                                                     int *keep,
+                                                     double *o_h, double *o_pr, double *o_wd, int64_t *list,
+                                                     unsigned long long *count) {
+    __shared__ float sm[kCH + 2 * kHalo];
+    const int s = blockIdx.y;
+    const int64_t c = blockIdx.x;
+    const int64_t beg = offsets[(int64_t)s * nchunk + c], end = offsets[(int64_t)s * nchunk + c + 1];
+    if (beg == end) return;
     const Series v = g.series(s);
-    const float *BX = bmax + (int64_t)s * g.nblk;
-    const float *BN = bmin + (int64_t)s * g.nblk;
-    const int64_t *AL = amin_lo + (int64_t)s * g.nblk;
-    const int64_t *AH = amin_hi + (int64_t)s * g.nblk;
-    const float xp = v.at(p);
-    const int64_t pb = p / kBS;
-
-    // left: walk down while samples <= xp, tracking the strict minimum seen first
-    float lmin = xp;
-    int64_t lb = p;
-    {
-        bool stop = false;
-        for (int64_t k = p; k >= pb * kBS; --k) {
-            const float x = v.at(k);
-            if (x > xp) { stop = true; break; }
-            if (x < lmin) { lmin = x; lb = k; }
+    const int64_t w0 = c * kCH > kHalo ? c * kCH - kHalo : 0;
+    const int64_t w1 = c * kCH + kCH + kHalo < v.n ? c * kCH + kCH + kHalo : v.n;
+    for (int64_t k = w0 + threadIdx.x; k < w1; k += kT) sm[k - w0] = v.at(k);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nloc = (int)(w1 - w0);
+    for (int64_t ci = beg + (threadIdx.x >> 5); ci < end; ci += kT / 32) {
+        const int64_t p = cand_idx[ci];
+        if (p >= w1) {   // the plateau midpoint of a candidate of this chunk lies beyond the window
+            if (lane == 0) list[atomicAdd(count, 1ull)] = ci;
+            continue;
         }
-        for (int64_t B = pb - 1; !stop && B >= 0; --B) {
-            if (BX[B] <= xp) {
-                if (BN[B] < lmin) { lmin = BN[B]; lb = AH[B]; }
-            } else {
-                for (int64_t k = B * kBS + kBS - 1; k >= B * kBS; --k) {
-                    const float x = v.at(k);
-                    if (x > xp) { stop = true; break; }
-                    if (x < lmin) { lmin = x; lb = k; }
+        const int pl = (int)(p - w0);
+        const float xp = sm[pl];
+        // prominence walks in window coordinates
+        unsigned kmin = fkey(xp);
+        int lbl = pl;
+        bool done = w0 == 0;              // the walk may end at the series start
+        for (int base = pl; base >= 0; base -= 32) {
+            const int k = base - lane;
+            const bool in = k >= 0;
+            const float x = in ? sm[k] : 0.f;
+            const unsigned up = __ballot_sync(kFull, in && x > xp);
+            const int nl = up ? __ffs(up) - 1 : 32;
+            const bool part = in && lane < nl;
+            const unsigned key = part ? fkey(x) : 0xFFFFFFFFu;
+            const unsigned mk = __reduce_min_sync(kFull, key);
+            if (mk < kmin) {
+                kmin = mk;
+                lbl = base - (__ffs(__ballot_sync(kFull, part && key == mk)) - 1);
+            }
+            if (up) { done = true; break; }
+        }
+        if (done) {
+            unsigned kr = fkey(xp);
+            int rbl = pl;
+            done = w1 == v.n;             // the walk may end at the series end
+            for (int base = pl; base < nloc; base += 32) {
+                const int k = base + lane;
+                const bool in = k < nloc;
+                const float x = in ? sm[k] : 0.f;
+                const unsigned up = __ballot_sync(kFull, in && x > xp);
+                const int nl = up ? __ffs(up) - 1 : 32;
+                const bool part = in && lane < nl;
+                const unsigned key = part ? fkey(x) : 0xFFFFFFFFu;
+                const unsigned mk = __reduce_min_sync(kFull, key);
+                if (mk < kr) {
+                    kr = mk;
+                    rbl = base + (__ffs(__ballot_sync(kFull, part && key == mk)) - 1);
                 }
+                if (up) { done = true; break; }
             }
-        }
-    }
-    // right: mirrored
-    float rmin = xp;
-    int64_t rb = p;
-    {
-        bool stop = false;
-        const int64_t pend = min((pb + 1) * kBS, v.n);
-        for (int64_t k = p; k < pend; ++k) {
-            const float x = v.at(k);
-            if (x > xp) { stop = true; break; }
-            if (x < rmin) { rmin = x; rb = k; }
-        }
-        for (int64_t B = pb + 1; !stop && B < g.nblk; ++B) {
-            if (BX[B] <= xp) {
-                if (BN[B] < rmin) { rmin = BN[B]; rb = AL[B]; }
-            } else {
-                const int64_t e = min((B + 1) * kBS, v.n);
-                for (int64_t k = B * kBS; k < e; ++k) {
-                    const float x = v.at(k);
-                    if (x > xp) { stop = true; break; }
-                    if (x < rmin) { rmin = x; rb = k; }
+            if (done) {
+                const float lmin = sm[lbl], rmin = sm[rbl];
+                const float bse = lmin > rmin ? lmin : rmin;
+                // h = xp - (xp - base) / 2 (FP64, the definition) and hf, the largest float <= h.
+                // When xp and base are within 2^27 of each other (and of moderate size), xp - base
+                // and h = (xp + base) / 2 are exact in FP64, so hf = RD(xp + base) / 2 in FP32; only
+                // the other cases evaluate h in FP64 here (FP64 is slow on this part).
+                const float aa = fabsf(xp), ab = fabsf(bse);
+                const float lo = fminf(aa, ab), hi = fmaxf(aa, ab);
+                const bool exact = hi <= 0x1p100f && (lo == 0.f ? (hi == 0.f || hi >= 0x1p-100f)
+                                                                : (lo >= 0x1p-100f && hi <= lo * 0x1p27f));
+                float hf;
+                if (exact) {
+                    hf = __fmul_rn(__fadd_rd(xp, bse), 0.5f);
+                } else {
+                    const double pr0 = __dsub_rn((double)xp, (double)bse);
+                    hf = __double2float_rd(__dsub_rn((double)xp, __dmul_rn(pr0, 0.5)));
                 }
+                // width walks: the first k from the peak with k at the base or !(h < x[k])
+                int kl = lbl;
+                for (int base = pl; base >= lbl; base -= 32) {
+                    const int k = base - lane;
+                    const unsigned st = __ballot_sync(kFull, k >= lbl && (k == lbl || !(sm[k] > hf)));
+                    if (st) { kl = base - (__ffs(st) - 1); break; }
+                }
+                int kr2 = rbl;
+                for (int base = pl; base <= rbl; base += 32) {
+                    const int k = base + lane;
+                    const unsigned st = __ballot_sync(kFull, k <= rbl && (k == rbl || !(sm[k] > hf)));
+                    if (st) { kr2 = base + (__ffs(st) - 1); break; }
+                }
+                // the width lies in (kr2 - kl - 2, kr2 - kl]: below min_width when kr2 - kl < mw_int
+                if (lane == 0 && (int64_t)(kr2 - kl) < mw_int) keep[ci] = 0;
+                if (lane == 0 && (int64_t)(kr2 - kl) >= mw_int) {
+                    const double dxp = (double)xp;
+                    const double pr = __dsub_rn(dxp, (double)bse);
+                    const double h = __dsub_rn(dxp, __dmul_rn(pr, 0.5));
+                    double lip = (double)(w0 + kl);
+                    {
+                        const double xk = (double)sm[kl];
+                        if (xk < h) lip = __dadd_rn(lip, __ddiv_rn(__dsub_rn(h, xk), __dsub_rn((double)sm[kl + 1], xk)));
+                    }
+                    double rip = (double)(w0 + kr2);
+                    {
+                        const double xk = (double)sm[kr2];
+                        if (xk < h) rip = __dsub_rn(rip, __ddiv_rn(__dsub_rn(h, xk), __dsub_rn((double)sm[kr2 - 1], xk)));
+                    }
+                    const double wd = __dsub_rn(rip, lip);
+                    keep[ci] = (wd >= min_width) ? 1 : 0;
+                    o_h[ci] = dxp;
+                    o_pr[ci] = pr;
+                    o_wd[ci] = wd;
+                }
+                continue;
             }
         }
+        if (lane == 0) list[atomicAdd(count, 1ull)] = ci;
     }
-    const double dxp = (double)xp;
-    const double base = (double)lmin > (double)rmin ? (double)lmin : (double)rmin;
-    const double pr = __dsub_rn(dxp, base);
-    const double h = __dsub_rn(dxp, __dmul_rn(pr, 0.5));
-
-    // width: walk from the peak towards each base while the samples stay above h
-    int64_t k = p;
-    {
-        // samples of p's own block first, then whole blocks whose minimum is above h
-        while (lb < k && h < (double)v.at(k)) {
-            if (k % kBS == 0) {
-                int64_t B = k / kBS - 1;
-                while (B >= 0 && B * kBS > lb && h < (double)BN[B]) --B;
-                // blocks B+1 .. k/kBS-1 are entirely above h and above lb
-                const int64_t nk = (B + 1) * kBS - 1;
-                if (nk < k - 1) { k = nk + 1; }
-            }
-            --k;
-        }
-    }
-    double lip = (double)k;
-    {
-        const double xk = (double)v.at(k);
-        if (xk < h) lip = __dadd_rn(lip, __ddiv_rn(__dsub_rn(h, xk), __dsub_rn((double)v.at(k + 1), xk)));
-    }
-    k = p;
-    {
-        while (k < rb && h < (double)v.at(k)) {
-            if (k % kBS == kBS - 1) {
-                int64_t B = k / kBS + 1;
-                while (B < g.nblk && (B + 1) * kBS - 1 < rb && h < (double)BN[B]) ++B;
-                const int64_t nk = B * kBS;   // first sample not skipped
-                if (nk > k + 1) { k = nk - 1; }
-            }
-            ++k;
-        }
-    }
-    double rip = (double)k;
-    {
-        const double xk = (double)v.at(k);
-        if (xk < h) rip = __dsub_rn(rip, __ddiv_rn(__dsub_rn(h, xk), __dsub_rn((double)v.at(k - 1), xk)));
-    }
-    const double wd = __dsub_rn(rip, lip);
-    keep[ci] = (wd >= min_width) ? 1 : 0;
-    o_h[ci] = dxp;
-    o_pr[ci] = pr;
-    o_wd[ci] = wd;
 }
 
 // ordered compaction of int flags: per 8192-element chunk counts, then writes
@@ -372,7 +704,7 @@ __global__ void k_coinc(int64_t npk, const int64_t *p_idx, const int *p_ser, con
 
 struct TrigWs {
     std::mutex mu;
-    DevBuf stats_mx, stats_mn, stats_lo, stats_hi, counts, offsets, cand_idx, cand_ser, keep, h, pr, wd, sel,
+    DevBuf stats_mx, stats_mn, stats_lo, stats_hi, sb_mx, sb_mn, sb_lo, sb_hi, longs, nlong, counts, offsets, cand_idx, cand_ser, keep, h, pr, wd, sel,
         p_idx, p_ser, p_h, p_pr, p_wd, start, ens;
 };
 TrigWs &trig_ws() {
@@ -404,19 +736,63 @@ gwe_status triggers_collect(const float *prob, int n_models, int n_slides, int64
     GWE_CUDA_TRY(ws.stats_mn.ensure(nstat * sizeof(float)));
     GWE_CUDA_TRY(ws.stats_lo.ensure(nstat * sizeof(int64_t)));
     GWE_CUDA_TRY(ws.stats_hi.ensure(nstat * sizeof(int64_t)));
-    k_stats<<<blocks_for(nstat, 8), 256, 0, st>>>(g, ws.stats_mx.as<float>(), ws.stats_mn.as<float>(),
-                                                   ws.stats_lo.as<int64_t>(), ws.stats_hi.as<int64_t>(), n_series);
-    note_launch();
+    {
+        ProfScope prof("k_trig_stats", st);
+        k_stats<<<blocks_for(nstat, 8), 256, 0, st>>>(g, ws.stats_mx.as<float>(), ws.stats_mn.as<float>(),
+                                                       ws.stats_lo.as<int64_t>(), ws.stats_hi.as<int64_t>(), n_series);
+        note_launch();
+    }
+    // summary tree: level 1 = the block statistics, then levels of kFan nodes until at most kFan remain
+    Tree tr{};
+    tr.MX[1] = ws.stats_mx.as<float>();
+    tr.MN[1] = ws.stats_mn.as<float>();
+    tr.AL[1] = ws.stats_lo.as<int64_t>();
+    tr.AH[1] = ws.stats_hi.as<int64_t>();
+    tr.cnt[1] = g.nblk;
+    int64_t upper = 0;
+    for (int64_t c = g.nblk; c > kFan;) {
+        c = (c + kFan - 1) / kFan;
+        upper += c * n_series;
+    }
+    GWE_CUDA_TRY(ws.sb_mx.ensure(std::max<int64_t>(upper, 1) * sizeof(float)));
+    GWE_CUDA_TRY(ws.sb_mn.ensure(std::max<int64_t>(upper, 1) * sizeof(float)));
+    GWE_CUDA_TRY(ws.sb_lo.ensure(std::max<int64_t>(upper, 1) * sizeof(int64_t)));
+    GWE_CUDA_TRY(ws.sb_hi.ensure(std::max<int64_t>(upper, 1) * sizeof(int64_t)));
+    int top = 1;
+    for (int64_t off = 0; tr.cnt[top] > kFan && top + 1 < kMaxLv; ++top) {
+        const int64_t cn = (tr.cnt[top] + kFan - 1) / kFan;
+        tr.MX[top + 1] = ws.sb_mx.as<float>() + off;
+        tr.MN[top + 1] = ws.sb_mn.as<float>() + off;
+        tr.AL[top + 1] = ws.sb_lo.as<int64_t>() + off;
+        tr.AH[top + 1] = ws.sb_hi.as<int64_t>() + off;
+        tr.cnt[top + 1] = cn;
+        {
+            ProfScope prof("k_trig_stats", st);
+            k_stats_up<<<blocks_for(cn * n_series, 256), 256, 0, st>>>(
+                tr.cnt[top], cn, n_series, tr.MX[top], tr.MN[top], tr.AL[top], tr.AH[top],
+                const_cast<float *>(tr.MX[top + 1]), const_cast<float *>(tr.MN[top + 1]),
+                const_cast<int64_t *>(tr.AL[top + 1]), const_cast<int64_t *>(tr.AH[top + 1]));
+            note_launch();
+        }
+        off += cn * n_series;
+    }
+    tr.top = top;
     const int64_t nchunk = (g.n + kCH - 1) / kCH;
     const int64_t ncnt = nchunk * n_series;
     GWE_CUDA_TRY(ws.counts.ensure(ncnt * sizeof(int64_t)));
     GWE_CUDA_TRY(ws.offsets.ensure((ncnt + 1) * sizeof(int64_t)));
-    const double dthr = (double)thr;
+    const float dthr = thr;
     dim3 cgrid((unsigned)nchunk, (unsigned)n_series);
-    k_cand<<<cgrid, kT, 0, st>>>(g, dthr, 0, ws.counts.as<int64_t>(), nullptr, nullptr, nullptr, nchunk);
-    note_launch();
-    k_scan<<<1, 1024, 0, st>>>(ws.counts.as<int64_t>(), ws.offsets.as<int64_t>(), ncnt);
-    note_launch();
+    {
+        ProfScope prof("k_trig_cand", st);
+        k_cand<<<cgrid, kT, 0, st>>>(g, dthr, 0, ws.counts.as<int64_t>(), nullptr, nullptr, nullptr, nchunk);
+        note_launch();
+    }
+    {
+        ProfScope prof("k_trig_scan", st);
+        k_scan<<<1, 1024, 0, st>>>(ws.counts.as<int64_t>(), ws.offsets.as<int64_t>(), ncnt);
+        note_launch();
+    }
     int64_t ncand = 0;
     GWE_CUDA_TRY(cudaMemcpyAsync(&ncand, ws.offsets.as<int64_t>() + ncnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GWE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -427,22 +803,48 @@ gwe_status triggers_collect(const float *prob, int n_models, int n_slides, int64
         GWE_CUDA_TRY(ws.h.ensure(ncand * sizeof(double)));
         GWE_CUDA_TRY(ws.pr.ensure(ncand * sizeof(double)));
         GWE_CUDA_TRY(ws.wd.ensure(ncand * sizeof(double)));
-        k_cand<<<cgrid, kT, 0, st>>>(g, dthr, 1, nullptr, ws.offsets.as<int64_t>(), ws.cand_idx.as<int64_t>(),
-                                     ws.cand_ser.as<int>(), nchunk);
-        note_launch();
-        k_eval<<<blocks_for(ncand, 128), 128, 0, st>>>(
-            g, ncand, ws.cand_idx.as<int64_t>(), ws.cand_ser.as<int>(), ws.stats_mx.as<float>(),
-            ws.stats_mn.as<float>(), ws.stats_lo.as<int64_t>(), ws.stats_hi.as<int64_t>(), min_width,
-            ws.keep.as<int>(), ws.h.as<double>(), ws.pr.as<double>(), ws.wd.as<double>());
-        note_launch();
+        {
+            ProfScope prof("k_trig_cand", st);
+            k_cand<<<cgrid, kT, 0, st>>>(g, dthr, 1, nullptr, ws.offsets.as<int64_t>(), ws.cand_idx.as<int64_t>(),
+                                         ws.cand_ser.as<int>(), nchunk);
+            note_launch();
+        }
+        // an integer span below mw_int cannot reach min_width (NaN: nothing is kept)
+        const int64_t mw_int = std::isnan(min_width) ? INT64_MAX
+                               : (min_width <= 0.0 ? 0 : (min_width >= 9.0e18 ? INT64_MAX : (int64_t)std::ceil(min_width)));
+        GWE_CUDA_TRY(ws.longs.ensure(ncand * sizeof(int64_t)));
+        GWE_CUDA_TRY(ws.nlong.ensure(sizeof(unsigned long long)));
+        GWE_CUDA_TRY(cudaMemsetAsync(ws.nlong.ptr, 0, sizeof(unsigned long long), st));
+        {
+            ProfScope prof("k_eval_local", st);
+            k_eval_local<<<cgrid, kT, 0, st>>>(g, nchunk, ws.offsets.as<int64_t>(), ws.cand_idx.as<int64_t>(),
+                                               min_width, mw_int, ws.keep.as<int>(), ws.h.as<double>(), ws.pr.as<double>(),
+                                               ws.wd.as<double>(), ws.longs.as<int64_t>(),
+                                               ws.nlong.as<unsigned long long>());
+            note_launch();
+        }
+        {
+            ProfScope prof("k_eval_tree", st);
+            k_eval_tree<<<2048, 128, 0, st>>>(g, ws.longs.as<int64_t>(), ws.nlong.as<int64_t>(),
+                                               ws.cand_idx.as<int64_t>(), ws.cand_ser.as<int>(), tr, min_width,
+                                               ws.keep.as<int>(), ws.h.as<double>(), ws.pr.as<double>(),
+                                               ws.wd.as<double>());
+            note_launch();
+        }
         const int64_t nfc = (ncand + kCH - 1) / kCH;
         GWE_CUDA_TRY(ws.counts.ensure(nfc * sizeof(int64_t)));
         GWE_CUDA_TRY(ws.offsets.ensure((nfc + 1) * sizeof(int64_t)));
-        k_flag_pass<<<(unsigned)nfc, kT, 0, st>>>(ws.keep.as<int>(), ncand, 0, ws.counts.as<int64_t>(), nullptr,
-                                                  nullptr);
-        note_launch();
-        k_scan<<<1, 1024, 0, st>>>(ws.counts.as<int64_t>(), ws.offsets.as<int64_t>(), nfc);
-        note_launch();
+        {
+            ProfScope prof("k_trig_compact", st);
+            k_flag_pass<<<(unsigned)nfc, kT, 0, st>>>(ws.keep.as<int>(), ncand, 0, ws.counts.as<int64_t>(), nullptr,
+                                                      nullptr);
+            note_launch();
+        }
+        {
+            ProfScope prof("k_trig_scan", st);
+            k_scan<<<1, 1024, 0, st>>>(ws.counts.as<int64_t>(), ws.offsets.as<int64_t>(), nfc);
+            note_launch();
+        }
         int64_t npk = 0;
         GWE_CUDA_TRY(cudaMemcpyAsync(&npk, ws.offsets.as<int64_t>() + nfc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         GWE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -455,20 +857,32 @@ gwe_status triggers_collect(const float *prob, int n_models, int n_slides, int64
             GWE_CUDA_TRY(ws.p_wd.ensure(npk * sizeof(double)));
             GWE_CUDA_TRY(ws.ens.ensure(npk * sizeof(int)));
             GWE_CUDA_TRY(ws.start.ensure((n_series + 1) * sizeof(int64_t)));
-            k_flag_pass<<<(unsigned)nfc, kT, 0, st>>>(ws.keep.as<int>(), ncand, 1, nullptr, ws.offsets.as<int64_t>(),
-                                                      ws.sel.as<int64_t>());
-            note_launch();
-            k_gather_peaks<<<blocks_for(npk, 256), 256, 0, st>>>(
-                npk, ws.sel.as<int64_t>(), ws.cand_idx.as<int64_t>(), ws.cand_ser.as<int>(), ws.h.as<double>(),
-                ws.pr.as<double>(), ws.wd.as<double>(), ws.p_idx.as<int64_t>(), ws.p_ser.as<int>(),
-                ws.p_h.as<double>(), ws.p_pr.as<double>(), ws.p_wd.as<double>());
-            note_launch();
-            k_series_start<<<blocks_for(n_series + 1, 128), 128, 0, st>>>(ws.p_ser.as<int>(), npk, n_series,
-                                                                         ws.start.as<int64_t>());
-            note_launch();
-            k_coinc<<<blocks_for(npk, 128), 128, 0, st>>>(npk, ws.p_idx.as<int64_t>(), ws.p_ser.as<int>(),
-                                                          ws.start.as<int64_t>(), n_models, coinc, ws.ens.as<int>());
-            note_launch();
+            {
+                ProfScope prof("k_trig_compact", st);
+                k_flag_pass<<<(unsigned)nfc, kT, 0, st>>>(ws.keep.as<int>(), ncand, 1, nullptr, ws.offsets.as<int64_t>(),
+                                                          ws.sel.as<int64_t>());
+                note_launch();
+            }
+            {
+                ProfScope prof("k_trig_compact", st);
+                k_gather_peaks<<<blocks_for(npk, 256), 256, 0, st>>>(
+                    npk, ws.sel.as<int64_t>(), ws.cand_idx.as<int64_t>(), ws.cand_ser.as<int>(), ws.h.as<double>(),
+                    ws.pr.as<double>(), ws.wd.as<double>(), ws.p_idx.as<int64_t>(), ws.p_ser.as<int>(),
+                    ws.p_h.as<double>(), ws.p_pr.as<double>(), ws.p_wd.as<double>());
+                note_launch();
+            }
+            {
+                ProfScope prof("k_trig_compact", st);
+                k_series_start<<<blocks_for(n_series + 1, 128), 128, 0, st>>>(ws.p_ser.as<int>(), npk, n_series,
+                                                                             ws.start.as<int64_t>());
+                note_launch();
+            }
+            {
+                ProfScope prof("k_coinc", st);
+                k_coinc<<<blocks_for(npk, 128), 128, 0, st>>>(npk, ws.p_idx.as<int64_t>(), ws.p_ser.as<int>(),
+                                                              ws.start.as<int64_t>(), n_models, coinc, ws.ens.as<int>());
+                note_launch();
+            }
             GWE_CUDA_TRY(cudaGetLastError());
             std::vector<int64_t> idx(npk);
             std::vector<int> ser(npk), ens(npk);

@@ -196,6 +196,8 @@ gwe_status whiten_run(const float *x, int64_t n, double fs, int seg, float *out,
     if (s == GWE_OK) s = plan_r2c(w, n, 1, &p_full);
     if (s == GWE_OK) s = plan_c2r(w, n, &p_inv);
     if (s != GWE_OK) return s;
+    // every whitening kernel and transform below, as one profiling entry
+    ProfScope prof("k_whiten", st);
     // Welch PSD
     k_seg_mean<<<n_seg, 256, 0, st>>>(x, step, seg, w.mean.as<double>());
     note_launch();

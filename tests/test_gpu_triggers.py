@@ -77,3 +77,17 @@ def test_triggers_capacity_error():
     with pytest.raises(gwe.GweError) as ei:
         gwe.gwe_triggers(torch.from_numpy(prob).to(dev), 1, 1, 4, 512, 256, 0.0, 0.0, 10, cap=3)
     assert ei.value.status == 6
+
+
+def test_triggers_superblock_walks():
+    """A long quantised random walk (160 windows, 41 superblocks of 8192 samples): prominence and
+    width walks that cross many blocks and superblocks, with equal minima in different blocks and
+    superblocks (first / last argmin rules)."""
+    rng = np.random.default_rng(12)
+    W, stride = 4096, 2048
+    nw = 160
+    walk = np.cumsum(rng.standard_normal((1, 2, nw * W)), axis=-1)
+    walk = np.round(walk * 0.02) / 20.0
+    prob = (1 / (1 + np.exp(-walk / 8.0))).astype(np.float32).reshape(1, 2, nw, W)
+    recs = _compare(prob, W, stride, float(np.quantile(prob, 0.2)), 0.0, 4096)
+    assert len(recs) > 0
