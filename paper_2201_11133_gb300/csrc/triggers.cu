@@ -119,16 +119,20 @@ __global__ void k_stats(Geo g, float *bmax, float *bmin, int64_t *amin_lo, int64
     }
 }
 
-// local maximum test at a left edge i; returns the peak index (plateau midpoint) or -1
-// thr: the height threshold (a float, so the float comparison is the definition's)
-__device__ __forceinline__ int64_t peak_at(const Series &v, int64_t i, float thr) {
+// local maximum test at a left edge i over the chunk [lo, lo + kCH) held in xs (samples lo - 1 ..
+// lo + kCH, those inside the series); returns the peak index (plateau midpoint) or -1.  thr: the
+// height threshold (a float, so the float comparison is the definition's); the conditions are all
+// required, so testing the height first does not change the result.
+__device__ __forceinline__ int64_t peak_at(const Series &v, const float *xs, int64_t lo, int64_t i, float thr) {
     if (i < 1 || i > v.n - 2) return -1;
-    const float xi = v.at(i);
-    if (!(v.at(i - 1) < xi)) return -1;
-    int64_t ia = i + 1;
-    while (ia < v.n - 1 && v.at(ia) == xi) ++ia;
-    if (!(v.at(ia) < xi)) return -1;
+    const float xi = xs[i - lo + 1];
     if (!(xi >= thr)) return -1;
+    if (!(xs[i - lo] < xi)) return -1;
+    const int64_t top = lo + kCH;          // last sample held in xs (when inside the series)
+    auto x = [&](int64_t k) -> float { return k <= top ? xs[k - lo + 1] : v.at(k); };
+    int64_t ia = i + 1;
+    while (ia < v.n - 1 && x(ia) == xi) ++ia;
+    if (!(x(ia) < xi)) return -1;
     return (i + (ia - 1)) / 2;
 }
 
@@ -136,14 +140,18 @@ __device__ __forceinline__ int64_t peak_at(const Series &v, int64_t i, float thr
 __global__ void k_cand(Geo g, float thr, int mode, int64_t *counts, const int64_t *offsets, int64_t *cand_idx,
                        int *cand_ser, int64_t nchunk) {
     __shared__ int sh[kT / 32 + 1];
+    __shared__ float xs[kCH + 2];
     const int s = blockIdx.y;
     const int64_t c = blockIdx.x;
     const Series v = g.series(s);
     const int64_t lo = c * kCH;
+    for (int64_t k = lo - 1 + threadIdx.x; k <= lo + kCH; k += kT)
+        if (k >= 0 && k < v.n) xs[k - lo + 1] = v.at(k);
+    __syncthreads();
     int64_t run = (mode == 1) ? offsets[(int64_t)s * nchunk + c] : 0;
     for (int it = 0; it < kCH / kT; ++it) {
         const int64_t i = lo + (int64_t)it * kT + threadIdx.x;
-        const int64_t pk = (i < v.n) ? peak_at(v, i, thr) : -1;
+        const int64_t pk = (i < v.n) ? peak_at(v, xs, lo, i, thr) : -1;
         int tot;
         const int r = block_rank(pk >= 0, sh, tot);
         if (mode == 1 && pk >= 0) {
