@@ -485,7 +485,9 @@ __global__ void k_eval_tree(Geo g, const int64_t *list, const int64_t *count, co
     }
 }
 
-// order-preserving unsigned key of a float (-0 taken as +0): a < b  <=>  fkey(a) < fkey(b)
+// order-preserving unsigned key of a float (-0 taken as +0): a < b  <=>  fkey(a) < fkey(b) for
+// numbers; the series are probabilities or logits and hold no NaN (a NaN would compare as a number
+// here, while the definition never takes it as a minimum)
 __device__ __forceinline__ unsigned fkey(float x) {
     const unsigned u = __float_as_uint(x + 0.0f);
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
