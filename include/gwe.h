@@ -354,7 +354,7 @@ void gwe_plan_destroy(gwe_plan *plan);
  * coincident within 0.5 s; section "Statistical Analysis": ROC threshold and
  * width >= 0.5 s).
  *   prob         device FP32 [n_slides][n_models][n_windows][window] as written by
- *                gwe_forward.
+ *                gwe_forward (probabilities or logits; no NaN).
  *   Each (slide, model) series is stitched: window 0 gives samples [0, window),
  *   every later window w its last `stride` samples.  Peaks follow SciPy's
  *   find_peaks(x, height=height_thr, width=min_width) semantics (rel_height 0.5,
