@@ -373,6 +373,22 @@ def stream_search(gwe, cfg, wb, sh, sl, thr, hours, dist, dev, stream, world):
     return res
 
 
+def training_roofline(cfg1, B, W, kernels, peaks, peak_kind):
+    """Roofline of the backward's row GEMMs (k_tc_rows, bound by HBM) from their measured time per
+    step.  Algorithmic bytes per row (one sample of one branch) and layer, with the stack inputs
+    and skip sums taken from the fused forward (BF16 handles, W a multiple of 128): recomputed
+    conv 8R (x in, gate cache and z out), residual 12R (z, x in; x FP32 and BF16 out), dz 10R + 2S
+    (dL/dx, dL/dskip, gate cache in; da out), dgrad 14R (da, dL/dx in; dL/dx FP32 and BF16 out)."""
+    kr = kernels.get("k_tc_rows")
+    if not kr or kr["ms_per_step"] <= 0:
+        return None
+    R, S, L = cfg1["r_ch"], cfg1["s_ch"], workload.n_layers(cfg1)
+    bytes_step = 2 * B * W * L * (44 * R + 2 * S)
+    ach = bytes_step / (kr["ms_per_step"] / 1000.0) / 1e9
+    return {"kernel": "k_tc_rows", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "peak_source": f"of {peak_kind}", "bytes_per_step": bytes_step}
+
+
 def training_step(gwe, cfg, B, dist, dev, stream, world):
     """Forward logits, dL/dlogit of the mean BCE, and the backward pass (weight and input gradients,
     per-stack recomputation) of one member on B windows of 2 x 4096 samples, half with chirps: with
@@ -424,6 +440,8 @@ def training_step(gwe, cfg, B, dist, dev, stream, world):
                                   for k, v in prof.items()}}
         m.close()
     res["speedup_bf16_vs_fp32"] = res["fp32"]["ms_per_step"] / res["bf16"]["ms_per_step"]
+    peaks, peak_kind = load_peaks()
+    res["bf16"]["roofline"] = training_roofline(cfg1, B, WINDOW, res["bf16"]["kernels"], peaks, peak_kind)
     return res
 
 
