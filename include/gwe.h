@@ -119,6 +119,61 @@ gwe_status gwe_model_create(const gwe_model_config *cfg, const float *host_weigh
 gwe_status gwe_model_set_weights(gwe_model *model, const float *host_weights);
 
 /*
+ * Replace the weights from a device buffer (FP32 blob, same layout; for
+ * example the master weights of a training loop).  The FP32 copy and the
+ * derived layouts are rebuilt by kernels on `stream`, with no host round
+ * trip, asynchronously; the new weights apply to every later launch on that
+ * stream (launches on other streams must be ordered by the caller).  For a
+ * GWE_FP8 handle the E4M3 images are built on the host (a synchronous copy to
+ * the host).  dev_weights may be any device buffer of n_models *
+ * gwe_param_count floats (it is copied).
+ */
+gwe_status gwe_model_set_weights_device(gwe_model *model, const float *dev_weights, void *stream);
+
+/*
+ * Seeded random initialisation (paper paragraph "AI ensemble construction":
+ * the members share the architecture and differ in their random
+ * initialisation).  Every weight tensor is drawn N(0, 1/fan_in), fan_in = input
+ * channels x kernel taps of the layer (1 for the input projection, R*kernel for
+ * a dilated convolution, R for the residual and skip projections, 2S for the
+ * head's first convolution, Hc for its second); every bias is 0.
+ * Weight number e of member m's blob (blob layout above) is the standard normal
+ * sqrt(-2 ln u1) cos(2 pi u2) with u1 = ((r[2j] >> 11) + 1) 2^-53 and
+ * u2 = (r[2j+1] >> 11) 2^-53, where r = Philox4x64-10(counter (e/2, 0, 0, 0),
+ * key (seed, m)) and j = e mod 2, scaled by 1/sqrt(fan_in) in FP64 and rounded
+ * to FP32.  The result does not depend on the machine.
+ *   gwe_init_weights      host only (no GPU needed): writes n_models *
+ *                         gwe_param_count(cfg) floats to host_out.
+ *   gwe_model_init_random gwe_init_weights followed by gwe_model_create.
+ * GWE_ERR_ARG for an invalid configuration or NULL output.
+ */
+gwe_status gwe_init_weights(const gwe_model_config *cfg, uint64_t seed, float *host_out);
+gwe_status gwe_model_init_random(const gwe_model_config *cfg, uint64_t seed, int precision, gwe_model **out);
+
+/* The counter-based generator of gwe_init_weights, Philox4x64-10 (Salmon et al.,
+ * SC 2011): out[0..3] = Philox4x64-10(counter[0..3], key[0..1]).  Host only;
+ * exported so that the stream can be checked against other implementations. */
+void gwe_philox4x64_10(const uint64_t *counter, const uint64_t *key, uint64_t *out);
+
+/*
+ * Operand format of the dilated convolutions of a GWE_BF16 handle.  Layers
+ * l < n take FP16 operands (both the activations and the weights; FP16 has
+ * three more mantissa bits than BF16 and runs at the same tensor rate), layers
+ * l >= n take BF16 operands; accumulation is FP32 either way.  Rounding errors
+ * of the first layers pass through every later layer, so they weigh most in
+ * the output: for the 30-layer R = 64 ensemble the default n = L/3 (10, the
+ * first dilation stack) keeps the bulk of the convolutions (two thirds) in BF16
+ * and brings the largest probability error against exact arithmetic from about
+ * 9e-3 to about 6e-3 (the paper states no precision; the TensorRT engines it
+ * deploys run FP16).  The default for every GWE_BF16 handle is floor(L/3).
+ * set: 0 <= n <= L (GWE_ERR_ARG otherwise); synchronises the device and
+ * rebuilds the weight images.  GWE_ERR_UNSUPPORTED for other precisions.
+ * get: the current n (0 for other precisions or a NULL handle).
+ */
+gwe_status gwe_model_set_f16_layers(gwe_model *model, int n);
+int gwe_model_f16_layers(const gwe_model *model);
+
+/*
  * Activation scales of a GWE_FP8 handle (the paper's TensorRT paragraph runs
  * the network at reduced precision; it does not state how activations are
  * scaled, so this call is the library's own).  Runs the FP32 forward of every
@@ -273,7 +328,9 @@ gwe_status gwe_set_cross_window_reuse(int enable);
  *   status      device pointer to one int owned by the caller, or NULL.  It is
  *               set to 0 on the stream, then to a nonzero wait-site code if a
  *               bounded device-side wait of the kernel gave up (the outputs are
- *               then invalid).  With NULL the code is written into the array.
+ *               then invalid).  With NULL the code goes to the handle's own
+ *               error word (allocated with the handle), and gwe_sync on the
+ *               handle returns GWE_ERR_TIMEOUT, as for the other calls.
  * Limits: window must be a multiple of 128; the number of CTAs is reduced so
  * that their lag rings fit the array (the 30-layer, R = 64 configuration
  * needs 768 KiB per CTA in BF16 and 384 KiB in FP8, so at most 32 or 64 CTAs
@@ -282,9 +339,11 @@ gwe_status gwe_set_cross_window_reuse(int enable);
  * rejected with GWE_ERR_ARG.
  * The first call on each device looks up the array's device address for that
  * device (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device shares the one array and
- * clears its error word and zero rows on the stream; calls whose executions
- * overlap on the GPU (for example on two streams) race on it, so serialise them.
+ * before any stream capture.  The address is kept per device and CUDA context:
+ * after cudaDeviceReset the next call looks it up again.  Every call on a
+ * device shares the one array (the previous call's lag rows stay in it) and
+ * clears its zero rows on the stream; calls whose executions overlap on the GPU
+ * (for example on two streams) race on it, so serialise them.
  */
 gwe_status gwe_forward_static(gwe_model *model, const float *strain_H, const float *strain_L, int64_t n_samples,
                               int window, int stride, float *out_prob, int *status, void *stream);
@@ -384,6 +443,37 @@ gwe_status gwe_triggers_segments(const float *prob, int n_models, int n_slides, 
                                  int n_segments, int window, int stride, float height_thr, double min_width,
                                  int64_t coinc, int flags, gwe_trigger *out, int32_t *out_segment, int64_t cap,
                                  int64_t *n_out, void *stream);
+
+/*
+ * Threshold sweep of the trigger statistics in one pass (section "Statistical
+ * Analysis": the ROC curve and the false-alarm rate come from sweeping the
+ * probability threshold, over [0, 0.9998] in the paper, on the zero-lag and
+ * the time-slid outputs; the paper post-processes ~500 GB per searched month
+ * on CPUs, section "Computational Efficiency").  The result is exactly what
+ * gwe_triggers would report once per threshold with the same min_width and
+ * coinc, counted instead of listed: peaks are found once at the lowest
+ * threshold (prominence and width do not depend on the threshold), and each
+ * model-0 peak's largest threshold at which it is still an ensemble trigger is
+ * computed on the device.
+ *   prob, n_models, n_slides, n_windows, window, stride, min_width, coinc
+ *                as gwe_triggers (one segment).
+ *   thresholds   host FP32 [n_thr], finite and in ascending order (a peak is
+ *                kept at threshold t when its height >= t, as in gwe_triggers).
+ *   ens_counts   host int64 [max(n_slides,1)][n_thr]: number of ensemble
+ *                triggers of each slide at each threshold (overwritten).
+ *   model_counts host int64 [max(n_slides,1)][n_models][n_thr] or NULL: number
+ *                of kept peaks of each model (overwritten).
+ * Synchronises `stream`.  GWE_ERR_ARG for unsorted or non-finite thresholds.
+ * The _segments form takes the segments of a gwe_forward_segments output (as
+ * gwe_triggers_segments) and sums the counts over them.
+ */
+gwe_status gwe_trigger_sweep(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,
+                             int stride, const float *thresholds, int n_thr, double min_width, int64_t coinc,
+                             int64_t *ens_counts, int64_t *model_counts, void *stream);
+gwe_status gwe_trigger_sweep_segments(const float *prob, int n_models, int n_slides, const int64_t *seg_len,
+                                      int n_segments, int window, int stride, const float *thresholds, int n_thr,
+                                      double min_width, int64_t coinc, int64_t *ens_counts, int64_t *model_counts,
+                                      void *stream);
 
 /* Input sample types of gwe_search_run. */
 #define GWE_INPUT_F32 0

@@ -19,9 +19,10 @@ from . import _build
 
 __all__ = [
     "GWE_FP32", "GWE_BF16", "GWE_FP8", "GweError", "load", "build",
-    "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_calibrate", "gwe_model_set_fp8_amax", "gwe_model_get_fp8_amax",
+    "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_set_weights_device", "gwe_init_weights",
+    "gwe_model_init_random", "gwe_philox4x64_10", "gwe_model_set_f16_layers", "gwe_model_f16_layers", "gwe_model_calibrate", "gwe_model_set_fp8_amax", "gwe_model_get_fp8_amax",
     "gwe_model_destroy",
-    "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
+    "gwe_trigger_sweep", "gwe_trigger_sweep_segments", "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
     "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static",
     "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE",
     "gwe_search_create", "gwe_search_run", "gwe_search_destroy", "GWE_INPUT_F32", "GWE_INPUT_F16", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
@@ -89,6 +90,12 @@ def load():
             "gwe_n_windows": (I64, [I64, I, I]),
             "gwe_model_create": (I, [P, P, I, P]),
             "gwe_model_set_weights": (I, [P, P]),
+            "gwe_model_set_weights_device": (I, [P, P, P]),
+            "gwe_init_weights": (I, [P, ctypes.c_uint64, P]),
+            "gwe_model_init_random": (I, [P, ctypes.c_uint64, I, P]),
+            "gwe_philox4x64_10": (None, [P, P, P]),
+            "gwe_model_set_f16_layers": (I, [P, I]),
+            "gwe_model_f16_layers": (I, [P]),
             "gwe_model_calibrate": (I, [P, P, P, I64, I, I, P]),
             "gwe_model_set_fp8_amax": (I, [P, P]),
             "gwe_model_get_fp8_amax": (I, [P, P]),
@@ -100,6 +107,8 @@ def load():
             "gwe_backward": (I, [P, I, P, P, I, I, P, P, P, P, P]),
             "gwe_triggers": (I, [P, I, I, I64, I, I, F, D, I64, I, P, I64, P, P]),
             "gwe_whiten": (I, [P, I64, D, I, I, P, P]),
+            "gwe_trigger_sweep": (I, [P, I, I, I64, I, I, P, I, D, I64, P, P, P]),
+            "gwe_trigger_sweep_segments": (I, [P, I, I, P, I, I, I, P, I, D, I64, P, P, P]),
             "gwe_sync": (I, [P, P]),
             "gwe_set_cross_window_reuse": (I, [I]),
             "gwe_debug_config": (I, [I, D]),
@@ -185,9 +194,50 @@ def gwe_model_create(cfg, host_weights: np.ndarray, precision: int = GWE_FP32) -
     return h.value
 
 
+def gwe_init_weights(cfg, seed: int) -> np.ndarray:
+    """Seeded FP32 weight blobs [n_models, P] (Philox4x64-10, N(0, 1/fan_in) weights, zero biases)."""
+    c = _cfg(cfg)
+    out = np.zeros((int(cfg["n_models"]), gwe_param_count(cfg)), dtype=np.float32)
+    _check(load().gwe_init_weights(ctypes.byref(c), int(seed), out.ctypes.data), "gwe_init_weights")
+    return out
+
+
+def gwe_model_init_random(cfg, seed: int, precision: int = GWE_FP32) -> int:
+    """Model handle with seeded random weights (gwe_init_weights + gwe_model_create)."""
+    c = _cfg(cfg)
+    h = ctypes.c_void_p()
+    _check(load().gwe_model_init_random(ctypes.byref(c), int(seed), int(precision), ctypes.byref(h)),
+           "gwe_model_init_random")
+    return h.value
+
+
+def gwe_philox4x64_10(counter, key) -> np.ndarray:
+    """Philox4x64-10 block (4 uint64) of the library's generator."""
+    ctr = np.ascontiguousarray(counter, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    load().gwe_philox4x64_10(ctr.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def gwe_model_set_f16_layers(model: int, n: int) -> None:
+    """GWE_BF16 handle: layers l < n take FP16 conv operands, the rest BF16 (default L // 3)."""
+    _check(load().gwe_model_set_f16_layers(model, int(n)), "gwe_model_set_f16_layers")
+
+
+def gwe_model_f16_layers(model: int) -> int:
+    return int(load().gwe_model_f16_layers(model))
+
+
 def gwe_model_set_weights(model: int, host_weights: np.ndarray) -> None:
     w = np.ascontiguousarray(host_weights, dtype=np.float32)
     _check(load().gwe_model_set_weights(model, w.ctypes.data), "gwe_model_set_weights")
+
+
+def gwe_model_set_weights_device(model: int, weights, stream=None) -> None:
+    """Replace the weights from a CUDA FP32 tensor (blob layout); rebuilt on the device, asynchronous."""
+    _check(load().gwe_model_set_weights_device(model, _dptr(weights), _stream(stream)),
+           "gwe_model_set_weights_device")
 
 
 def gwe_model_calibrate(model: int, strain_H, strain_L, n_samples: int, window: int, stride: int,
@@ -295,6 +345,36 @@ def gwe_triggers(prob, n_models: int, n_slides: int, n_windows: int, window: int
                           ctypes.byref(n_out), _stream(stream))
     _check(st, "gwe_triggers")
     return out[:n_out.value].copy()
+
+
+def gwe_trigger_sweep(prob, n_models: int, n_slides: int, n_windows: int, window: int, stride: int, thresholds,
+                      min_width: float, coinc: int, per_model: bool = True, stream=None):
+    """(ensemble counts [slides, K], per-model peak counts [slides, models, K] or None) of a threshold sweep."""
+    thr = np.ascontiguousarray(thresholds, dtype=np.float32)
+    ns = max(1, int(n_slides))
+    ens = np.zeros((ns, thr.shape[0]), dtype=np.int64)
+    mod = np.zeros((ns, int(n_models), thr.shape[0]), dtype=np.int64) if per_model else None
+    _check(load().gwe_trigger_sweep(_dptr(prob), int(n_models), int(n_slides), int(n_windows), int(window),
+                                    int(stride), thr.ctypes.data, int(thr.shape[0]), float(min_width), int(coinc),
+                                    ens.ctypes.data, mod.ctypes.data if mod is not None else None, _stream(stream)),
+           "gwe_trigger_sweep")
+    return ens, mod
+
+
+def gwe_trigger_sweep_segments(prob, n_models: int, n_slides: int, seg_len, window: int, stride: int, thresholds,
+                               min_width: float, coinc: int, per_model: bool = True, stream=None):
+    """As gwe_trigger_sweep over the segments of a gwe_forward_segments output (counts summed)."""
+    thr = np.ascontiguousarray(thresholds, dtype=np.float32)
+    ln = np.ascontiguousarray(seg_len, dtype=np.int64)
+    ns = max(1, int(n_slides))
+    ens = np.zeros((ns, thr.shape[0]), dtype=np.int64)
+    mod = np.zeros((ns, int(n_models), thr.shape[0]), dtype=np.int64) if per_model else None
+    _check(load().gwe_trigger_sweep_segments(_dptr(prob), int(n_models), int(n_slides), ln.ctypes.data,
+                                             int(ln.shape[0]), int(window), int(stride), thr.ctypes.data,
+                                             int(thr.shape[0]), float(min_width), int(coinc), ens.ctypes.data,
+                                             mod.ctypes.data if mod is not None else None, _stream(stream)),
+           "gwe_trigger_sweep_segments")
+    return ens, mod
 
 
 def gwe_forward_static(model: int, strain_H, strain_L, n_samples: int, window: int, stride: int, out_prob,
@@ -430,6 +510,17 @@ class Model:
         self.cfg = dict(cfg)
         self.precision = int(precision)
         self.handle = gwe_model_create(cfg, host_weights, precision)
+        self.weights_token = 0      # changes whenever the handle's weights are replaced through set_weights*
+
+    def set_weights(self, host_weights: np.ndarray) -> None:
+        gwe_model_set_weights(self.handle, host_weights)
+        self.weights_token += 1
+
+    def set_weights_device(self, weights, stream=None) -> int:
+        """Replace the weights from a CUDA FP32 tensor; returns the new weights token."""
+        gwe_model_set_weights_device(self.handle, weights.detach().float().contiguous(), stream)
+        self.weights_token += 1
+        return self.weights_token
 
     def close(self):
         if getattr(self, "handle", None):
@@ -494,17 +585,24 @@ def _autograd_function():
         def forward(ctx, weights, x_H, x_L, model):
             if int(model.cfg["n_models"]) != 1:
                 raise ValueError("GweLogits needs a one-member handle")
-            gwe_model_set_weights(model.handle, weights.detach().float().cpu().numpy())
+            if not weights.is_cuda:
+                raise ValueError("GweLogits: the weight blob must be a CUDA tensor")
+            # weights go to the handle on the device (no host round trip); the token identifies them
+            ctx.wtoken = model.set_weights_device(weights)
             out = model.logits(x_H.contiguous(), x_L.contiguous())[0]
-            ctx.save_for_backward(x_H, x_L)
+            ctx.save_for_backward(weights, x_H, x_L)
             ctx.model = model
             ctx.wdevice = weights.device
             return out
 
         @staticmethod
         def backward(ctx, grad_out):
-            x_H, x_L = ctx.saved_tensors
+            weights, x_H, x_L = ctx.saved_tensors
             model = ctx.model
+            if model.weights_token != ctx.wtoken:
+                # another forward replaced the handle's weights since this one: restore this
+                # forward's weights (saved_tensors raises if they were modified in place)
+                ctx.wtoken = model.set_weights_device(weights)
             B, W = int(x_H.shape[0]), int(x_H.shape[1])
             dev = x_H.device
             gw = torch.empty(gwe_param_count(model.cfg), dtype=torch.float32, device=dev)

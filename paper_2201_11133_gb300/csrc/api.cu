@@ -2,6 +2,7 @@
 // model handles and dispatch to the precision-specific paths.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include <cstring>
@@ -98,6 +99,104 @@ int64_t gwe_n_windows(int64_t n, int window, int stride) {
     return (n - window) / stride + 1;
 }
 
+}  // extern "C"
+
+namespace gwe {
+namespace {
+
+// Philox4x64-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC 2011): ten rounds of two 64 x 64 -> 128-bit products with the published multipliers and
+// Weyl key increments.  Host code only (weight initialisation).
+void philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        const unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
+        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        const uint64_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
+}
+
+// Standard normal number e of the stream (seed, model): block e / 2 of Philox4x64-10 with counter
+// (e / 2, 0, 0, 0) and key (seed, model); words 2j, 2j + 1 (j = e mod 2) give u1 in (0, 1] and
+// u2 in [0, 1) (53 bits each) and the Box-Muller cosine branch sqrt(-2 ln u1) cos(2 pi u2).
+double philox_normal(uint64_t seed, uint64_t model, uint64_t e) {
+    const uint64_t ctr[4] = {e >> 1, 0, 0, 0}, key[2] = {seed, model};
+    uint64_t r[4];
+    philox4x64_10(ctr, key, r);
+    const int j = (int)(e & 1);
+    const double u1 = (double)((r[2 * j] >> 11) + 1) * 0x1.0p-53;
+    const double u2 = (double)(r[2 * j + 1] >> 11) * 0x1.0p-53;
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586476925286766559 * u2);
+}
+
+}  // namespace
+}  // namespace gwe
+
+extern "C" {
+
+void gwe_philox4x64_10(const uint64_t *counter, const uint64_t *key, uint64_t *out) {
+    philox4x64_10(counter, key, out);
+}
+
+gwe_status gwe_init_weights(const gwe_model_config *cfg, uint64_t seed, float *host_out) {
+    clear_error();
+    Dims d;
+    GWE_ARG_CHECK(make_dims(cfg, &d), "invalid configuration");
+    GWE_ARG_CHECK(host_out != nullptr, "host_out is NULL");
+    // fan-in per weight tensor: inputs x kernel taps of the layer it feeds
+    for (int mi = 0; mi < d.n_models; ++mi) {
+        float *w = host_out + (int64_t)mi * d.P;
+        std::fill(w, w + d.P, 0.f);
+        auto fill = [&](int64_t off, int64_t n, int fan_in) {
+            const double sc = 1.0 / std::sqrt((double)fan_in);
+            for (int64_t e = off; e < off + n; ++e) w[e] = (float)(philox_normal(seed, (uint64_t)mi, (uint64_t)e) * sc);
+        };
+        for (int b = 0; b < 2; ++b) {
+            fill(off_branch(d, b), d.R, 1);                                   // w_in (1 channel, 1 tap)
+            for (int l = 0; l < d.L; ++l) {
+                fill(off_wconv(d, b, l), (int64_t)2 * d.R * d.k * d.R, d.R * d.k);
+                fill(off_wres(d, b, l), (int64_t)d.R * d.R, d.R);
+                fill(off_wskip(d, b, l), (int64_t)d.S * d.R, d.R);
+            }
+        }
+        fill(off_wh1(d), (int64_t)d.Hc * 2 * d.S, 2 * d.S);
+        fill(off_wh2(d), d.Hc, d.Hc);
+    }
+    return GWE_OK;
+}
+
+gwe_status gwe_model_init_random(const gwe_model_config *cfg, uint64_t seed, int precision, gwe_model **out) {
+    clear_error();
+    GWE_ARG_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    Dims d;
+    GWE_ARG_CHECK(make_dims(cfg, &d), "invalid configuration");
+    std::vector<float> hb;
+    try {
+        hb.resize((size_t)d.P * d.n_models);
+    } catch (...) {
+        set_error("host allocation failed");
+        return GWE_ERR_OOM;
+    }
+    gwe_status st = gwe_init_weights(cfg, seed, hb.data());
+    if (st != GWE_OK) return st;
+    return gwe_model_create(cfg, hb.data(), precision, out);
+}
+
 gwe_status gwe_model_create(const gwe_model_config *cfg, const float *host_weights, int precision,
                             gwe_model **out) {
     clear_error();
@@ -148,6 +247,20 @@ gwe_status gwe_model_set_weights(gwe_model *m, const float *hb) {
     return GWE_OK;
 }
 
+gwe_status gwe_model_set_weights_device(gwe_model *m, const float *dev_weights, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr && dev_weights != nullptr, "NULL argument");
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = (size_t)m->dims.P * m->dims.n_models * sizeof(float);
+    if (dev_weights != m->w32.as<float>())
+        GWE_CUDA_TRY(cudaMemcpyAsync(m->w32.ptr, dev_weights, bytes, cudaMemcpyDeviceToDevice, st));
+    ++m->wstamp;
+    gwe_status r = fp32_repack_device(m, st);
+    if (r != GWE_OK) return r;
+    if (m->precision == GWE_BF16 || m->precision == GWE_FP8) return tc_rebuild_from_device(m, st);
+    return GWE_OK;
+}
+
 gwe_status gwe_model_calibrate(gwe_model *m, const float *sH, const float *sL, int64_t n, int window, int stride,
                                void *stream) {
     clear_error();
@@ -173,6 +286,21 @@ gwe_status gwe_model_set_fp8_amax(gwe_model *m, const float *amax) {
     for (int64_t i = 0; i < n; ++i)
         GWE_ARG_CHECK(std::isfinite(amax[i]) && amax[i] >= 0.f, "amax entries must be finite and >= 0");
     return tc_set_amax(m, amax);
+}
+
+gwe_status gwe_model_set_f16_layers(gwe_model *m, int n) {
+    clear_error();
+    GWE_ARG_CHECK(m != nullptr, "model is NULL");
+    if (m->precision != GWE_BF16) {
+        set_error("gwe_model_set_f16_layers: not a GWE_BF16 handle");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    return tc_set_f16_layers(m, n);
+}
+
+int gwe_model_f16_layers(const gwe_model *m) {
+    if (!m || m->precision != GWE_BF16) return 0;
+    return tc_f16_layers(const_cast<gwe_model *>(m));
 }
 
 gwe_status gwe_model_get_fp8_amax(gwe_model *m, float *amax) {
@@ -306,6 +434,50 @@ gwe_status gwe_triggers_segments(const float *prob, int n_models, int n_slides, 
     }
     return triggers_run_segments(prob, n_models, n_slides, nw.data(), n_segments, window, stride, height_thr,
                                  min_width, coinc, flags, out, out_segment, cap, n_out, as_stream(stream));
+}
+
+static gwe_status check_sweep(const float *thr, int n_thr, int64_t *ens_counts) {
+    GWE_ARG_CHECK(thr != nullptr && n_thr > 0, "no thresholds");
+    GWE_ARG_CHECK(ens_counts != nullptr, "ens_counts is NULL");
+    for (int k = 0; k < n_thr; ++k) {
+        GWE_ARG_CHECK(std::isfinite(thr[k]), "thresholds must be finite");
+        GWE_ARG_CHECK(k == 0 || thr[k] >= thr[k - 1], "thresholds must be in ascending order");
+    }
+    return GWE_OK;
+}
+
+gwe_status gwe_trigger_sweep(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,
+                             int stride, const float *thresholds, int n_thr, double min_width, int64_t coinc,
+                             int64_t *ens_counts, int64_t *model_counts, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(prob != nullptr, "prob is NULL");
+    GWE_ARG_CHECK(n_models > 0 && n_slides >= 0 && n_windows >= 0, "bad counts");
+    GWE_ARG_CHECK(window > 0 && stride > 0 && stride <= window, "bad window/stride");
+    GWE_ARG_CHECK(coinc >= 0, "coinc must be >= 0");
+    gwe_status r = check_sweep(thresholds, n_thr, ens_counts);
+    if (r != GWE_OK) return r;
+    return triggers_sweep(prob, n_models, n_slides, &n_windows, 1, window, stride, thresholds, n_thr, min_width, coinc,
+                          ens_counts, model_counts, as_stream(stream));
+}
+
+gwe_status gwe_trigger_sweep_segments(const float *prob, int n_models, int n_slides, const int64_t *seg_len,
+                                      int n_segments, int window, int stride, const float *thresholds, int n_thr,
+                                      double min_width, int64_t coinc, int64_t *ens_counts, int64_t *model_counts,
+                                      void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(prob != nullptr && seg_len != nullptr, "NULL argument");
+    GWE_ARG_CHECK(n_models > 0 && n_slides >= 0 && n_segments > 0, "bad counts");
+    GWE_ARG_CHECK(window > 0 && stride > 0 && stride <= window, "bad window/stride");
+    GWE_ARG_CHECK(coinc >= 0, "coinc must be >= 0");
+    gwe_status r = check_sweep(thresholds, n_thr, ens_counts);
+    if (r != GWE_OK) return r;
+    std::vector<int64_t> nw(n_segments);
+    for (int g = 0; g < n_segments; ++g) {
+        GWE_ARG_CHECK(seg_len[g] >= 0, "negative segment length");
+        nw[g] = gwe_n_windows(seg_len[g], window, stride);
+    }
+    return triggers_sweep(prob, n_models, n_slides, nw.data(), n_segments, window, stride, thresholds, n_thr,
+                          min_width, coinc, ens_counts, model_counts, as_stream(stream));
 }
 
 gwe_status gwe_sync(gwe_model *m, void *stream) {

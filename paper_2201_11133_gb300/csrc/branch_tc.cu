@@ -37,6 +37,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,9 +90,9 @@ struct TcShape {
     static constexpr uint32_t SKIP_BYTES = S * R * 2;
     static constexpr uint32_t RS_BYTES = RES_BYTES + SKIP_BYTES;
     static constexpr uint32_t HEADP_BYTES = HP * HQ * 2;
-    // per-layer bias slots: conv = FP16 b_conv [2R] (BF16) or FP32 {scale, bias} [2R] (FP8);
+    // per-layer bias slots: conv = FP32 b_conv [2R] (16-bit path) or FP32 {scale, bias} [2R] (FP8);
     // res = FP32 b_res [R] (+ FP8: the next layer's input quantisation factors [R])
-    static constexpr uint32_t CB_BYTES = F8 ? 16 * R : 4 * R;
+    static constexpr uint32_t CB_BYTES = F8 ? 16 * R : 8 * R;
     static constexpr uint32_t RB_BYTES = F8 ? 8 * R : 4 * R;
     static constexpr uint32_t ECONV = cmax(CONV_BYTES, HEADP_BYTES);
     static constexpr uint32_t ERS = cmax(RS_BYTES, HEADP_BYTES);
@@ -171,6 +172,7 @@ struct TcParams {
     int L, lps;
     uint64_t ring_rows;        // lag-history rows per branch (sum of dilations)
     int *err;                  // error word: wait site of the first timeout
+    int n16;                   // 16-bit path: layers l < n16 take FP16 conv operands, the others BF16
     int model0;                // jobs cover models model0 .. model0 + n_models - 1
     // Projection mode (proj != NULL): instead of the head, store per branch the head's first
     // convolution restricted to that branch, P_H = W_h1[:, H] ReLU(s_H) + b_h1 and
@@ -217,6 +219,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t *>(&h);
+}
+// conv operand pair of the 16-bit path: FP16 (f16 = true) or BF16
+__device__ __forceinline__ uint32_t pack_x2(float a, float b, bool f16) {
+    return f16 ? pack_h2(a, b) : pack_bf16(a, b);
+}
+__device__ __forceinline__ float tanh_f32(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 __device__ __forceinline__ uint32_t tanh_h2(uint32_t x) {
     uint32_t y;
@@ -459,6 +470,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             // -------------------------------------------------------- MMA issuer of branch b (+ head on branch 0)
             if (lane == 0) {
                 constexpr uint32_t ID_CONV = F8 ? idesc_e4m3(128, Sh::N1) : idesc_f16(128, Sh::N1, 1);
+                // layers l < n16 of the 16-bit path: both conv operands FP16 (same descriptor form as
+                // the residual / skip MMAs); never one FP16 and one BF16 operand
+                constexpr uint32_t ID_CONV16 = idesc_f16(128, Sh::N1, 0);
                 constexpr uint32_t ID_RES = idesc_f16(128, R, 0);
                 constexpr uint32_t ID_SKIP = idesc_f16(128, S, 0);
                 constexpr uint32_t ID_HEAD = idesc_f16(128, Sh::HP, 0);
@@ -502,11 +516,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             tc_fence_after();
                             // K = 2R in steps of 16: the lagged rows (staging rows 128 - n ..), then the current ones
                             const uint64_t a_lag = a_lag0 + (uint64_t)(kTile - n);
+                            const uint32_t id_conv = (!F8 && l < p.n16) ? ID_CONV16 : ID_CONV;
                             auto conv_mma = [&](uint64_t ad, uint64_t bd, uint32_t acc) {
                                 if constexpr (F8)
                                     mma_f8(dcol, ad, bd, ID_CONV, acc);
                                 else
-                                    mma_f16(dcol, ad, bd, ID_CONV, acc);
+                                    mma_f16(dcol, ad, bd, id_conv, acc);
                             };
                             conv_mma(a_lag, b_conv0, 0u);
 #pragma unroll
@@ -606,9 +621,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[idx]);
         };
-        // x (FP32 registers) -> this thread's chunks of the staging row: BF16, or FP8 E4M3 after
-        // multiplying by the next layer's per-channel quantisation factors `inv` (FP32)
-        auto store_x = [&](const float *inv_g, uint32_t inv_s) {
+        // x (FP32 registers) -> this thread's chunks of the staging row for the conv of layer lc:
+        // FP16 (lc < n16) or BF16, or FP8 E4M3 after multiplying by layer lc's per-channel
+        // quantisation factors `inv` (FP32)
+        auto store_x = [&](const float *inv_g, uint32_t inv_s, int lc) {
             if constexpr (F8) {
 #pragma unroll
                 for (int c = 0; c < RH / 16; ++c) {
@@ -634,44 +650,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                            make_uint4(wv[0], wv[1], wv[2], wv[3]));
                 }
             } else {
+                const bool f16 = lc < p.n16;
 #pragma unroll
                 for (int c = 0; c < RH / 8; ++c) {
                     uint4 v;
-                    v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
-                    v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
-                    v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
-                    v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+                    v.x = pack_x2(x[8 * c + 0], x[8 * c + 1], f16);
+                    v.y = pack_x2(x[8 * c + 2], x[8 * c + 3], f16);
+                    v.z = pack_x2(x[8 * c + 4], x[8 * c + 5], f16);
+                    v.w = pack_x2(x[8 * c + 6], x[8 * c + 7], f16);
                     sts128(st + (hf * (RH / 8) + c) * Sh::STAGE_LBO + (kTile + r) * 16, v);
                 }
             }
         };
-        // z for 16 channels starting at ch from the f / g accumulator columns
+        // z for 16 channels starting at ch from the f / g accumulator columns, in FP32:
+        // f = acc_f + b_f, g/2 = acc_g + b_g/2 (the g half of the conv weights and biases is
+        // pre-halved), z = tanh(f) * (0.5 tanh(g/2) + 0.5); z leaves as FP16 pairs (the operand of
+        // the residual / skip MMAs).  FP8: acc is first multiplied by the output channel's weight
+        // scale (FP32 {scale, bias} pairs).
         auto gate16 = [&](const uint32_t (&fr)[16], const uint32_t (&gr)[16], int ch, uint32_t bslot, uint32_t (&zz)[8]) {
-            if constexpr (F8) {
-                // a = acc * scale + bias per output channel (FP32 {scale, bias} pairs), then as below
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const uint4 sf = lds128(bslot + (ch + 2 * jj) * 8);          // {s, b} of f channels 2jj, 2jj+1
-                    const uint4 sg4 = lds128(bslot + (R + ch + 2 * jj) * 8);     // same for g
-                    const float f0 = fmaf(__uint_as_float(fr[2 * jj]), __uint_as_float(sf.x), __uint_as_float(sf.y));
-                    const float f1 = fmaf(__uint_as_float(fr[2 * jj + 1]), __uint_as_float(sf.z), __uint_as_float(sf.w));
-                    const float g0 = fmaf(__uint_as_float(gr[2 * jj]), __uint_as_float(sg4.x), __uint_as_float(sg4.y));
-                    const float g1 = fmaf(__uint_as_float(gr[2 * jj + 1]), __uint_as_float(sg4.z), __uint_as_float(sg4.w));
-                    const uint32_t sgm = hfma2(tanh_h2(pack_h2(g0, g1)), half2_half, half2_half);
-                    zz[jj] = hmul2(tanh_h2(pack_h2(f0, f1)), sgm);
-                }
-                return;
-            }
-            const uint4 bf0 = lds128(bslot + ch * 2), bf1 = lds128(bslot + ch * 2 + 16);
-            const uint4 bg0 = lds128(bslot + (R + ch) * 2), bg1 = lds128(bslot + (R + ch) * 2 + 16);
-            const uint32_t bfw[8] = {bf0.x, bf0.y, bf0.z, bf0.w, bf1.x, bf1.y, bf1.z, bf1.w};
-            const uint32_t bgw[8] = {bg0.x, bg0.y, bg0.z, bg0.w, bg1.x, bg1.y, bg1.z, bg1.w};
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
-                const uint32_t hfv = hadd2(pack_h2(__uint_as_float(fr[2 * jj]), __uint_as_float(fr[2 * jj + 1])), bfw[jj]);
-                const uint32_t hgv = hadd2(pack_h2(__uint_as_float(gr[2 * jj]), __uint_as_float(gr[2 * jj + 1])), bgw[jj]);
-                const uint32_t sg = hfma2(tanh_h2(hgv), half2_half, half2_half);
-                zz[jj] = hmul2(tanh_h2(hfv), sg);
+                float f0, f1, g0, g1;
+                if constexpr (F8) {
+                    const uint4 sf = lds128(bslot + (ch + 2 * jj) * 8);          // {s, b} of f channels 2jj, 2jj+1
+                    const uint4 sg4 = lds128(bslot + (R + ch + 2 * jj) * 8);     // same for g
+                    f0 = fmaf(__uint_as_float(fr[2 * jj]), __uint_as_float(sf.x), __uint_as_float(sf.y));
+                    f1 = fmaf(__uint_as_float(fr[2 * jj + 1]), __uint_as_float(sf.z), __uint_as_float(sf.w));
+                    g0 = fmaf(__uint_as_float(gr[2 * jj]), __uint_as_float(sg4.x), __uint_as_float(sg4.y));
+                    g1 = fmaf(__uint_as_float(gr[2 * jj + 1]), __uint_as_float(sg4.z), __uint_as_float(sg4.w));
+                } else {
+                    // FP32 biases of f channels ch + 2jj, +1 and of the matching g channels
+                    uint32_t bfv0, bfv1, bgv0, bgv1;
+                    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(bfv0), "=r"(bfv1) : "r"(bslot + (ch + 2 * jj) * 4));
+                    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(bgv0), "=r"(bgv1) : "r"(bslot + (R + ch + 2 * jj) * 4));
+                    f0 = __uint_as_float(fr[2 * jj]) + __uint_as_float(bfv0);
+                    f1 = __uint_as_float(fr[2 * jj + 1]) + __uint_as_float(bfv1);
+                    g0 = __uint_as_float(gr[2 * jj]) + __uint_as_float(bgv0);
+                    g1 = __uint_as_float(gr[2 * jj + 1]) + __uint_as_float(bgv1);
+                }
+                const float s0 = fmaf(tanh_f32(g0), 0.5f, 0.5f), s1 = fmaf(tanh_f32(g1), 0.5f, 0.5f);
+                zz[jj] = pack_h2(tanh_f32(f0) * s0, tanh_f32(f1) * s1);
             }
         };
 
@@ -720,7 +738,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     tmem_st_wait();
                     // quantisation factors of layer l0 (FP8): the residual slot of layer l0 - 1
                     store_x(reinterpret_cast<const float *>(pbr + Sh::HDR_BYTES + (uint64_t)(l0 - 1) * Sh::PL_BYTES +
-                                                            Sh::CB_BYTES) + R + c0, 0u);
+                                                            Sh::CB_BYTES) + R + c0, 0u, l0);
                     fence_proxy_async_smem();
                     tc_fence_before();
                     warp_arrive(B_XREADY + b);
@@ -735,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         x[4 * c4 + 2] = fmaf(wi.z, sval, bi.z);
                         x[4 * c4 + 3] = fmaf(wi.w, sval, bi.w);
                     }
-                    store_x(reinterpret_cast<const float *>(pbr + 8 * R + 4 * S) + c0, 0u);
+                    store_x(reinterpret_cast<const float *>(pbr + 8 * R + 4 * S) + c0, 0u, 0);
                     fence_proxy_async_smem();
                     tc_fence_before();
                     warp_arrive(B_XREADY + b);
@@ -755,7 +773,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         !warp_wait(B_BIAS + 4 * b + (g & 1), (g >> 1) & 1, 36)) { ok = false; break; }
                     ++ph_conv;
                     tc_fence_after();
-                    // gate: z = tanh(f + b_f) * (0.5 tanh(g/2 + b_g/2) + 0.5), FP16x2
+                    // gate: z = tanh(f + b_f) * (0.5 tanh(g/2 + b_g/2) + 0.5), FP32
                     {
                         const uint32_t bslot = sb + (g & 1) * Sh::CB_BYTES;
                         uint32_t fa[16], ga[16];
@@ -796,13 +814,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                                     lds128(st + ck * Sh::STAGE_LBO + (kTile + r) * 16);
                             }
                         } else {
+                            // the format of layer l's conv operand
+                            const bool f16 = l < p.n16;
 #pragma unroll
                             for (int c = 0; c < RH / 8; ++c) {
                                 uint4 v;
-                                v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
-                                v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
-                                v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
-                                v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+                                v.x = pack_x2(x[8 * c + 0], x[8 * c + 1], f16);
+                                v.y = pack_x2(x[8 * c + 2], x[8 * c + 3], f16);
+                                v.z = pack_x2(x[8 * c + 4], x[8 * c + 5], f16);
+                                v.w = pack_x2(x[8 * c + 6], x[8 * c + 7], f16);
                                 *reinterpret_cast<uint4 *>(dst + (uint64_t)(hf * (RH / 8) + c) * d * 16) = v;
                             }
                         }
@@ -835,7 +855,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         tmem_ld_wait();
 #pragma unroll
                         for (int k = 0; k < RH; ++k) x[k] += __uint_as_float(rr[k]);
-                        store_x(nullptr, rslot + (R + c0) * 4);
+                        store_x(nullptr, rslot + (R + c0) * 4, l + 1);
                         fence_proxy_async_smem();
                         tc_fence_before();
                         warp_arrive(B_XREADY + b);
@@ -987,7 +1007,8 @@ template <int HC, int T>
 __global__ void __launch_bounds__(T) k_slide_head(const uint16_t *__restrict__ proj, int64_t nw, int W,
                                                   const int32_t *__restrict__ koff, int n_slides, int spb, int n_seg,
                                                   const int64_t *__restrict__ seg_w0,
-                                                  const float *__restrict__ w2, float b2, float *__restrict__ out,
+                                                  const float *__restrict__ w2, const float *__restrict__ b2p,
+                                                  float *__restrict__ out,
                                                   int64_t slide_stride, int logits) {
     constexpr int NC = HC / 8;                    // 16-byte chunks per sample
     extern __shared__ uint4 ph_s[];               // [NC][T]
@@ -1007,6 +1028,7 @@ __global__ void __launch_bounds__(T) k_slide_head(const uint16_t *__restrict__ p
     const uint4 *pH = reinterpret_cast<const uint4 *>(proj + (uint64_t)w * HC * W);
     for (int c = 0; c < NC; ++c) ph_s[c * T + t] = pH[(uint64_t)c * W + t0 + t];
     for (int j = t; j < HC / 2; j += T) w2h[j] = pack_h2(w2[2 * j], w2[2 * j + 1]);
+    const float b2 = __ldg(b2p);
     __syncthreads();
     const uint32_t one2 = 0x3C003C00u;            // (1, 1) in FP16x2
     // Livingston window of slide si (wrapping within the segment)
@@ -1149,13 +1171,13 @@ struct SlideShape {
 
 struct TcState {
     int variant = -1;            // 0: (R, S, Hc) = (32, 32, 32); 1: (64, 128, 256)
-    bool f8 = false;             // FP8 E4M3 dilated convolutions (else BF16)
+    bool f8 = false;             // FP8 E4M3 dilated convolutions (else 16-bit: FP16 / BF16)
+    int n16 = 0;                 // 16-bit path: layers l < n16 take FP16 conv operands, the rest BF16
     std::vector<float> amax;     // FP8: calibrated max |x_l| per [model][branch][layer][channel]
     DevBuf img, pblob, zeros, err, slides;
     TcWork work;                 // buffers of the handle's own forward calls
     uint64_t img_stride = 0, pblob_stride = 0;
     int sms = 0;
-    std::vector<float> b2_host;   // b_h2 per model (slide heads take it by value)
 };
 
 int tc_variant(const Dims &d) {
@@ -1193,8 +1215,9 @@ constexpr float kE4M3Max = 448.f;
 inline float f8_act_scale(float amax) { return amax > 0.f ? kF8Margin * amax / kE4M3Max : 1.f; }
 inline uint8_t to_e4m3(float f) { return (uint8_t)__nv_cvt_float_to_fp8(f, __NV_SATFINITE, __NV_E4M3); }
 
+// n16 (16-bit path): layers l < n16 store their conv weights in FP16, the others in BF16
 template <int R, int S, int HC, bool F8>
-void build_images(const Dims &d, const float *hb, const float *amax, std::vector<uint8_t> &img,
+void build_images(const Dims &d, const float *hb, const float *amax, int n16, std::vector<uint8_t> &img,
                   std::vector<uint8_t> &pbl, uint64_t &img_stride, uint64_t &pb_stride) {
     using Sh = TcShape<R, S, HC, F8>;
     // amax (FP8 only): [model][branch][layer][channel]
@@ -1230,12 +1253,13 @@ void build_images(const Dims &d, const float *hb, const float *amax, std::vector
                         wscale[((int64_t)b * L + l) * 2 * R + o] = wo;
                     }
                 } else {
+                    const bool f16 = l < n16;
                     for (int o = 0; o < 2 * R; ++o)
                         for (int k = 0; k < 2 * R; ++k) {
                             const int tap = k < R ? 0 : 1, i = k % R;
                             float v = wc[((int64_t)o * 2 + tap) * R + i];
                             if (o >= R) v *= 0.5f;
-                            put16(tmp, chunk_off(2 * R, o, k), to_bf16(v));
+                            put16(tmp, chunk_off(2 * R, o, k), f16 ? to_f16(v) : to_bf16(v));
                         }
                 }
                 std::memcpy(im0 + (uint64_t)l * Sh::LAYER_IMG + (uint64_t)b * Sh::CONV_BYTES, tmp.data(), tmp.size());
@@ -1293,10 +1317,9 @@ void build_images(const Dims &d, const float *hb, const float *amax, std::vector
                         sb[2 * o + 1] = hlf * bc[o];
                     }
                 } else {
-                    for (int o = 0; o < 2 * R; ++o) {
-                        const uint16_t h = to_f16(o < R ? bc[o] : 0.5f * bc[o]);
-                        std::memcpy(pl + 2 * o, &h, 2);
-                    }
+                    // FP32 b_conv, g half pre-halved
+                    float *bcs = reinterpret_cast<float *>(pl);
+                    for (int o = 0; o < 2 * R; ++o) bcs[o] = o < R ? bc[o] : 0.5f * bc[o];
                 }
                 float *br = reinterpret_cast<float *>(pl + Sh::CB_BYTES);
                 for (int c = 0; c < R; ++c) br[c] = src[off_bres(d, b, l) + c];
@@ -1312,6 +1335,95 @@ void build_images(const Dims &d, const float *hb, const float *amax, std::vector
         }
         ph[2 * HC] = src[off_bh2(d)];
     }
+}
+
+// The images of the 16-bit path built on the device from the FP32 blobs (one thread per blob
+// element scatters it; the skip-bias sums by k_pack_bsk); the same bytes as build_images<.., false>.
+__device__ __forceinline__ size_t chunk_off_d(int rows, int n, int k) {
+    return (size_t)(k / 8) * rows * 16 + (size_t)n * 16 + (k % 8) * 2;
+}
+
+template <int R, int S, int HC>
+__global__ void k_pack_tc16(const float *__restrict__ blob, int64_t P, int n_models, int L, int n16, int64_t Pb,
+                            int64_t Pl, uint8_t *__restrict__ img, uint64_t img_stride, uint8_t *__restrict__ pbl,
+                            uint64_t pb_stride) {
+    using Sh = TcShape<R, S, HC, false>;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= P * n_models) return;
+    const int mi = (int)(gid / P);
+    const int64_t e = gid % P;
+    const float v = blob[gid];
+    uint8_t *im = img + img_stride * mi;
+    uint8_t *pm = pbl + pb_stride * mi;
+    auto put_b16 = [&](size_t off, float x) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        *reinterpret_cast<__nv_bfloat16 *>(im + off) = h;
+    };
+    auto put_f16 = [&](size_t off, float x) { *reinterpret_cast<__half *>(im + off) = __float2half_rn(x); };
+    if (e < 2 * Pb) {
+        const int b = (int)(e / Pb);
+        int64_t r = e % Pb;
+        float *pf = reinterpret_cast<float *>(pm + (uint64_t)b * Sh::pb_bytes(L));
+        if (r < 2 * R) {                       // w_in, b_in
+            pf[r] = v;
+            return;
+        }
+        r -= 2 * R;
+        const int l = (int)(r / Pl);
+        int64_t q = r % Pl;
+        float *pl = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(pf) + Sh::HDR_BYTES + (uint64_t)l * Sh::PL_BYTES);
+        const uint64_t lay = (uint64_t)l * Sh::LAYER_IMG;
+        if (q < 4LL * R * R) {                 // conv (o, tap, i) -> row o, K = tap * R + i; g half halved
+            const int o = (int)(q / (2 * R)), k = (int)(q % (2 * R));
+            const float x = o < R ? v : 0.5f * v;
+            const size_t off = lay + (uint64_t)b * Sh::CONV_BYTES + chunk_off_d(2 * R, o, k);
+            if (l < n16) put_f16(off, x); else put_b16(off, x);
+            return;
+        }
+        if ((q -= 4LL * R * R) < 2 * R) {      // b_conv (FP32, g half halved)
+            pl[q] = q < R ? v : 0.5f * v;
+            return;
+        }
+        if ((q -= 2 * R) < (int64_t)R * R) {   // w_res (o, k)
+            put_f16(lay + 2ull * Sh::CONV_BYTES + (uint64_t)b * Sh::RS_BYTES + chunk_off_d(R, (int)(q / R), (int)(q % R)), v);
+            return;
+        }
+        if ((q -= (int64_t)R * R) < R) {       // b_res
+            reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(pl) + Sh::CB_BYTES)[q] = v;
+            return;
+        }
+        if ((q -= R) < (int64_t)S * R) {       // w_skip (o, k)
+            put_f16(lay + 2ull * Sh::CONV_BYTES + (uint64_t)b * Sh::RS_BYTES + Sh::RES_BYTES +
+                        chunk_off_d(S, (int)(q / R), (int)(q % R)),
+                    v);
+            return;
+        }
+        return;                                // b_skip: summed by k_pack_bsk
+    }
+    int64_t h = e - 2 * Pb;
+    if (h < (int64_t)HC * 2 * S) {             // w_h1 (j, c) -> piece (j / HP, c / HQ), row j % HP, K c % HQ
+        const int j = (int)(h / (2 * S)), c = (int)(h % (2 * S));
+        const int pc = (j / Sh::HP) * 4 + c / Sh::HQ;
+        put_f16((uint64_t)L * Sh::LAYER_IMG + (uint64_t)pc * Sh::HEADP_BYTES + chunk_off_d(Sh::HP, j % Sh::HP, c % Sh::HQ), v);
+        return;
+    }
+    h -= (int64_t)HC * 2 * S;
+    reinterpret_cast<float *>(pm + 2ull * Sh::pb_bytes(L))[h] = v;   // b_h1 [HC], w_h2 [HC], b_h2
+}
+
+// summed skip biases per (model, branch, channel), FP64 in layer order as the host builder
+template <int R, int S, int HC>
+__global__ void k_pack_bsk(const float *__restrict__ blob, int64_t P, int n_models, int L, int64_t Pb, int64_t Pl,
+                           uint8_t *__restrict__ pbl, uint64_t pb_stride) {
+    using Sh = TcShape<R, S, HC, false>;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_models * 2 * S) return;
+    const int mi = i / (2 * S), b = (i / S) % 2, c = i % S;
+    const float *src = blob + (int64_t)mi * P + (int64_t)b * Pb + 2 * R;
+    const int64_t boff = (int64_t)2 * R * 2 * R + 2 * R + (int64_t)R * R + R + (int64_t)S * R;   // b_skip in a layer
+    double acc = 0.0;
+    for (int l = 0; l < L; ++l) acc += (double)src[(int64_t)l * Pl + boff + c];
+    reinterpret_cast<float *>(pbl + pb_stride * mi + (uint64_t)b * Sh::pb_bytes(L))[2 * R + c] = (float)acc;
 }
 
 template <int R, int S, int HC, bool F8>
@@ -1413,6 +1525,7 @@ gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const
     p.lps = d.lps;
     p.ring_rows = ring_rows;
     p.err = s.err.as<int>();
+    p.n16 = s.f8 ? 0 : s.n16;
     p.model0 = 0;
     p.proj = nullptr;
     p.save_x = nullptr;
@@ -1442,7 +1555,7 @@ gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const
 }
 
 template <int HC, int T>
-void launch_slide_head(const TcLaunch &L, const float *w2, float b2, float *out, cudaStream_t st) {
+void launch_slide_head(const TcLaunch &L, const float *w2, const float *b2, float *out, cudaStream_t st) {
     const int spb = L.shape.spb > 0 ? L.shape.spb : L.n_slides;
     dim3 g2((unsigned)L.nw, (unsigned)(L.p.W / T), (unsigned)((L.n_slides + spb - 1) / spb));
     k_slide_head<HC, T><<<g2, T, (HC / 8) * T * 16, st>>>(L.proj, L.nw, L.p.W, L.dsl, L.n_slides, spb, L.p.n_seg,
@@ -1454,8 +1567,10 @@ void launch_slide_head(const TcLaunch &L, const float *w2, float b2, float *out,
 template <int HC>
 gwe_status issue_slide_heads(gwe_model *m, TcState &s, const TcLaunch &L, int mi, cudaStream_t st) {
     const Dims &d = m->dims;
+    // w_h2 and b_h2 are read from the handle's FP32 blob on the device, so that a recorded graph
+    // picks up later weight changes
     const float *w2 = m->w32.as<float>() + (int64_t)mi * d.P + off_wh2(d);
-    const float b2 = s.b2_host[mi];
+    const float *b2 = m->w32.as<float>() + (int64_t)mi * d.P + off_bh2(d);
     float *out = L.out + (int64_t)mi * L.nw * L.p.W;
     ProfScope prof("k_slide_head", st);
     switch (L.shape.tile) {
@@ -1570,7 +1685,7 @@ gwe_status build_upload(gwe_model *m, TcState &s, const float *hb) {
     std::vector<uint8_t> img, pbl;
     tc_dispatch(s, [&](auto t) {
         using T = decltype(t);
-        build_images<T::R, T::S, T::HC, T::F8>(d, hb, s.amax.data(), img, pbl, s.img_stride, s.pblob_stride);
+        build_images<T::R, T::S, T::HC, T::F8>(d, hb, s.amax.data(), s.n16, img, pbl, s.img_stride, s.pblob_stride);
         return 0;
     });
     GWE_CUDA_TRY(s.img.ensure(img.size()));
@@ -1580,9 +1695,54 @@ gwe_status build_upload(gwe_model *m, TcState &s, const float *hb) {
     return GWE_OK;
 }
 
+// the images of a 16-bit handle from its device FP32 blobs (m->w32), on `st`
+gwe_status build_device(gwe_model *m, TcState &s, cudaStream_t st) {
+    const Dims &d = m->dims;
+    return tc_dispatch(s, [&](auto t) -> gwe_status {
+        using T = decltype(t);
+        using Sh = TcShape<T::R, T::S, T::HC, false>;
+        if constexpr (T::F8) {
+            set_error("device weight packing covers the 16-bit path only");
+            return GWE_ERR_UNSUPPORTED;
+        } else {
+            s.img_stride = (Sh::img_bytes(d.L) + 255) & ~uint64_t(255);
+            s.pblob_stride = ((uint64_t)Sh::pm_bytes(d.L) + 255) & ~uint64_t(255);
+            GWE_CUDA_TRY(s.img.ensure(s.img_stride * d.n_models));
+            GWE_CUDA_TRY(s.pblob.ensure(s.pblob_stride * d.n_models));
+            GWE_CUDA_TRY(cudaMemsetAsync(s.img.ptr, 0, s.img_stride * d.n_models, st));
+            GWE_CUDA_TRY(cudaMemsetAsync(s.pblob.ptr, 0, s.pblob_stride * d.n_models, st));
+            const int64_t n = d.P * d.n_models;
+            k_pack_tc16<T::R, T::S, T::HC><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                m->w32.as<float>(), d.P, d.n_models, d.L, s.n16, d.Pb, d.Pl, s.img.as<uint8_t>(), s.img_stride,
+                s.pblob.as<uint8_t>(), s.pblob_stride);
+            const int nb = d.n_models * 2 * T::S;
+            k_pack_bsk<T::R, T::S, T::HC><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(
+                m->w32.as<float>(), d.P, d.n_models, d.L, d.Pb, d.Pl, s.pblob.as<uint8_t>(), s.pblob_stride);
+            note_launch(2);
+            GWE_CUDA_TRY(cudaGetLastError());
+            return GWE_OK;
+        }
+    });
+}
+
 }  // namespace
 
 bool tc_supported(const Dims &d) { return tc_variant(d) >= 0 && d.lps <= 10; }
+
+gwe_status tc_rebuild_from_device(gwe_model *m, cudaStream_t st) {
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
+    if (!s || s->variant < 0) {
+        set_error("tensor-core path not prepared");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    if (!s->f8) return build_device(m, *s, st);
+    // FP8: the E4M3 images need the per-row maxima of the scaled weights; built on the host
+    const Dims &d = m->dims;
+    GWE_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<float> hb((size_t)d.P * d.n_models);
+    GWE_CUDA_TRY(cudaMemcpy(hb.data(), m->w32.ptr, hb.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    return build_upload(m, *s, hb.data());
+}
 
 gwe_status tc_prepare(gwe_model *m, const float *hb, bool f8) {
     const Dims &d = m->dims;
@@ -1596,6 +1756,7 @@ gwe_status tc_prepare(gwe_model *m, const float *hb, bool f8) {
         s = new TcState();
         m->tc = s;
     }
+    if (s->variant < 0) s->n16 = f8 ? 0 : d.L / 3;   // default: the first third of the layers in FP16
     s->variant = tc_variant(d);
     s->f8 = f8;
     if (f8 && s->amax.size() != (size_t)d.n_models * 2 * d.L * d.R) {
@@ -1620,8 +1781,6 @@ gwe_status tc_prepare(gwe_model *m, const float *hb, bool f8) {
     GWE_CUDA_TRY(s->err.ensure(256));
     GWE_CUDA_TRY(cudaMemset(s->err.ptr, 0, 256));
     GWE_CUDA_TRY(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, m->device));
-    s->b2_host.resize(d.n_models);
-    for (int mi = 0; mi < d.n_models; ++mi) s->b2_host[mi] = hb[(int64_t)mi * d.P + off_bh2(d)];
     GWE_CUDA_TRY(tc_dispatch(*s, [](auto t) {
         using T = decltype(t);
         return set_tc_attr<T::R, T::S, T::HC, T::F8>();
@@ -1656,6 +1815,30 @@ gwe_status tc_set_amax(gwe_model *m, const float *amax) {
     std::vector<float> hb((size_t)d.P * d.n_models);
     GWE_CUDA_TRY(cudaMemcpy(hb.data(), m->w32.ptr, hb.size() * sizeof(float), cudaMemcpyDeviceToHost));
     return build_upload(m, *s, hb.data());
+}
+
+gwe_status tc_set_f16_layers(gwe_model *m, int n16) {
+    TcState *s = reinterpret_cast<TcState *>(m->tc);
+    if (!s || s->variant < 0 || s->f8) {
+        set_error("gwe_model_set_f16_layers: needs a GWE_BF16 handle");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    if (n16 < 0 || n16 > m->dims.L) {
+        set_error("gwe_model_set_f16_layers: n must lie in [0, layers]");
+        return GWE_ERR_ARG;
+    }
+    if (n16 == s->n16) return GWE_OK;
+    GWE_CUDA_TRY(cudaDeviceSynchronize());   // no launch may still read the old images
+    s->n16 = n16;
+    const Dims &d = m->dims;
+    std::vector<float> hb((size_t)d.P * d.n_models);
+    GWE_CUDA_TRY(cudaMemcpy(hb.data(), m->w32.ptr, hb.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    return build_upload(m, *s, hb.data());
+}
+
+int tc_f16_layers(gwe_model *m) {
+    const TcState *s = reinterpret_cast<const TcState *>(m->tc);
+    return (s && s->variant >= 0 && !s->f8) ? s->n16 : 0;
 }
 
 gwe_status tc_get_amax(gwe_model *m, float *amax) {
@@ -1775,18 +1958,29 @@ namespace gwe {
 namespace {
 
 constexpr size_t kStaticScratchBytes = 24u << 20;     // 24 MiB
-constexpr size_t kStaticErrOff = 0;                   // one int (wait site of a timeout)
-constexpr size_t kStaticZeroOff = 256;                // 4 KiB of zero rows
-constexpr size_t kStaticRingOff = 256 + 4096;         // per-CTA lag rings
+constexpr size_t kStaticZeroOff = 0;                  // 4 KiB of zero rows
+constexpr size_t kStaticRingOff = 4096;               // per-CTA lag rings
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_mu;
-uint8_t *g_static_ptr[kMaxDevices] = {};
+// Device address of the array, looked up once per device and CUDA context: the array's name in
+// host code is only a stand-in for it.  The lookup is keyed on the context's unique id
+// (cuCtxGetId, reached through the runtime's driver entry point) as well as the device ordinal,
+// because cudaDeviceReset destroys the primary context and the module, and the next context may
+// place the array at another address.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
 
-// Device address of the array for the current device, looked up once per device (the
-// array's name in host code is only a stand-in for it).
+struct StaticSlot {
+    unsigned long long ctx_id = 0;
+    uint8_t *ptr = nullptr;
+};
+std::mutex g_static_mu;
+StaticSlot g_static_slot[kMaxDevices];
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+
 gwe_status static_scratch(uint8_t **out) {
     int dev = 0;
     GWE_CUDA_TRY(cudaGetDevice(&dev));
@@ -1794,17 +1988,38 @@ gwe_status static_scratch(uint8_t **out) {
         set_error("gwe_forward_static: device ordinal out of range");
         return GWE_ERR_UNSUPPORTED;
     }
+    GWE_CUDA_TRY(cudaSetDevice(dev));   // makes the device's primary context current (allocates nothing)
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        GWE_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+        GWE_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            set_error("gwe_forward_static: cuCtxGetCurrent / cuCtxGetId not available from the driver");
+            return GWE_ERR_CUDA;
+        }
+        g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+        g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f2);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) {
+        set_error("gwe_forward_static: no current CUDA context");
+        return GWE_ERR_CUDA;
+    }
+    StaticSlot &slot = g_static_slot[dev];
+    if (slot.ptr == nullptr || slot.ctx_id != id) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || p == nullptr) {
             set_error(std::string("gwe_forward_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
             return GWE_ERR_CUDA;
         }
-        g_static_ptr[dev] = reinterpret_cast<uint8_t *>(p);
+        slot.ptr = reinterpret_cast<uint8_t *>(p);
+        slot.ctx_id = id;
     }
-    *out = g_static_ptr[dev];
+    *out = slot.ptr;
     return GWE_OK;
 }
 
@@ -1824,10 +2039,12 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
         return GWE_ERR_ARG;
     }
     const int grid = (int)std::min<int64_t>(std::min<int64_t>(s.sms, n_jobs), (int64_t)(cap / ring_cta));
-    int *err = status ? status : reinterpret_cast<int *>(scratch + kStaticErrOff);
-    // the error word and the zero rows must start at zero; the ring needs no clearing (rows before
-    // a window's start are read from the zero rows)
-    GWE_CUDA_TRY(cudaMemsetAsync(scratch, 0, kStaticRingOff, st));
+    // a timeout goes to the caller's status word, or without one to the handle's error word, which
+    // gwe_sync reads (and clears) as for every other call on the handle
+    int *err = status ? status : s.err.as<int>();
+    // the zero rows must be zero; the ring needs no clearing (rows before a window's start are read
+    // from the zero rows)
+    GWE_CUDA_TRY(cudaMemsetAsync(scratch + kStaticZeroOff, 0, kStaticRingOff - kStaticZeroOff, st));
     if (status) GWE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     TcParams p;
     p.wimg = s.img.as<uint8_t>();
@@ -1853,6 +2070,7 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.lps = d.lps;
     p.ring_rows = ring_rows;
     p.err = err;
+    p.n16 = s.f8 ? 0 : s.n16;
     p.model0 = 0;
     p.proj = nullptr;
     p.save_x = nullptr;

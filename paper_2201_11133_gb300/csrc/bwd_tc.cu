@@ -568,51 +568,61 @@ __global__ void k_f32_to_bf16(const float *__restrict__ in, __nv_bfloat16 *__res
 //   dgr  [R][4R]       row i: Wconv[o][1][i] at k = o, Wconv[o][0][i] at k = 2R + o
 struct TcBwd {
     DevBuf img;
-    std::vector<uint8_t> host;
     size_t conv_b = 0, rs_b = 0, dz_b = 0, dg_b = 0, layer_b = 0;
     int model = -1;
     uint64_t stamp = 0;
     DevBuf xsave, skip, dskip32, dskip16, x32, x16, gate16, z16, dx32[2], dx16[2], da16, err;
 };
 
-inline size_t choff(int rows, int n, int k) { return (size_t)(k / 8) * rows * 16 + (size_t)n * 16 + (k % 8) * 2; }
+__host__ __device__ inline size_t choff(int rows, int n, int k) { return (size_t)(k / 8) * rows * 16 + (size_t)n * 16 + (k % 8) * 2; }
 
-void put_bf16(std::vector<uint8_t> &v, size_t off, float x) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    std::memcpy(v.data() + off, &h, 2);
-}
+// BF16 B images of one member's branch layers, gathered on the device from its FP32 blob
+// (one thread per image element), per (layer, branch) in this order:
+//   conv  [2R rows: conv output o][2R K: tap * R + input i]         (recomputed forward)
+//   rs    [R + S rows: residual then skip output][R K: input i]     (recomputed forward)
+//   dz    [R rows: input i][R + S K: residual then skip output]     (dz = [dx | dskip] . [Wres ; Wskip])
+//   dg    [R rows: input i][4R K: (tap 1 outputs, tap 0 outputs)]   (dx = [da(t) | da(t + d)] . [W1 ; W0])
+// each in the chunk-column layout of choff.
+struct BwdGeo {
+    int R, S, L;
+    int64_t Pb, Pl;            // floats per branch / per layer of the blob
+    size_t conv_b, rs_b, dz_b, dg_b, layer_b;
+};
 
-void build_bwd_images(const Dims &d, const float *blob, TcBwd &t) {
-    const int R = d.R, S = d.S, L = d.L;
-    t.conv_b = (size_t)2 * R * 2 * R * 2;
-    t.rs_b = (size_t)(R + S) * R * 2;
-    t.dz_b = (size_t)R * (R + S) * 2;
-    t.dg_b = (size_t)R * 4 * R * 2;
-    t.layer_b = t.conv_b + t.rs_b + t.dz_b + t.dg_b;
-    t.host.assign(t.layer_b * 2 * L, 0);
-    for (int b = 0; b < 2; ++b)
-        for (int l = 0; l < L; ++l) {
-            const size_t base = t.layer_b * ((size_t)l * 2 + b);
-            const float *wc = blob + off_wconv(d, b, l);      // [2R][2][R]
-            const float *wr = blob + off_wres(d, b, l);       // [R][R]
-            const float *ws = blob + off_wskip(d, b, l);      // [S][R]
-            for (int o = 0; o < 2 * R; ++o)
-                for (int k = 0; k < 2 * R; ++k) put_bf16(t.host, base + choff(2 * R, o, k), wc[o * 2 * R + k]);
-            const size_t rs = base + t.conv_b;
-            for (int o = 0; o < R + S; ++o)
-                for (int i = 0; i < R; ++i)
-                    put_bf16(t.host, rs + choff(R + S, o, i), o < R ? wr[o * R + i] : ws[(o - R) * R + i]);
-            const size_t dz = rs + t.rs_b;
-            for (int i = 0; i < R; ++i)
-                for (int k = 0; k < R + S; ++k)
-                    put_bf16(t.host, dz + choff(R, i, k), k < R ? wr[k * R + i] : ws[(k - R) * R + i]);
-            const size_t dg = dz + t.dz_b;
-            for (int i = 0; i < R; ++i)
-                for (int k = 0; k < 4 * R; ++k) {
-                    const int o = k % (2 * R), tap = k < 2 * R ? 1 : 0;
-                    put_bf16(t.host, dg + choff(R, i, k), wc[(o * 2 + tap) * R + i]);
-                }
-        }
+__global__ void k_pack_bwd(const float *__restrict__ blob, BwdGeo g, __nv_bfloat16 *__restrict__ img) {
+    const int64_t per = (int64_t)(g.layer_b / 2);       // elements per (layer, branch)
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= per * 2 * g.L) return;
+    const int lb = (int)(e / per);
+    const int l = lb >> 1, b = lb & 1;
+    int64_t q = e % per;
+    const int R = g.R, S = g.S;
+    const float *lay = blob + (int64_t)b * g.Pb + 2 * R + (int64_t)l * g.Pl;
+    const float *wc = lay;                                             // [2R][2][R]
+    const float *wr = lay + (int64_t)2 * R * 2 * R + 2 * R;            // [R][R]
+    const float *ws = wr + (int64_t)R * R + R;                         // [S][R]
+    size_t off = g.layer_b * (size_t)lb;
+    float v;
+    if (q < 4LL * R * R) {                                             // conv: (o, k)
+        const int o = (int)(q / (2 * R)), k = (int)(q % (2 * R));
+        v = wc[(int64_t)o * 2 * R + k];
+        off += choff(2 * R, o, k);
+    } else if ((q -= 4LL * R * R) < (int64_t)(R + S) * R) {            // rs: (o, i)
+        const int o = (int)(q / R), i = (int)(q % R);
+        v = o < R ? wr[(int64_t)o * R + i] : ws[(int64_t)(o - R) * R + i];
+        off += g.conv_b + choff(R + S, o, i);
+    } else if ((q -= (int64_t)(R + S) * R) < (int64_t)R * (R + S)) {   // dz: (i, k)
+        const int i = (int)(q / (R + S)), k = (int)(q % (R + S));
+        v = k < R ? wr[(int64_t)k * R + i] : ws[(int64_t)(k - R) * R + i];
+        off += g.conv_b + g.rs_b + choff(R, i, k);
+    } else {                                                           // dg: (i, k)
+        q -= (int64_t)R * (R + S);
+        const int i = (int)(q / (4 * R)), k = (int)(q % (4 * R));
+        const int o = k % (2 * R), tap = k < 2 * R ? 1 : 0;
+        v = wc[((int64_t)o * 2 + tap) * R + i];
+        off += g.conv_b + g.rs_b + g.dz_b + choff(R, i, k);
+    }
+    img[off / 2] = __float2bfloat16_rn(v);
 }
 
 int g_rows_smem_set = 0;
@@ -727,14 +737,26 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
     }
     const int R = d.R, S = d.S, L = d.L, lps = d.lps, stacks = d.stacks;
     const float *blob = m->w32.as<float>() + (int64_t)mi * d.P;
-    // B images from the current FP32 weights (rebuilt when the weights or the member change)
+    // B images from the current FP32 weights, gathered on the device on `st` (rebuilt when the
+    // weights or the member change; no host round trip)
     const uint64_t stamp = m->wstamp;
-    if (t->model != mi || t->stamp != stamp || t->host.empty()) {
-        std::vector<float> hb((size_t)d.P);
-        GWE_CUDA_TRY(cudaMemcpy(hb.data(), blob, sizeof(float) * d.P, cudaMemcpyDeviceToHost));
-        build_bwd_images(d, hb.data(), *t);
-        GWE_CUDA_TRY(t->img.ensure(t->host.size()));
-        GWE_CUDA_TRY(cudaMemcpy(t->img.ptr, t->host.data(), t->host.size(), cudaMemcpyHostToDevice));
+    if (t->model != mi || t->stamp != stamp || t->layer_b == 0) {
+        BwdGeo g;
+        g.R = R;
+        g.S = S;
+        g.L = L;
+        g.Pb = d.Pb;
+        g.Pl = d.Pl;
+        g.conv_b = t->conv_b = (size_t)2 * R * 2 * R * 2;
+        g.rs_b = t->rs_b = (size_t)(R + S) * R * 2;
+        g.dz_b = t->dz_b = (size_t)R * (R + S) * 2;
+        g.dg_b = t->dg_b = (size_t)R * 4 * R * 2;
+        g.layer_b = t->layer_b = t->conv_b + t->rs_b + t->dz_b + t->dg_b;
+        GWE_CUDA_TRY(t->img.ensure(t->layer_b * 2 * L));
+        const int64_t n = (int64_t)(t->layer_b / 2) * 2 * L;
+        k_pack_bwd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(blob, g, t->img.as<__nv_bfloat16>());
+        note_launch();
+        GWE_CUDA_TRY(cudaGetLastError());
         t->model = mi;
         t->stamp = stamp;
     }

@@ -308,7 +308,96 @@ Variant variant_of(const Dims &d) {
 
 int64_t round4(int64_t x) { return (x + 3) & ~int64_t(3); }
 
+// The FP32 kernel layout (fp32_prepare's host loops) from the device blobs: one thread per blob
+// element writes it to its place; padding stays as cleared.
+struct F32Geo {
+    int R, S, Hc, L, n_models;
+    int64_t P, Pb, Pl, head_blob;
+    int64_t layer_stride, conv_off, rs_off, bconv_off, bres_off, bskip_off, layers_off, head_off, model_stride;
+};
+
+__global__ void k_pack_fp32(const float *__restrict__ blob, F32Geo g, float *__restrict__ out) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= g.P * g.n_models) return;
+    const int mi = (int)(gid / g.P);
+    const int64_t e = gid % g.P;
+    const int R = g.R, S = g.S, Hc = g.Hc;
+    float *dst = out + (int64_t)mi * g.model_stride;
+    const float v = blob[gid];
+    if (e < 2 * g.Pb) {
+        const int b = (int)(e / g.Pb);
+        int64_t r = e % g.Pb;
+        if (r < R) { dst[b * R + r] = v; return; }                      // w_in
+        if (r < 2 * R) { dst[2 * R + b * R + (r - R)] = v; return; }    // b_in
+        r -= 2 * R;
+        const int l = (int)(r / g.Pl);
+        int64_t q = r % g.Pl;
+        float *ly = dst + g.layers_off + ((int64_t)b * g.L + l) * g.layer_stride;
+        if (q < 4LL * R * R) {                                         // conv (o, tap, i)
+            const int o = (int)(q / (2 * R)), tap = (int)((q / R) % 2), i = (int)(q % R);
+            ly[g.conv_off + (int64_t)(tap * R + i) * 2 * R + o] = v;
+            return;
+        }
+        if ((q -= 4LL * R * R) < 2 * R) { ly[g.bconv_off + q] = v; return; }
+        if ((q -= 2 * R) < (int64_t)R * R) {                           // w_res (o, k)
+            ly[g.rs_off + (q % R) * (R + S) + q / R] = v;
+            return;
+        }
+        if ((q -= (int64_t)R * R) < R) { ly[g.bres_off + q] = v; return; }
+        if ((q -= R) < (int64_t)S * R) {                               // w_skip (o, k)
+            ly[g.rs_off + (q % R) * (R + S) + R + q / R] = v;
+            return;
+        }
+        q -= (int64_t)S * R;
+        ly[g.bskip_off + q] = v;
+        return;
+    }
+    int64_t h = e - 2 * g.Pb;
+    float *hd = dst + g.head_off;
+    if (h < (int64_t)Hc * 2 * S) {                                     // w_h1 (j, b * S + k)
+        const int j = (int)(h / (2 * S)), c = (int)(h % (2 * S));
+        hd[(int64_t)c * Hc + j] = v;
+        return;
+    }
+    h -= (int64_t)Hc * 2 * S;
+    hd[2LL * S * Hc + h] = v;                                          // b_h1, w_h2, b_h2
+}
+
 }  // namespace
+
+gwe_status fp32_repack_device(gwe_model *m, cudaStream_t st) {
+    const Dims &d = m->dims;
+    Fp32Weights &f = m->f32;
+    if (!f.buf.ptr || f.model_stride == 0) {
+        set_error("FP32 layout not prepared");
+        return GWE_ERR_UNSUPPORTED;
+    }
+    F32Geo g;
+    g.R = d.R;
+    g.S = d.S;
+    g.Hc = d.Hc;
+    g.L = d.L;
+    g.n_models = d.n_models;
+    g.P = d.P;
+    g.Pb = d.Pb;
+    g.Pl = d.Pl;
+    g.head_blob = d.head_off;
+    g.layer_stride = f.layer_stride;
+    g.conv_off = f.conv_off;
+    g.rs_off = f.rs_off;
+    g.bconv_off = f.bconv_off;
+    g.bres_off = f.bres_off;
+    g.bskip_off = f.bskip_off;
+    g.layers_off = round4(4 * d.R);
+    g.head_off = f.head_off;
+    g.model_stride = f.model_stride;
+    GWE_CUDA_TRY(cudaMemsetAsync(f.buf.ptr, 0, sizeof(float) * f.model_stride * d.n_models, st));
+    const int64_t n = d.P * d.n_models;
+    k_pack_fp32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->w32.as<float>(), g, f.buf.as<float>());
+    note_launch();
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
 
 gwe_status fp32_prepare(gwe_model *m, const float *hb) {
     const Dims &d = m->dims;

@@ -135,6 +135,9 @@ struct Segments {
 
 // fp32_path.cu
 gwe_status fp32_prepare(gwe_model *m, const float *host_blob);
+// the FP32 kernel layout from the device FP32 blobs m->w32 (asynchronous on st; fp32_prepare must
+// have run once for the handle)
+gwe_status fp32_repack_device(gwe_model *m, cudaStream_t st);
 // bwd_tc.cu: backward of one member with BF16 tensor-core GEMMs (FP32 accumulation)
 bool tc_backward_supported(const Dims &d);
 gwe_status tc_backward(gwe_model *m, void *&state, int model_index, const float *xH, const float *xL, int batch,
@@ -161,10 +164,16 @@ gwe_status debug_config(int drop, double wait_seconds);
 void set_cross_window_reuse(int enable);
 // f8: E4M3 convolutions, calibrated on synthetic unit-variance white noise until tc_calibrate runs
 gwe_status tc_prepare(gwe_model *m, const float *host_blob, bool f8);
+// rebuild the tensor-core images from the device FP32 blobs m->w32 (16-bit path: on the device,
+// asynchronous on st; FP8: on the host, synchronous)
+gwe_status tc_rebuild_from_device(gwe_model *m, cudaStream_t st);
 gwe_status tc_calibrate(gwe_model *m, const float *sH, const float *sL, int64_t n_samples, int window, int stride,
                         cudaStream_t st);
 gwe_status tc_set_amax(gwe_model *m, const float *host_amax);   // [n_models][2][L][R]
 gwe_status tc_get_amax(gwe_model *m, float *host_amax);
+// 16-bit path: layers l < n16 take FP16 conv operands, the rest BF16 (rebuilds the images)
+gwe_status tc_set_f16_layers(gwe_model *m, int n16);
+int tc_f16_layers(gwe_model *m);
 void tc_release(gwe_model *m);
 gwe_status tc_forward(gwe_model *m, const float *sH, const float *sL, const Segments &sg, int window, int stride,
                       const int32_t *slides, int n_slides, float *out, bool logits, cudaStream_t st);
@@ -184,6 +193,11 @@ gwe_status whiten_run(const float *x, int64_t n, double fs, int seg, float *out,
 gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,
                         int stride, float thr, double min_width, int64_t coinc, int flags, gwe_trigger *out,
                         int64_t cap, int64_t *n_out, cudaStream_t st);
+// threshold sweep over the segments (n_seg = 1: one series of seg_nw[0] windows): ensemble-trigger
+// counts per slide and threshold, optional per-model peak counts (host arrays, overwritten)
+gwe_status triggers_sweep(const float *prob, int n_models, int n_slides, const int64_t *seg_nw, int n_seg, int W,
+                          int stride, const float *thr, int n_thr, double min_width, int64_t coinc,
+                          int64_t *ens_counts, int64_t *model_counts, cudaStream_t st);
 // the same over the segments of a gwe_forward_segments output (segment g: seg_nw[g] windows);
 // out_seg (optional) receives each record's segment
 gwe_status triggers_run_segments(const float *prob, int n_models, int n_slides, const int64_t *seg_nw, int n_seg,

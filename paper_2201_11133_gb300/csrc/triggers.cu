@@ -712,11 +712,111 @@ __global__ void k_coinc(int64_t npk, const int64_t *p_idx, const int *p_ser, con
     ens[i] = ok ? 1 : 0;
 }
 
+// Threshold sweep (section "Statistical Analysis": the ROC and false-alarm curves come from
+// sweeping the height threshold over [0, 0.9998]).  A peak's prominence and width do not depend
+// on the threshold, so with the peaks found once at the lowest threshold (and the width cut
+// applied), model-0 peak p0 is an ensemble trigger at threshold thr iff h(p0) >= thr and some
+// candidate window [a, a + coinc] of k_coinc holds, for every other model, a peak of height
+// >= thr.  Its largest such threshold is
+//   T(p0) = min(h(p0), max over candidate windows a of min over models m >= 1 of
+//                      (largest height of model m's peaks in [a, a + coinc])),
+// (the candidate windows of the peaks above any threshold are among those of all the peaks, and
+// a window that serves at thr serves at every lower one), and it is a trigger at every
+// threshold <= T(p0).  Each peak adds one to the histogram bin of its value: the number of
+// thresholds <= value (thresholds ascending); count(thr_k) is then the sum of the bins above k.
+__device__ __forceinline__ double max_height_in(const int64_t *pk, const double *ph, int64_t lo_i, int64_t hi_i,
+                                                int64_t a, int64_t b) {
+    int64_t lo = lo_i, hi = hi_i;   // first peak >= a
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (pk[mid] < a) lo = mid + 1; else hi = mid;
+    }
+    double mx = -INFINITY;
+    for (int64_t q = lo; q < hi_i && pk[q] <= b; ++q) mx = fmax(mx, ph[q]);
+    return mx;
+}
+
+__device__ __forceinline__ int thr_bin(const double *thr, int K, double v) {
+    int lo = 0, hi = K;             // number of thresholds <= v
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (thr[mid] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// one thread per kept peak: model histogram bin of its height; model-0 peaks also the ensemble
+// histogram bin of T(p0).  hist_m [series][K + 1], hist_e [slide][K + 1]
+__global__ void k_sweep_hist(int64_t npk, const int64_t *p_idx, const int *p_ser, const double *p_h,
+                             const int64_t *start, int n_models, int64_t coinc, const double *thr, int K,
+                             unsigned long long *hist_m, unsigned long long *hist_e) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npk) return;
+    const int s = p_ser[i];
+    const int m = s % n_models;
+    const double h0 = p_h[i];
+    atomicAdd(&hist_m[(int64_t)s * (K + 1) + thr_bin(thr, K, h0)], 1ull);
+    if (m != 0) return;
+    const int64_t p0 = p_idx[i];
+    double best = -INFINITY;
+    for (int mc = -1; mc < n_models; ++mc) {
+        int64_t qlo = 0, qhi = 1;
+        if (mc >= 0) {
+            const int64_t b0 = start[s + mc], b1 = start[s + mc + 1];
+            int64_t lo = b0, hi = b1;   // peaks q of model mc with q in [p0, p0 + coinc]
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) / 2;
+                if (p_idx[mid] < p0) lo = mid + 1; else hi = mid;
+            }
+            qlo = lo;
+            qhi = b1;
+        }
+        for (int64_t q = qlo; q < qhi; ++q) {
+            int64_t a;
+            if (mc < 0) {
+                a = p0 - coinc;
+            } else {
+                if (p_idx[q] > p0 + coinc) break;
+                a = p_idx[q] - coinc;
+            }
+            double v = INFINITY;
+            for (int mm = 1; mm < n_models && v > best; ++mm)
+                v = fmin(v, max_height_in(p_idx, p_h, start[s + mm], start[s + mm + 1], a, a + coinc));
+            best = fmax(best, v);
+        }
+    }
+    const double T = fmin(h0, best);
+    atomicAdd(&hist_e[(int64_t)(s / n_models) * (K + 1) + thr_bin(thr, K, T)], 1ull);
+}
+
+// counts[row][k] = sum over bins b > k of hist[row][b]
+__global__ void k_sweep_suffix(const unsigned long long *hist, int rows, int K, long long *counts) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    unsigned long long acc = 0;
+    for (int k = K - 1; k >= 0; --k) {
+        acc += hist[(int64_t)r * (K + 1) + k + 1];
+        counts[(int64_t)r * K + k] = (long long)acc;
+    }
+}
+
 struct TrigWs {
     std::mutex mu;
     DevBuf stats_mx, stats_mn, stats_lo, stats_hi, sb_mx, sb_mn, sb_lo, sb_hi, longs, nlong, counts, offsets, cand_idx, cand_ser, keep, h, pr, wd, sel,
-        p_idx, p_ser, p_h, p_pr, p_wd, start, ens;
+        p_idx, p_ser, p_h, p_pr, p_wd, start, ens, sw_thr, sw_hist, sw_counts;
 };
+
+}  // namespace
+
+// a threshold sweep request of triggers_collect: thresholds ascending (host, FP64 values of FP32
+// thresholds), counts accumulated into the host arrays (per slide, and per slide and model)
+struct SweepReq {
+    std::vector<double> thr;
+    int64_t *ens_counts = nullptr;     // [n_slides][K]
+    int64_t *model_counts = nullptr;   // [n_slides][n_models][K] or NULL
+};
+
+namespace {
 TrigWs &trig_ws() {
     static TrigWs *w = new TrigWs();   // kept until process exit
     return *w;
@@ -729,9 +829,11 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 namespace {
 
 // all records of one segment's (slide, model) series, appended to recs
+// With sw != NULL (threshold sweep, thr = the lowest threshold) the kept peaks go to the sweep
+// histograms and their counts are added to sw's host arrays instead of records.
 gwe_status triggers_collect(const float *prob, int n_models, int n_slides, int64_t nw, int64_t series_nw, int W,
                             int stride, float thr, double min_width, int64_t coinc, int flags,
-                            std::vector<gwe_trigger> &recs, cudaStream_t st) {
+                            std::vector<gwe_trigger> &recs, cudaStream_t st, const SweepReq *sw = nullptr) {
     TrigWs &ws = trig_ws();
     std::lock_guard<std::mutex> lock(ws.mu);
     const int ns = n_slides > 0 ? n_slides : 1;
@@ -887,6 +989,38 @@ gwe_status triggers_collect(const float *prob, int n_models, int n_slides, int64
                                                                              ws.start.as<int64_t>());
                 note_launch();
             }
+            if (sw) {
+                const int K = (int)sw->thr.size();
+                const int64_t hm = (int64_t)n_series * (K + 1), he = (int64_t)ns * (K + 1);
+                GWE_CUDA_TRY(ws.sw_thr.ensure(K * sizeof(double)));
+                GWE_CUDA_TRY(ws.sw_hist.ensure((hm + he) * sizeof(unsigned long long)));
+                GWE_CUDA_TRY(ws.sw_counts.ensure((int64_t)(n_series + ns) * K * sizeof(long long)));
+                GWE_CUDA_TRY(cudaMemcpyAsync(ws.sw_thr.ptr, sw->thr.data(), K * sizeof(double), cudaMemcpyHostToDevice, st));
+                GWE_CUDA_TRY(cudaMemsetAsync(ws.sw_hist.ptr, 0, (hm + he) * sizeof(unsigned long long), st));
+                unsigned long long *hist_m = ws.sw_hist.as<unsigned long long>(), *hist_e = hist_m + hm;
+                long long *cnt = ws.sw_counts.as<long long>();
+                {
+                    ProfScope prof("k_sweep", st);
+                    k_sweep_hist<<<blocks_for(npk, 128), 128, 0, st>>>(npk, ws.p_idx.as<int64_t>(), ws.p_ser.as<int>(),
+                                                                       ws.p_h.as<double>(), ws.start.as<int64_t>(),
+                                                                       n_models, coinc, ws.sw_thr.as<double>(), K,
+                                                                       hist_m, hist_e);
+                    note_launch();
+                }
+                {
+                    ProfScope prof("k_sweep", st);
+                    k_sweep_suffix<<<blocks_for(n_series + ns, 128), 128, 0, st>>>(hist_m, n_series + ns, K, cnt);
+                    note_launch();
+                }
+                GWE_CUDA_TRY(cudaGetLastError());
+                std::vector<long long> hc((size_t)(n_series + ns) * K);
+                GWE_CUDA_TRY(cudaMemcpyAsync(hc.data(), cnt, hc.size() * sizeof(long long), cudaMemcpyDeviceToHost, st));
+                GWE_CUDA_TRY(cudaStreamSynchronize(st));
+                for (int64_t i = 0; i < (int64_t)ns * K; ++i) sw->ens_counts[i] += hc[(size_t)n_series * K + i];
+                if (sw->model_counts)
+                    for (int64_t i = 0; i < (int64_t)n_series * K; ++i) sw->model_counts[i] += hc[i];
+                return GWE_OK;
+            }
             {
                 ProfScope prof("k_coinc", st);
                 k_coinc<<<blocks_for(npk, 128), 128, 0, st>>>(npk, ws.p_idx.as<int64_t>(), ws.p_ser.as<int>(),
@@ -947,6 +1081,30 @@ gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t n
     gwe_status r = triggers_collect(prob, n_models, n_slides, nw, nw, W, stride, thr, min_width, coinc, flags, recs, st);
     if (r != GWE_OK) return r;
     return copy_out(recs, nullptr, out, nullptr, cap, n_out);
+}
+
+gwe_status triggers_sweep(const float *prob, int n_models, int n_slides, const int64_t *seg_nw, int n_seg, int W,
+                          int stride, const float *thr, int n_thr, double min_width, int64_t coinc,
+                          int64_t *ens_counts, int64_t *model_counts, cudaStream_t st) {
+    const int ns = n_slides > 0 ? n_slides : 1;
+    SweepReq sw;
+    sw.thr.resize(n_thr);
+    for (int k = 0; k < n_thr; ++k) sw.thr[k] = (double)thr[k];
+    sw.ens_counts = ens_counts;
+    sw.model_counts = model_counts;
+    std::fill(ens_counts, ens_counts + (int64_t)ns * n_thr, 0);
+    if (model_counts) std::fill(model_counts, model_counts + (int64_t)ns * n_models * n_thr, 0);
+    int64_t nw_all = 0;
+    for (int g = 0; g < n_seg; ++g) nw_all += seg_nw[g];
+    std::vector<gwe_trigger> none;
+    int64_t wo = 0;
+    for (int g = 0; g < n_seg; ++g) {
+        gwe_status r = triggers_collect(prob + wo * W, n_models, n_slides, seg_nw[g], nw_all, W, stride, thr[0],
+                                        min_width, coinc, 0, none, st, &sw);
+        if (r != GWE_OK) return r;
+        wo += seg_nw[g];
+    }
+    return GWE_OK;
 }
 
 gwe_status triggers_run_segments(const float *prob, int n_models, int n_slides, const int64_t *seg_nw, int n_seg,

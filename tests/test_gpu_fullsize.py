@@ -3,15 +3,15 @@ launch configuration the benchmark times (device whitening of the raw coloured
 strain, one persistent forward launch over all 7199 windows with cross-window
 reuse, device triggers), checked on outputs the oracle computes directly:
 
-* probabilities of sampled windows (first and last windows, windows at the
-  boundaries of the persistent kernel's per-CTA window ranges, where the reuse
-  carry restarts, and windows spread over the hour) against the FP64 network
-  on the same whitened inputs, within 1.5e-2: the BF16 rounding of the
-  convolution operands alone (an FP64 evaluation of the network with both
-  conv operands rounded to BF16 and everything else exact) reaches ~1e-2 on
-  windows of this workload, so the 1e-2 bound of the small-input tests is met
-  there with little margin (up to 1.03e-2 measured on one sampled window of
-  the hour);
+* probabilities of sampled windows (first and last windows, every window where
+  one of the persistent kernel's per-CTA window ranges starts (no carry), the
+  window after each (the first that takes layers over from its predecessor),
+  and windows spread over the hour) against the FP64 network on the same
+  whitened inputs, within the 1e-2 bound of the 16-bit tensor-core path (the
+  handle's default operand formats: FP16 for the convolutions of the first
+  third of the layers, BF16 for the rest; an FP64 evaluation with only those
+  roundings gives at most ~7.3e-3 on 32 windows of this workload, against
+  ~9.3e-3 with BF16 everywhere);
 * the trigger records of the whole hour against the oracle's peak finding and
   coincidence on the same probabilities (bit-exact);
 * 64 one-second time slides over the hour: sampled (offset, window) pairs
@@ -51,7 +51,7 @@ def _range_starts(n_jobs, grid):
     return [c * q + min(c, rm) for c in range(grid)]
 
 
-TOL = 1.5e-2
+TOL = 1e-2
 
 
 def test_hour_forward_sampled_windows(hour):
@@ -65,20 +65,24 @@ def test_hour_forward_sampled_windows(hour):
     sms = torch.cuda.get_device_properties(hour["dev"]).multi_processor_count
     starts = _range_starts(cfg["n_models"] * nw, min(sms, cfg["n_models"] * nw))
     worst = 0.0
+    assert gwe.gwe_model_f16_layers(m.handle) == 10
+    n_checked = 0
     for mi in range(cfg["n_models"]):
-        # windows of model mi where a CTA range starts (no carry) and the one after it (first reuse)
-        bnd = [j - mi * nw for j in starts if mi * nw <= j < (mi + 1) * nw][1:3]
+        # every window of model mi where a CTA range starts (no carry) and the one after it (first reuse)
+        bnd = [j - mi * nw for j in starts if mi * nw <= j < (mi + 1) * nw]
         ws = sorted({0, 1, nw // 2, nw - 2, nw - 1, *bnd, *[b + 1 for b in bnd if b + 1 < nw]})
+        assert len(ws) >= 40
+        n_checked += len(ws)
         xh = np.stack([hour["hw"][w * STRIDE:w * STRIDE + W] for w in ws])
         xl = np.stack([hour["lw"][w * STRIDE:w * STRIDE + W] for w in ws])
         ref = sigmoid(oracle.forward_windows(cfg, wb[mi], xh, xl))
         got = out[0, mi, ws].cpu().numpy().astype(np.float64)
         err = float(np.max(np.abs(got - ref)))
         worst = max(worst, err)
-        print(f"model {mi}: windows {ws}: max |dprob| {err:.2e}")
+        print(f"model {mi}: {len(ws)} windows: max |dprob| {err:.2e}")
         assert err <= TOL
     hour["prob"] = out
-    print(f"hour forward sampled max |dprob| {worst:.2e}")
+    print(f"hour forward: {n_checked} sampled windows, max |dprob| {worst:.2e}")
 
 
 def test_hour_triggers_bit_exact(hour):
