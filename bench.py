@@ -187,12 +187,28 @@ WELCH_SEG = 16384      # 4 s Welch segments
 
 
 def make_inputs(seed: int, minutes: float = 60.0):
-    """Coloured (unwhitened) two-detector strain with leading-order chirps, float32."""
+    """Coloured (unwhitened) two-detector strain with leading-order chirps, float32; with the injections'
+    (merger, network SNR, chirp mass)."""
     n = int(round(minutes * 60)) * FS
     n_inj = max(1, int(round(200 * minutes / 60.0)))
-    sh, sl, mergers = workload.coloured_stream(n, seed=seed, n_inj=n_inj, snr_range=(6.0, 20.0),
-                                               mc_range=(5.0, 30.0))
-    return sh, sl, mergers
+    sh, sl, mergers, params = workload.coloured_stream(n, seed=seed, n_inj=n_inj, snr_range=(6.0, 20.0),
+                                                       mc_range=(5.0, 30.0), with_params=True)
+    return sh, sl, mergers, params
+
+
+TRAINED = os.path.join(ROOT, "paper_2201_11133_gb300", "weights", "ensemble_trained_lite.npz")
+
+
+def ensemble_weights(cfg):
+    """(FP32 blobs [n_models, P], description): the trained-lite members when their file is present
+    (paper_2201_11133_gb300.train), else seeded random initialisation."""
+    if os.path.exists(TRAINED):
+        z = np.load(TRAINED)
+        w = z["weights"].astype(np.float32)
+        if w.shape == (cfg["n_models"], workload.param_count(cfg)):
+            steps = int(z["meta"][0]) if "meta" in z else -1
+            return w, f"trained-lite ({steps} steps per member, synthetic chirps)"
+    return workload.init_weights(cfg, seed=3000), "seeded random init"
 
 
 # ---------------------------------------------------------------------------
@@ -229,8 +245,8 @@ def run_reference(args):
     if rank != 0:
         return
     cfg = workload.config("ensemble")
-    wb = workload.init_weights(cfg, seed=3000)
-    sh, sl, _ = make_inputs(1000)
+    wb, _ = ensemble_weights(cfg)
+    sh, sl, _, _ = make_inputs(1000)
     import oracle
     oracle.build()
     n_win = args.ref_windows
@@ -472,6 +488,13 @@ def main():
     ap.add_argument("--train-batch", type=int, default=256,
                     help="time one training step (forward logits, BCE gradient, hand-written backward) of one "
                          "30-layer model on this many windows (0: skip)")
+    ap.add_argument("--thr", type=float, default=0.9,
+                    help="probability threshold of the triggers with trained members")
+    ap.add_argument("--sweep-thresholds", type=int, default=64,
+                    help="thresholds of the on-device ROC / false-alarm sweep over [0, 0.9998] (0: skip)")
+    ap.add_argument("--glitches", type=int, default=100,
+                    help="trained members: sine-Gaussian glitches (one detector each) injected into a copy of the "
+                         "hour, triggers near them counted per model and for the ensemble (0: skip)")
     ap.add_argument("--compare-minutes", type=float, default=6.0,
                     help="time the other precisions' forward steps too (FP8 on the whole workload, FP32 on "
                          "this many minutes of it); 0: skip")
@@ -481,6 +504,7 @@ def main():
 
     import torch
     import paper_2201_11133_gb300 as gwe
+    from paper_2201_11133_gb300 import evaluate as ev
     from paper_2201_11133_gb300 import multi
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -495,10 +519,11 @@ def main():
 
     gwe.build()
     cfg = workload.config("ensemble")
-    wb = workload.init_weights(cfg, seed=3000)
+    wb, weights_desc = ensemble_weights(cfg)
+    trained = weights_desc.startswith("trained")
     prec = PREC_NAMES[args.precision]
     model = gwe.Model(cfg, wb, prec)
-    sh, sl, mergers = make_inputs(1000 + 7 * rank, args.minutes)   # each rank its own hour (weak scaling)
+    sh, sl, mergers, inj_params = make_inputs(1000 + 7 * rank, args.minutes)   # each rank its own hour (weak scaling)
     n = sh.shape[0]
     nw = gwe.gwe_n_windows(n, WINDOW, STRIDE)
     H = torch.from_numpy(sh).to(dev)          # coloured (unwhitened) strain
@@ -509,12 +534,16 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    # trigger threshold: the 99.9th percentile of one forward's probabilities (fixed before timing)
+    # trigger threshold: args.thr for trained members; for random-init members the 99.9th percentile of
+    # one forward's probabilities (fixed before timing)
     gwe.gwe_whiten(H, n, float(FS), WELCH_SEG, Hw)
     gwe.gwe_whiten(L, n, float(FS), WELCH_SEG, Lw)
     model.forward(Hw, Lw, WINDOW, STRIDE, out=out)
     torch.cuda.synchronize()
-    thr = float(torch.quantile(out[0, 0, :, ::97].reshape(-1).float(), 0.999).item())
+    if trained:
+        thr = float(args.thr)
+    else:
+        thr = float(torch.quantile(out[0, 0, :, ::97].reshape(-1).float(), 0.999).item())
     min_width, coinc = 2048.0, 2048
 
     def step(h, l_):
@@ -618,7 +647,40 @@ def main():
         prof_sl = gwe.gwe_profile_read()
         gwe.gwe_profile_enable(False)
         t_sl = multi.max_over_ranks(sum(st_ms) / len(st_ms), dist, dev)
-        slides_res = {"offsets": k_sl, "ms_per_step": t_sl,
+        # on-device threshold sweep over the zero-lag and the 64 slid outputs (ROC / false-alarm curve)
+        if args.sweep_thresholds > 0:
+            thr_grid = np.linspace(0.0, 0.9998, args.sweep_thresholds).astype(np.float32)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bg, _ = gwe.gwe_trigger_sweep(out_sl, cfg["n_models"], k_sl, nw, WINDOW, STRIDE, thr_grid, min_width,
+                                          coinc, per_model=False, stream=stream)
+            t_sweep_bg = time.perf_counter() - t0
+            fg, fg_model = gwe.gwe_trigger_sweep(out, cfg["n_models"], 1, nw, WINDOW, STRIDE, thr_grid, min_width,
+                                                 coinc, stream=stream)
+            hours_bg = k_sl * strain_s / 3600.0
+            sweep_res = {"thresholds": [float(t) for t in thr_grid], "min_width": min_width, "coinc": coinc,
+                         "zero_lag_ensemble": [int(v) for v in fg[0]],
+                         "zero_lag_per_model": [[int(v) for v in row] for row in fg_model[0]],
+                         "background_ensemble": [int(v) for v in bg.sum(0)],
+                         "background_hours": hours_bg,
+                         "far_per_hour": [float(v) / hours_bg for v in bg.sum(0)],
+                         "seconds_64_slides": t_sweep_bg,
+                         "note": "one pass over the 64 slid series per threshold vector (peaks found once at the "
+                                 "lowest threshold, each model-0 peak's largest threshold as an ensemble trigger)"}
+            if trained:
+                # recovered injections at a few thresholds of the sweep grid (zero lag)
+                rec_at = {}
+                for tq in (0.5, 0.9, 0.99):
+                    r_t = gwe.gwe_triggers(out, cfg["n_models"], 1, nw, WINDOW, STRIDE, tq, min_width, coinc,
+                                           flags=0, stream=stream)
+                    hit = ev.recovered(r_t["index"][r_t["model"] == -1], [p[0] for p in inj_params])
+                    bg_t = gwe.gwe_trigger_sweep(out_sl, cfg["n_models"], k_sl, nw, WINDOW, STRIDE,
+                                                 np.array([tq], dtype=np.float32), min_width, coinc,
+                                                 per_model=False, stream=stream)[0].sum()
+                    rec_at[f"{tq:g}"] = {"recovered_fraction": float(hit.mean()),
+                                         "far_per_hour": float(bg_t) / hours_bg}
+                sweep_res["recovery_at"] = rec_at
+        slides_res = {"offsets": k_sl, "ms_per_step": t_sl, "threshold_sweep": sweep_res if args.sweep_thresholds > 0 else None,
                       "physical_strain_s_per_s": world * strain_s / (t_sl / 1000.0),
                       "effective_strain_s_per_s": world * strain_s * k_sl / (t_sl / 1000.0),
                       "ensemble_triggers": int(np.sum(recs["model"] == -1)) if len(recs) else 0,
@@ -627,6 +689,51 @@ def main():
                       "note": "branch pass once per window (projections of the head's first conv kept in FP16), "
                               "slide heads per offset, triggers on every (offset, model) series"}
         del out_sl
+
+    # sensitivity of the trained ensemble (the last timed step's zero-lag triggers at thr): injections
+    # recovered per network-SNR bin, and the false-alarm rate from the slid background
+    sensitivity = None
+    if trained:
+        r0 = gwe.gwe_triggers(out, cfg["n_models"], 1, nw, WINDOW, STRIDE, thr, min_width, coinc, flags=0,
+                              stream=stream)
+        ens0 = r0["index"][r0["model"] == -1]
+        rows = ev.recovery_by_snr(ens0, inj_params)
+        sensitivity = {"threshold": thr, "min_width": min_width, "coinc": coinc,
+                       "ensemble_triggers": int(len(ens0)),
+                       "recovered_by_snr": [{"snr": [lo, hi], "injections": k, "recovered": h}
+                                            for lo, hi, k, h in rows],
+                       "recovered_total": int(sum(r[3] for r in rows)), "injections": len(inj_params),
+                       "false_alarms_per_hour": (ev.far_per_hour(slides_res["ensemble_triggers"], args.slides,
+                                                                 strain_s) if slides_res else None),
+                       "recovery_window_s": [-4.0, 0.5]}
+
+    # glitches: sine-Gaussians in one detector each, whitened with the mean and the median PSD; triggers
+    # within 1 s of a glitch counted per model and for the ensemble (coincidence of the members)
+    glitches = None
+    if trained and args.glitches > 0:
+        gh, gl = sh.copy(), sl.copy()
+        glist = workload.add_glitches(gh, gl, args.glitches, seed=4242 + rank, snr_range=(10.0, 60.0),
+                                      avoid=mergers, guard=8 * FS)
+        cent = np.array(sorted(g[0] for g in glist), dtype=np.int64)
+        Hg, Lg = torch.from_numpy(gh).to(dev), torch.from_numpy(gl).to(dev)
+        glitches = {"n": len(glist), "snr": [10.0, 60.0], "f0_hz": [30.0, 500.0], "q": [3.0, 30.0]}
+        for avg_name, avg in (("mean_psd", gwe.GWE_PSD_MEAN), ("median_psd", gwe.GWE_PSD_MEDIAN)):
+            gwe.gwe_whiten_ex(Hg, n, float(FS), WELCH_SEG, Hw, psd_average=avg, stream=stream)
+            gwe.gwe_whiten_ex(Lg, n, float(FS), WELCH_SEG, Lw, psd_average=avg, stream=stream)
+            gwe.gwe_forward(model.handle, Hw, Lw, n, WINDOW, STRIDE, None, out, stream)
+            rg = gwe.gwe_triggers(out, cfg["n_models"], 1, nw, WINDOW, STRIDE, thr, min_width, coinc,
+                                  flags=gwe.GWE_TRIG_PER_MODEL, stream=stream)
+            near = lambda idx: int(ev.recovered(idx, cent, before=FS, after=FS).sum())
+            glitches[avg_name] = {
+                "glitches_with_model_peak": [near(rg["index"][rg["model"] == mi]) for mi in range(cfg["n_models"])],
+                "glitches_with_ensemble_trigger": near(rg["index"][rg["model"] == -1]),
+                "injections_recovered": int(ev.recovered(rg["index"][rg["model"] == -1],
+                                                         [p[0] for p in inj_params]).sum())}
+        del Hg, Lg
+        # the later legs read the clean whitened hour
+        gwe.gwe_whiten(H, n, float(FS), WELCH_SEG, Hw, stream=stream)
+        gwe.gwe_whiten(L, n, float(FS), WELCH_SEG, Lw, stream=stream)
+        torch.cuda.synchronize()
 
     # many uneven science segments x 64 offsets, FP8, through one autotuned CUDA-graph plan
     batched = None
@@ -744,13 +851,16 @@ def main():
                    "stride": STRIDE, "n_windows": nw, "models": cfg["n_models"], "layers": workload.n_layers(cfg),
                    "r_ch": cfg["r_ch"], "s_ch": cfg["s_ch"], "head_ch": cfg["head_ch"],
                    "precision": args.precision, "injections": len(mergers), "trigger_thr": thr,
-                   "l2": "flushed before every timed step (256 MiB write)", "triggers_last_step": n_trig},
+                   "l2": "flushed before every timed step (256 MiB write)", "triggers_last_step": n_trig,
+                   "weights": weights_desc},
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "time_slides": slides_res,
+        "sensitivity": sensitivity,
+        "glitches": glitches,
         "batched_slides": batched,
         "streaming": streaming,
         "training": train,

@@ -539,28 +539,50 @@ gwe_status gwe_search_run(gwe_search *search, const void *strain_H, const void *
 /* Release a search. */
 void gwe_search_destroy(gwe_search *search);
 
+/* PSD averages of the whitening front end. */
+#define GWE_PSD_MEAN 0     /* mean of |X|^2 over the Welch segments */
+#define GWE_PSD_MEDIAN 1   /* median over the segments, divided by the median's bias */
+
+/* Options of gwe_whiten_ex. */
+typedef struct {
+    int psd_average;       /* GWE_PSD_MEAN or GWE_PSD_MEDIAN */
+    double tukey_alpha;    /* taper fraction in [0, 1] of a Tukey window on the strain before its
+                              transform (0: none) */
+    double f_low;          /* the whitened spectrum is zero below this frequency, Hz (>= 0; default 15) */
+} gwe_whiten_options;
+
 /*
  * Whitening front end (paper section "Materials and Methods", paragraph "Data
  * preparation": the strain is whitened with power spectral densities
  * estimated from the data, then normalised to unit standard deviation).
  * Welch PSD: segments of seg_len samples at 50 % overlap, each minus its mean,
- * periodic Hann window, one-sided density, averaged over segments; the segment
- * transforms are FP32, the accumulation of |X|^2 and the PSD are FP64.  The
- * strain spectrum (FP32 transform of all n samples) is divided by
+ * periodic Hann window, one-sided density; |X|^2 of the segments averaged by
+ * the mean or (GWE_PSD_MEDIAN, robust against loud short glitches such as the
+ * ones the paper's section "Event Detection" discusses) by the median over
+ * segments divided by 1 - 1/2 + 1/3 - ... (the bias of the median of
+ * exponentially distributed values; over the largest odd number of terms <= the
+ * number of segments).  The segment transforms are FP32; FP64 is used only for
+ * |X|^2 and its accumulation or selection over segments.  The strain (times a
+ * Tukey window when tukey_alpha > 0) is transformed (FP32), divided by
  * sqrt(fs * PSD / 2), the PSD interpolated linearly onto the data's frequency
- * grid, zeroed below 15 Hz, transformed back and scaled to unit standard
- * deviation (FP64 sums).  The FFTs are cuFFT calls; everything else is this
- * library's kernels.
+ * grid, zeroed below f_low, transformed back and scaled to unit standard
+ * deviation (FP32 compensated sums).  The FFTs are cuFFT calls; everything
+ * else is this library's kernels.
  *   strain   device FP32 [n] (one detector; not modified).
  *   n        samples; >= seg_len.
  *   fs       sample rate in Hz (> 0).
  *   seg_len  Welch segment length, a power of two >= 16 (16384 = 4 s at 4096 Hz).
- *   flags    0.
+ *   flags    (gwe_whiten) 0, or GWE_PSD_MEDIAN for the median average; no taper,
+ *            f_low = 15 Hz.
+ *   options  (gwe_whiten_ex) as above.
  *   out      device FP32 [n], whitened strain; must not alias strain.
  * Asynchronous on `stream`; plans and work buffers are cached in the library
- * (one whitening at a time per process).  GWE_ERR_ARG for invalid arguments.
+ * (one whitening at a time per process).  GWE_ERR_ARG for invalid arguments;
+ * GWE_ERR_UNSUPPORTED for a median over more than 16384 segments.
  */
 gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream);
+gwe_status gwe_whiten_ex(const float *strain, int64_t n, double fs, int seg_len, const gwe_whiten_options *options,
+                         float *out, void *stream);
 
 /*
  * Per-kernel device timing.  gwe_profile_enable(1) clears the accumulators and

@@ -22,7 +22,7 @@ __all__ = [
     "gwe_param_count", "gwe_n_windows", "gwe_model_create", "gwe_model_set_weights", "gwe_model_set_weights_device", "gwe_init_weights",
     "gwe_model_init_random", "gwe_philox4x64_10", "gwe_model_set_f16_layers", "gwe_model_f16_layers", "gwe_model_calibrate", "gwe_model_set_fp8_amax", "gwe_model_get_fp8_amax",
     "gwe_model_destroy",
-    "gwe_trigger_sweep", "gwe_trigger_sweep_segments", "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_last_error",
+    "gwe_trigger_sweep", "gwe_trigger_sweep_segments", "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_whiten_ex", "GWE_PSD_MEAN", "GWE_PSD_MEDIAN", "gwe_last_error",
     "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static",
     "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE",
     "gwe_search_create", "gwe_search_run", "gwe_search_destroy", "GWE_INPUT_F32", "GWE_INPUT_F16", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
@@ -32,6 +32,7 @@ GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
 GWE_TRIG_PER_MODEL = 1
 GWE_PLAN_AUTOTUNE = 1
 GWE_INPUT_F32, GWE_INPUT_F16 = 0, 1
+GWE_PSD_MEAN, GWE_PSD_MEDIAN = 0, 1
 _STATUS = {0: "GWE_OK", 1: "GWE_ERR_ARG", 2: "GWE_ERR_CUDA", 3: "GWE_ERR_OOM", 4: "GWE_ERR_TIMEOUT",
            5: "GWE_ERR_UNSUPPORTED", 6: "GWE_ERR_CAPACITY"}
 
@@ -107,6 +108,7 @@ def load():
             "gwe_backward": (I, [P, I, P, P, I, I, P, P, P, P, P]),
             "gwe_triggers": (I, [P, I, I, I64, I, I, F, D, I64, I, P, I64, P, P]),
             "gwe_whiten": (I, [P, I64, D, I, I, P, P]),
+            "gwe_whiten_ex": (I, [P, I64, D, I, P, P, P]),
             "gwe_trigger_sweep": (I, [P, I, I, I64, I, I, P, I, D, I64, P, P, P]),
             "gwe_trigger_sweep_segments": (I, [P, I, I, P, I, I, I, P, I, D, I64, P, P, P]),
             "gwe_sync": (I, [P, P]),
@@ -481,6 +483,18 @@ def gwe_sync(model: int, stream=None) -> None:
 def gwe_whiten(strain, n: int, fs: float, seg_len: int, out, flags: int = 0, stream=None) -> None:
     _check(load().gwe_whiten(_dptr(strain), int(n), float(fs), int(seg_len), int(flags), _dptr(out),
                              _stream(stream)), "gwe_whiten")
+
+
+class _WhitenOptions(ctypes.Structure):
+    _fields_ = [("psd_average", ctypes.c_int), ("tukey_alpha", ctypes.c_double), ("f_low", ctypes.c_double)]
+
+
+def gwe_whiten_ex(strain, n: int, fs: float, seg_len: int, out, psd_average: int = GWE_PSD_MEAN,
+                  tukey_alpha: float = 0.0, f_low: float = 15.0, stream=None) -> None:
+    """Whitening with options: mean or median Welch PSD, Tukey taper, low-frequency cut."""
+    o = _WhitenOptions(int(psd_average), float(tukey_alpha), float(f_low))
+    _check(load().gwe_whiten_ex(_dptr(strain), int(n), float(fs), int(seg_len), ctypes.byref(o), _dptr(out),
+                                _stream(stream)), "gwe_whiten_ex")
 
 
 def gwe_profile_enable(on: bool = True) -> None:

@@ -502,15 +502,26 @@ gwe_status gwe_debug_config(int drop, double wait_seconds) {
     return debug_config(drop, wait_seconds);
 }
 
-gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream) {
+gwe_status gwe_whiten_ex(const float *strain, int64_t n, double fs, int seg_len, const gwe_whiten_options *opt,
+                         float *out, void *stream) {
     clear_error();
-    GWE_ARG_CHECK(strain != nullptr && out != nullptr, "NULL buffer");
+    GWE_ARG_CHECK(strain != nullptr && out != nullptr && opt != nullptr, "NULL argument");
     GWE_ARG_CHECK(out != strain, "out must not alias strain");
     GWE_ARG_CHECK(fs > 0.0, "fs must be positive");
     GWE_ARG_CHECK(seg_len >= 16 && (seg_len & (seg_len - 1)) == 0, "seg_len must be a power of two >= 16");
     GWE_ARG_CHECK(n >= seg_len, "n_samples < seg_len");
-    GWE_ARG_CHECK(flags == 0, "flags must be 0");
-    return whiten_run(strain, n, fs, seg_len, out, as_stream(stream));
+    GWE_ARG_CHECK(opt->psd_average == GWE_PSD_MEAN || opt->psd_average == GWE_PSD_MEDIAN, "unknown psd_average");
+    GWE_ARG_CHECK(opt->tukey_alpha >= 0.0 && opt->tukey_alpha <= 1.0, "tukey_alpha must lie in [0, 1]");
+    GWE_ARG_CHECK(opt->f_low >= 0.0 && opt->f_low < fs / 2.0, "f_low must lie in [0, fs / 2)");
+    return whiten_run(strain, n, fs, seg_len, *opt, out, as_stream(stream));
+}
+
+gwe_status gwe_whiten(const float *strain, int64_t n, double fs, int seg_len, int flags, float *out, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(flags == 0 || flags == GWE_PSD_MEDIAN, "flags must be 0 or GWE_PSD_MEDIAN");
+    gwe_whiten_options o = whiten_defaults();
+    o.psd_average = flags;
+    return gwe_whiten_ex(strain, n, fs, seg_len, &o, out, stream);
 }
 
 }  // extern "C"

@@ -187,7 +187,16 @@ gwe_status tc_forward_save(gwe_model *m, int mi, const float *xH, const float *x
                            float *save_x, float *save_skip, cudaStream_t st);
 
 // whiten.cu: Welch PSD (FP64 accumulation) and spectral whitening of one detector's strain
-gwe_status whiten_run(const float *x, int64_t n, double fs, int seg, float *out, cudaStream_t st);
+gwe_status whiten_run(const float *x, int64_t n, double fs, int seg, const gwe_whiten_options &opt, float *out,
+                      cudaStream_t st);
+// the defaults of gwe_whiten: mean PSD, no taper, f_low 15 Hz
+inline gwe_whiten_options whiten_defaults() {
+    gwe_whiten_options o;
+    o.psd_average = GWE_PSD_MEAN;
+    o.tukey_alpha = 0.0;
+    o.f_low = 15.0;
+    return o;
+}
 
 // triggers.cu
 gwe_status triggers_run(const float *prob, int n_models, int n_slides, int64_t n_windows, int window,

@@ -151,7 +151,8 @@ gwe_status run(SearchImpl &S, const void *sH, const void *sL, int64_t n, int hos
         }
         if (host_input) GWE_CUDA_TRY(cudaEventRecord(S.consumed[b], st));
         for (int det = 0; det < 2; ++det) {
-            gwe_status r = whiten_run(S.x[det].as<float>(), span, c.fs, c.welch_seg, S.xw[det].as<float>(), st);
+            gwe_status r = whiten_run(S.x[det].as<float>(), span, c.fs, c.welch_seg, whiten_defaults(),
+                                          S.xw[det].as<float>(), st);
             if (r != GWE_OK) return r;
         }
         // ensemble forward over the span's windows

@@ -125,3 +125,147 @@ def test_tc_backward_training_steps_lower_the_loss():
         losses.append(float(loss.item()))
     assert losses[-1] < losses[0], losses
     m.close()
+
+
+def _smooth_net(cfg, seed):
+    """Weights on which no ReLU of the network can change state: the skip and head weights are
+    scaled by 0.1 (a valid network with small skip terms), every skip term W_skip z + b_skip is
+    positive (|z| < 1 and b_skip[o] = 0.1 + sum_i |W_skip[o, i]|), so the skip sums h are positive
+    and bounded by h_max, and the head's u = W_h1 h + b_h1 is positive
+    (b_h1[j] = 0.1 + h_max sum_k |W_h1[j, k]|).  The network is then smooth in its weights and
+    inputs, and gradients are comparable entry by entry."""
+    wb = workload.init_weights(cfg, seed=seed, bias_std=0.1)[0].astype(np.float64)
+    off = workload.param_offsets(cfg)
+    L = int(cfg["stacks"]) * int(cfg["layers_per_stack"])
+    h_max = 0.0
+    for br in ("H", "L"):
+        tot = 0.0
+        for l in range(L):
+            o, sh = off[f"{br}.{l}.w_skip"]
+            n = int(np.prod(sh))
+            wb[o:o + n] *= 0.1
+            ws = wb[o:o + n].reshape(sh)
+            ob_, _ = off[f"{br}.{l}.b_skip"]
+            b = 0.1 + np.abs(ws).sum(1)
+            wb[ob_:ob_ + b.size] = b
+            tot += float((np.abs(ws).sum(1) + b).max())
+        h_max = max(h_max, tot)
+    o, sh = off["w_h1"]
+    n = int(np.prod(sh))
+    wb[o:o + n] *= 0.1
+    w1 = wb[o:o + n].reshape(sh)
+    ob_, _ = off["b_h1"]
+    wb[ob_:ob_ + sh[0]] = 0.1 + h_max * np.abs(w1).sum(1)
+    return wb.astype(np.float32)[None, :]
+
+
+def _smooth_setup(seed_w, seed_x):
+    cfg = dict(workload.config("small", n_models=1), stacks=1, layers_per_stack=3)
+    wb = _smooth_net(cfg, seed_w)
+    B, W = 2, 256
+    rng = np.random.default_rng(seed_x)
+    xh = rng.standard_normal((B, W)).astype(np.float32)
+    xl = rng.standard_normal((B, W)).astype(np.float32)
+    c = (rng.standard_normal((B, W)) / (B * W)).astype(np.float32)
+    return cfg, wb, xh, xl, c, rng
+
+
+def _handle_grad(cfg, wb, xh, xl, c, n16):
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    dev = require_gpu()
+    m = gwe.Model(cfg, wb, gwe.GWE_BF16)
+    gwe.gwe_model_set_f16_layers(m.handle, n16)
+    B, W = xh.shape
+    P = gwe.gwe_param_count(cfg)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    gw = torch.empty(P, device=dev)
+    gh = torch.empty((B, W), device=dev)
+    gl = torch.empty((B, W), device=dev)
+    gwe.gwe_backward(m.handle, 0, t(xh), t(xl), B, W, t(c), gw, gh, gl)
+    m.sync()
+    return m, tuple(a.cpu().numpy().astype(np.float64) for a in (gw, gh, gl))
+
+
+def test_tc_backward_elementwise_on_smooth_net():
+    """Entry by entry against the BF16 reading of the backward (R19), on a 3-layer network with no
+    ReLU state changes; tolerance 1e-2 of the largest entry of each parameter tensor (and of each
+    strain gradient), which covers BF16 operands that the kernels and the FP64 reading round to
+    neighbouring values from inputs that differ at the 1e-7 level (FP32 vs FP64 accumulation)."""
+    from oracle import bf16_backward as ob
+    cfg, wb, xh, xl, c, _ = _smooth_setup(3500, 6)
+    m, (gw, gh, gl) = _handle_grad(cfg, wb, xh, xl, c, 0)   # the reading rounds every conv operand to BF16
+    m.close()
+    qw, qh, ql = ob.backward(cfg, workload.param_offsets(cfg), wb[0], xh, xl, c)
+    worst = 0.0
+    for name, (o, sh) in workload.param_offsets(cfg).items():
+        n = int(np.prod(sh))
+        ref = qw[o:o + n]
+        scale = max(float(np.max(np.abs(ref))), 1e-30)
+        e = float(np.max(np.abs(gw[o:o + n] - ref))) / scale
+        worst = max(worst, e)
+        assert e <= 1e-2, (name, e)
+    for got, ref, what in ((gh, qh, "strain_H"), (gl, ql, "strain_L")):
+        e = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        print(f"smooth net {what}: max |kernels - reading| / max |reading| {e:.2e}")
+        assert e <= 1e-2, (what, e)
+    print(f"smooth net weights: worst per-tensor max |kernels - reading| / max |reading| {worst:.2e}")
+
+
+def test_tc_backward_against_central_differences_of_exact_forward():
+    """The tensor-core gradient against central differences of the FP64 forward (the oracle) along
+    random directions over every parameter: within 1e-2 relative (the BF16 rounding of the
+    backward's operands)."""
+    cfg, wb, xh, xl, c, rng = _smooth_setup(3600, 7)
+    m, (g, _, _) = _handle_grad(cfg, wb, xh, xl, c, 0)
+    m.close()
+    w = wb[0].astype(np.float64)
+    L = lambda wv: float(np.sum(oracle.forward_windows(cfg, wv, xh, xl) * c))
+    for trial in range(3):
+        v = rng.standard_normal(w.size)
+        v *= np.abs(w).max() / np.abs(v).max()
+        h = 1e-5
+        fd = (L(w + h * v) - L(w - h * v)) / (2 * h)
+        an = float(np.dot(g, v))
+        rel = abs(fd - an) / abs(fd)
+        print(f"central differences of the FP64 forward, trial {trial}: fd {fd:.6e} tensor-core {an:.6e} rel {rel:.2e}")
+        assert rel <= 1e-2
+
+
+def test_tc_backward_central_differences_of_handle_forward():
+    """The handle's gradient against central differences of its own tensor-core forward: along the
+    head's FP32 parameters (b_h1, w_h2, b_h2: everything after the last 16-bit rounding, so the
+    differences are exact up to FP32) within 1e-3, and along every parameter with a step large
+    against the forward's FP16 rounding (n16 = L: all conv operands FP16) within 3e-2."""
+    import torch
+    cfg, wb, xh, xl, c, rng = _smooth_setup(3700, 8)
+    dev = require_gpu()
+    off = workload.param_offsets(cfg)
+    L_ = int(cfg["stacks"]) * int(cfg["layers_per_stack"])
+    m, (g, _, _) = _handle_grad(cfg, wb, xh, xl, c, L_)
+    xt, lt = torch.from_numpy(xh).to(dev), torch.from_numpy(xl).to(dev)
+    ct = torch.from_numpy(c).to(dev).double()
+    w0 = torch.from_numpy(wb[0]).to(dev)
+
+    def loss(wv):
+        m.set_weights_device(wv)
+        lg = m.logits(xt, lt)[0]
+        m.sync()
+        return float((lg.double() * ct).sum().item())
+
+    P = w0.numel()
+    for tag, names, h, tol in (("head", ["b_h1", "w_h2", "b_h2"], 1e-2, 1e-3),
+                               ("all", list(off), 2e-2, 3e-2)):
+        v = np.zeros(P)
+        for n in names:
+            o, sh = off[n]
+            k = int(np.prod(sh))
+            v[o:o + k] = rng.standard_normal(k) * max(float(np.abs(wb[0][o:o + k]).max()), 1e-3)
+        v /= np.abs(v).max()
+        vt = torch.from_numpy(v.astype(np.float32)).to(dev)
+        fd = (loss(w0 + h * vt) - loss(w0 - h * vt)) / (2 * h)
+        an = float(np.dot(g, v))
+        rel = abs(fd - an) / max(abs(an), 1e-30)
+        print(f"central differences of the handle forward ({tag}): fd {fd:.6e} analytic {an:.6e} rel {rel:.2e}")
+        assert rel <= tol, (tag, fd, an)
+    m.close()

@@ -5,8 +5,14 @@ through the C-ABI.
 Parity is checked against the oracle's FP8 reading (the same E4M3
 quantisation, every other step exact in FP64) with the activation maxima set
 from the oracle's own calibration, so that both sides quantise with the same
-scales.  The error against exact arithmetic is printed: it is the format's
-(3 mantissa bits), as the reading shows, not the kernel's."""
+scales: entry by entry at depth one.  Deeper, the kernel and the reading round
+some values that lie within ~1e-7 of an E4M3 rounding midpoint to neighbouring
+codes (2^-3 apart), and from there they carry independent quantisation noise of
+the same size; every output is then checked entry by entry against exact
+arithmetic, within 1.5 times the largest error of the reading itself (the
+format's error: 3 mantissa bits per operand).  That error exceeds the 3e-2
+target on these random-init networks (about 3e-2 at 8 layers, 0.1 at 30), which
+is the format's property, not the kernel's."""
 import numpy as np
 import pytest
 
@@ -20,9 +26,8 @@ pytestmark = pytest.mark.gpu
 # gate/projections that the BF16 path also has, the two sides round a value that lies within about
 # 1e-7 (relative) of an E4M3 rounding midpoint to neighbouring codes, which is rare at depth one.
 TOL_IMPL_1LAYER = 1e-3
-# Deeper, those flips feed through the residual stream and the two sides become independent
-# quantisation-noise draws of the same size: the statistics of their errors must agree.
-STAT_RATIO = (0.6, 1.6)
+# Deeper: |gpu - exact| <= FORMAT_FACTOR * max |reading - exact|, entry by entry.
+FORMAT_FACTOR = 1.5
 
 
 def _model(cfg, wb):
@@ -62,18 +67,16 @@ def test_fp8_one_layer_against_fp8_reading():
         assert e <= TOL_IMPL_1LAYER
 
 
-def _stat_check(tag, got, q8, exact):
-    """The GPU path's error against exact arithmetic has the size of the FP8 reading's."""
+def _format_check(tag, got, q8, exact):
+    """Entry by entry: the GPU path is within FORMAT_FACTOR x the FP8 format's own largest error."""
     g, r = np.abs(got - exact), np.abs(q8 - exact)
-    ratio_mean, ratio_p99 = g.mean() / r.mean(), np.quantile(g, 0.99) / np.quantile(r, 0.99)
-    print(f"{tag}: mean|gpu-exact| {g.mean():.4g} vs mean|reading-exact| {r.mean():.4g} (x{ratio_mean:.2f}); "
-          f"p99 {np.quantile(g, 0.99):.4g} vs {np.quantile(r, 0.99):.4g} (x{ratio_p99:.2f}); "
-          f"max {g.max():.4g} vs {r.max():.4g}; max|gpu-reading| {np.max(np.abs(got - q8)):.4g}")
-    assert STAT_RATIO[0] <= ratio_mean <= STAT_RATIO[1]
-    assert STAT_RATIO[0] <= ratio_p99 <= STAT_RATIO[1]
+    bound = FORMAT_FACTOR * float(r.max())
+    print(f"{tag}: max|gpu-exact| {g.max():.4g}, max|reading-exact| {r.max():.4g} (bound {bound:.4g}); "
+          f"mean {g.mean():.4g} vs {r.mean():.4g}; max|gpu-reading| {np.max(np.abs(got - q8)):.4g}")
+    assert np.all(g <= bound)
 
 
-def test_fp8_small_batch_error_statistics():
+def test_fp8_small_batch_elementwise():
     import torch
     dev = require_gpu()
     cfg = workload.config("small")
@@ -87,10 +90,10 @@ def test_fp8_small_batch_error_statistics():
     got = sigmoid(lg.cpu().numpy()[0].astype(np.float64))
     q8 = sigmoid(oracle.forward_windows_q8(cfg, wb[0], amax[0].astype(np.float64), xh, xl))
     exact = sigmoid(oracle.forward_windows(cfg, wb[0], xh, xl))
-    _stat_check("fp8 small (8 layers)", got, q8, exact)
+    _format_check("fp8 small (8 layers)", got, q8, exact)
 
 
-def test_fp8_thirty_layer_error_statistics():
+def test_fp8_thirty_layer_elementwise():
     import torch
     dev = require_gpu()
     cfg = workload.config("ensemble")
@@ -109,7 +112,7 @@ def test_fp8_thirty_layer_error_statistics():
     q8 = np.stack([sigmoid(oracle.forward_windows_q8(cfg, wb[k], amax[k].astype(np.float64), xh, xl))
                    for k in range(cfg["n_models"])])
     exact = np.stack([sigmoid(oracle.forward_windows(cfg, wb[k], xh, xl)) for k in range(cfg["n_models"])])
-    _stat_check("fp8 30-layer ensemble", got, q8, exact)
+    _format_check("fp8 30-layer ensemble", got, q8, exact)
 
 
 def test_fp8_time_slides_match_explicit_pairs():

@@ -1,0 +1,107 @@
+"""The trained-lite ensemble (paper_2201_11133_gb300.train: 4 members trained on
+synthetic chirps with the library's forward and backward kernels): on a
+held-out stream (white noise with whitened chirps, seeds unseen in training)
+the device's peaks and ensemble triggers, from the device's probabilities,
+agree with the oracle's, from its FP64 probabilities under the same weights,
+at the paper's width cut (0.5 s) -- the agreement reading of
+test_gpu_trigger_agreement (two-sided, solid triggers of either side found by
+the other) -- and the members detect the loud injections."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WEIGHTS = os.path.join(ROOT, "paper_2201_11133_gb300", "weights", "ensemble_trained_lite.npz")
+W, STRIDE, COINC, MW = 4096, 2048, 2048, 2048.0
+TOL = 1e-2
+RADIUS = 256
+
+
+def _pairs(a, b):
+    used = np.zeros(len(b), dtype=bool)
+    hits = 0
+    for x in np.sort(a):
+        j = np.searchsorted(b, x - RADIUS)
+        while j < len(b) and b[j] <= x + RADIUS:
+            if not used[j]:
+                used[j] = True
+                hits += 1
+                break
+            j += 1
+    return hits
+
+
+def _solid(h, pr, wd, thr):
+    return (np.abs(h - thr) > TOL) & (pr >= 0.05) & (np.abs(wd - MW) > 0.01 * MW)
+
+
+@pytest.fixture(scope="module")
+def held_out():
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    if not os.path.exists(WEIGHTS):
+        pytest.skip("trained weights not present")
+    dev = require_gpu()
+    cfg = workload.config("ensemble")
+    wb = np.load(WEIGHTS)["weights"].astype(np.float32)
+    n = 40 * 4096
+    sh, sl, mergers = workload.stream(n, seed=9091, n_inj=4, snr_range=(12.0, 20.0), mc_range=(5.0, 30.0),
+                                      min_gap=6 * 4096)
+    ref = oracle.forward_stream(cfg, wb, sh, sl, W, STRIDE).astype(np.float32)
+    m = gwe.Model(cfg, wb, gwe.GWE_BF16)
+    prob = m.forward(torch.from_numpy(sh).to(dev), torch.from_numpy(sl).to(dev), W, STRIDE)
+    m.sync()
+    m.close()
+    return dict(cfg=cfg, ref=ref, prob=prob, mergers=mergers)
+
+
+@pytest.mark.parametrize("thr", [0.5, 0.9])
+def test_trained_ensemble_triggers_agree_with_oracle(held_out, thr):
+    import paper_2201_11133_gb300 as gwe
+    cfg, ref, prob = held_out["cfg"], held_out["ref"], held_out["prob"]
+    nm = int(cfg["n_models"])
+    err = float(np.max(np.abs(prob.cpu().numpy() - ref)))
+    print(f"trained ensemble, held-out stream: max |dprob| {err:.2e}")
+    assert err <= TOL
+    per_model, ens = oracle.triggers(ref, W, STRIDE, thr, MW, COINC)
+    recs = gwe.gwe_triggers(prob, nm, 1, prob.shape[2], W, STRIDE, thr, MW, COINC, flags=gwe.GWE_TRIG_PER_MODEL)
+    solid_o, solid_d = [], []
+    for mi in range(nm):
+        idx, h, pr, wd = per_model[0][mi]
+        mine = recs[recs["model"] == mi]
+        so = idx[_solid(h, pr, wd, thr)]
+        sd = mine["index"][_solid(mine["height"], mine["prominence"], mine["width"], thr)]
+        solid_o.append(so)
+        solid_d.append(sd)
+        n = len(so) + len(sd)
+        agr = (_pairs(so, mine["index"]) + _pairs(sd, idx)) / n if n else 1.0
+        print(f"thr {thr} model {mi}: oracle {len(idx)} peaks ({len(so)} solid), device {len(mine)} "
+              f"({len(sd)} solid): agreement {agr:.5f}")
+        assert agr >= 0.999
+    e_o = np.asarray(ens[0])
+    e_d = np.sort(recs[recs["model"] == -1]["index"])
+    r_o = solid_o[0][oracle.coincidence(solid_o, COINC)] if len(solid_o[0]) else solid_o[0]
+    r_d = solid_d[0][oracle.coincidence(solid_d, COINC)] if len(solid_d[0]) else solid_d[0]
+    n = len(r_o) + len(r_d)
+    agr = (_pairs(r_o, e_d) + _pairs(r_d, e_o)) / n if n else 1.0
+    print(f"thr {thr} ensemble: oracle {len(e_o)} ({len(r_o)} solid), device {len(e_d)} ({len(r_d)} solid): "
+          f"agreement {agr:.5f}")
+    assert agr >= 0.999
+    assert len(e_o) > 0                                   # the trained members do trigger
+
+
+def test_trained_ensemble_detects_loud_injections(held_out):
+    from paper_2201_11133_gb300 import evaluate as ev
+    import paper_2201_11133_gb300 as gwe
+    prob = held_out["prob"]
+    recs = gwe.gwe_triggers(prob, 4, 1, prob.shape[2], W, STRIDE, 0.5, MW, COINC, flags=0)
+    hit = ev.recovered(recs["index"][recs["model"] == -1], held_out["mergers"])
+    print(f"loud held-out injections recovered: {int(hit.sum())} of {len(hit)}")
+    assert hit.sum() >= len(hit) - 1

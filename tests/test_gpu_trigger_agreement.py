@@ -1,10 +1,22 @@
 """Trigger-set agreement between the tensor-core path and the FP64 oracle on the
-same strain: ensemble triggers found on the device from the device's
+same strain: peaks and ensemble triggers found on the device from the device's
 probabilities against those the oracle finds from its own probabilities.
-Reading of "trigger agreement": triggers match when their indices differ by at
-most 256 samples; triggers whose oracle height lies within the probability
-tolerance of the threshold, or whose width lies within 1 % of the minimum
-width, are marginal and counted separately (they may flip either way)."""
+
+Reading of "trigger agreement" (at least 99.9 %), two-sided so that extra
+device triggers count against it as much as missed ones: every solid trigger
+of either side must be found among all triggers of the other side (matched
+when their indices differ by at most 256 samples), and the agreement is
+(solid oracle triggers found on the device + solid device triggers found by the
+oracle) / (solid oracle triggers + solid device triggers).  A peak is solid on
+its side unless its height lies within the path's probability tolerance of the
+threshold, its prominence is below 0.05, or its width lies within 1 % of
+min_width (those may flip either way under the tolerance).  An ensemble
+trigger is solid when its model-0 peak is solid and the coincidence holds with
+the solid peaks of the other models alone.  The plain Jaccard index of the full
+sets is printed too.  Random-init models give jagged series, so the thresholds
+are quantiles of the oracle's probabilities and min_width takes the values 0,
+16 and 2048 (the jagged series of random-init members have no peaks 2048 samples
+wide; the trained ensemble's test covers that cut)."""
 import numpy as np
 import pytest
 
@@ -14,64 +26,110 @@ from gpu_util import require_gpu
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-2       # BF16 probability tolerance
-TOL_FP8 = 3e-2   # FP8 probability tolerance (the 8-layer model's FP8 error is 2.9e-2)
+TOL = {"bf16": 1e-2, "fp8": 3e-2}   # probability tolerance of the path
+COINC = 2048
+RADIUS = 256
+_CACHE = {}
 
 
-def _match(a, b, radius=256):
-    a, b = np.sort(np.asarray(a)), np.sort(np.asarray(b))
+def _pairs(a, b, radius=RADIUS):
+    """Greedy one-to-one matching of sorted index arrays a, b within `radius`: list of (i, j)."""
     used = np.zeros(len(b), dtype=bool)
-    hits = 0
-    for x in a:
+    out = []
+    for i, x in enumerate(a):
         j = np.searchsorted(b, x - radius)
         while j < len(b) and b[j] <= x + radius:
             if not used[j]:
                 used[j] = True
-                hits += 1
+                out.append((i, j))
                 break
             j += 1
-    return hits
+    return out
 
 
-@pytest.mark.parametrize("q,prec", [(0.5, "bf16"), (0.8, "bf16"), (0.5, "fp8"), (0.8, "fp8")])
-def test_trigger_agreement(q, prec):
-    """Random-init models give jagged probability series (median prominence ~0.15), so the
-    threshold sweep uses quantiles of the oracle's probabilities and no width cut."""
+def _solid(h, pr, wd, thr, tol, mw):
+    ok = (np.abs(h - thr) > tol) & (pr >= 0.05)
+    if mw > 0:
+        ok &= np.abs(wd - mw) > 0.01 * mw
+    return ok
+
+
+def _found(a, b):
+    """How many elements of a have a partner in b (one-to-one, within RADIUS)."""
+    return len(_pairs(np.sort(a), np.sort(b)))
+
+
+def _agreement(solid_o, all_o, solid_d, all_d):
+    n = len(solid_o) + len(solid_d)
+    hits = _found(solid_o, all_d) + _found(solid_d, all_o)
+    full = _found(all_o, all_d)
+    jac = full / max(1, len(all_o) + len(all_d) - full)
+    return (hits / n if n else 1.0), n, jac
+
+
+def _setup(name, prec):
     import torch
     import paper_2201_11133_gb300 as gwe
+    key = (name, prec)
+    if key in _CACHE:
+        return _CACHE[key]
     dev = require_gpu()
-    cfg = workload.config("small", n_models=4)
-    W, stride = 1024, 512
-    n = W + 40 * stride
-    sh, sl, _ = workload.stream(n, seed=61, n_inj=2)
-    wb = workload.init_weights(cfg, seed=3000, bias_std=0.1)
+    if name == "small":
+        cfg = workload.config("small", n_models=4)
+        W, stride, nwin, seed = 1024, 512, 40, 61
+        wb = workload.init_weights(cfg, seed=3000, bias_std=0.1)
+    else:
+        cfg = workload.config("ensemble")
+        W, stride, nwin, seed = 4096, 2048, 24, 62
+        wb = workload.init_weights(cfg, seed=3000, bias_std=0.05)
+    n = W + nwin * stride
+    sh, sl, _ = workload.stream(n, seed=seed, n_inj=2)
     ref = oracle.forward_stream(cfg, wb, sh, sl, W, stride).astype(np.float32)
-    thr = float(np.quantile(ref, q))
-    coinc = 2048
-    per_model, ens = oracle.triggers(ref, W, stride, thr, 0.0, coinc)
-    tol = TOL if prec == "bf16" else TOL_FP8
     m = gwe.Model(cfg, wb, gwe.GWE_BF16 if prec == "bf16" else gwe.GWE_FP8)
     prob = m.forward(torch.from_numpy(sh).to(dev), torch.from_numpy(sl).to(dev), W, stride)
     m.sync()
-    recs = gwe.gwe_triggers(prob, 4, 1, prob.shape[2], W, stride, thr, 0.0, coinc)
-    for mi in range(4):
-        idx, h, pr, _ = per_model[0][mi]
-        solid = idx[(pr >= 0.05) & (np.abs(h - thr) > tol)]
-        got_m = recs[recs["model"] == mi]["index"]
-        if len(solid):
-            recall = _match(solid, got_m) / len(solid)
-            print(f"{prec} q {q} model {mi}: {len(idx)} oracle peaks, {len(solid)} solid, recall {recall:.5f}")
-            assert recall >= 0.999
-    got = recs[recs["model"] == -1]["index"]
-    idx0, h0, pr0, _ = per_model[0][0]
-    info = {int(i): (hh, pp) for i, hh, pp in zip(idx0, h0, pr0)}
-    marginal = {int(i) for i in ens[0] if abs(info[int(i)][0] - thr) <= tol or info[int(i)][1] < 0.05}
-    solid_e = [int(i) for i in ens[0] if int(i) not in marginal]
-    hits = _match(solid_e, got)
-    union = len(solid_e) + len(got) - _match(got, ens[0])
-    jacc = hits / max(1, len(solid_e))
-    print(f"{prec} q {q}: {len(ens[0])} oracle ensemble triggers ({len(marginal)} marginal), device {len(got)}, "
-          f"solid recall {jacc:.5f}")
-    assert len(solid_e) > 0
-    assert jacc >= 0.999
     m.close()
+    _CACHE[key] = (cfg, W, stride, ref, prob)
+    return _CACHE[key]
+
+
+# FP8 runs without a width cut: its 3e-2 probability error moves the half-height crossings of the jagged
+# random-init peaks by more samples than the 1 % marginal band of a 16-sample cut
+CASES = [(name, prec, q, mw) for name, prec in [("small", "bf16"), ("small", "fp8"), ("ensemble", "bf16")]
+         for q in (0.5, 0.8) for mw in (0.0, 16.0, 2048.0) if prec == "bf16" or mw == 0.0]
+
+
+@pytest.mark.parametrize("name,prec,q,mw", CASES)
+def test_trigger_agreement(name, prec, q, mw):
+    import paper_2201_11133_gb300 as gwe
+    cfg, W, stride, ref, prob = _setup(name, prec)
+    nm = int(cfg["n_models"])
+    tol = TOL[prec]
+    thr = float(np.quantile(ref, q))
+    per_model, ens = oracle.triggers(ref, W, stride, thr, mw, COINC)
+    recs = gwe.gwe_triggers(prob, nm, 1, prob.shape[2], W, stride, thr, mw, COINC, flags=gwe.GWE_TRIG_PER_MODEL)
+    solid_o, solid_d = [], []
+    total = 0
+    for mi in range(nm):
+        idx, h, pr, wd = per_model[0][mi]
+        mine = recs[recs["model"] == mi]
+        so = idx[_solid(h, pr, wd, thr, tol, mw)]
+        sd = mine["index"][_solid(mine["height"], mine["prominence"], mine["width"], thr, tol, mw)]
+        solid_o.append(so)
+        solid_d.append(sd)
+        agr, n, jac = _agreement(so, idx, sd, mine["index"])
+        total += len(so)
+        print(f"{name} {prec} q {q} mw {mw} model {mi}: oracle {len(idx)} peaks ({len(so)} solid), device "
+              f"{len(mine)} ({len(sd)} solid): agreement {agr:.5f} over {n}, Jaccard {jac:.5f}")
+        assert agr >= 0.999
+    e_o = np.asarray(ens[0])
+    e_d = recs[recs["model"] == -1]["index"]
+    # solid ensemble triggers: coincidence with the solid peaks alone
+    r_o = solid_o[0][oracle.coincidence(solid_o, COINC)] if len(solid_o[0]) else solid_o[0]
+    r_d = solid_d[0][oracle.coincidence(solid_d, COINC)] if len(solid_d[0]) else solid_d[0]
+    agr, n, jac = _agreement(r_o, e_o, r_d, e_d)
+    print(f"{name} {prec} q {q} mw {mw} ensemble: oracle {len(e_o)} ({len(r_o)} solid), device {len(e_d)} "
+          f"({len(r_d)} solid): agreement {agr:.5f} over {n}, Jaccard {jac:.5f}")
+    if mw == 0.0:
+        assert total > 0                  # the sweep point without a width cut has peaks to compare
+    assert agr >= 0.999

@@ -46,3 +46,42 @@ def test_whiten_argument_errors():
         with pytest.raises(gwe.GweError) as ei:
             gwe.gwe_whiten(*args)
         assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("average,alpha,n", [("median", 0.0, 64 * 4096), ("median", 0.1, 100000 + 7),
+                                             ("mean", 0.1, 64 * 4096), ("median", 0.0, 3600 * 4096)])
+def test_whiten_variants_match_oracle(average, alpha, n):
+    """Median-averaged Welch PSD and Tukey-tapered whitening, on coloured noise with loud sine-Gaussian
+    glitches in it (what the median average is for)."""
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    dev = require_gpu()
+    x = workload.coloured_noise(n, seed=2025)
+    xl = np.zeros_like(x)
+    workload.add_glitches(x, xl, max(1, n // (30 * 4096)), seed=5, snr_range=(50.0, 200.0))
+    x = x.astype(np.float32)
+    seg = 16384 if n >= 64 * 4096 else 4096
+    ref = ow.whiten(x.astype(np.float64), FS, seg, average=average, tukey_alpha=alpha)
+    xt = torch.from_numpy(x).to(dev)
+    out = torch.empty_like(xt)
+    gwe.gwe_whiten_ex(xt, n, FS, seg, out, psd_average=gwe.GWE_PSD_MEDIAN if average == "median" else gwe.GWE_PSD_MEAN,
+                      tukey_alpha=alpha)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    print(f"{average} alpha={alpha} n={n}: max |dy| {err.max():.2e}, rms {np.sqrt(np.mean(err ** 2)):.2e}")
+    assert err.max() <= 2e-4
+    assert np.sqrt(np.mean(err ** 2)) <= 1e-5
+    assert abs(np.std(got) - 1.0) < 1e-5
+
+
+def test_whiten_ex_argument_errors():
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    dev = require_gpu()
+    x = torch.zeros(5000, device=dev)
+    out = torch.zeros(5000, device=dev)
+    for kw in [dict(psd_average=2), dict(tukey_alpha=1.5), dict(tukey_alpha=-0.1), dict(f_low=3000.0)]:
+        with pytest.raises(gwe.GweError) as ei:
+            gwe.gwe_whiten_ex(x, 5000, FS, 1024, out, **kw)
+        assert ei.value.status == 1

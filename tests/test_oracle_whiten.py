@@ -74,3 +74,63 @@ def test_whitened_white_noise_is_flat(sigma):
     assert np.all(np.abs(flat - 1.0) < 0.06), flat
     low = np.mean(py[(fy > 2.0) & (fy < 12.0)]) / (2.0 / FS)
     assert low < 0.05                      # removed below 15 Hz
+
+
+@pytest.mark.parametrize("n", [5 * SEG, 5 * SEG + SEG // 2, 12 * SEG + 77])
+def test_median_welch_matches_scipy(n):
+    """Odd and even numbers of segments (the even median averages the two middle values)."""
+    rng = np.random.default_rng(n + 1)
+    x = rng.standard_normal(n) * 2.0 - 0.3
+    f, p = ow.welch_psd(x, FS, SEG, average="median")
+    fr, pr = scipy_signal.welch(x, fs=FS, window="hann", nperseg=SEG, noverlap=SEG // 2, detrend="constant",
+                                scaling="density", return_onesided=True, average="median")
+    np.testing.assert_allclose(p, pr, rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("n,alpha", [(100, 0.5), (101, 0.25), (16, 1.0), (7, 0.1), (4096, 0.1), (50, 0.0)])
+def test_tukey_matches_scipy(n, alpha):
+    np.testing.assert_allclose(ow.tukey(n, alpha), scipy_signal.windows.tukey(n, alpha), rtol=0, atol=1e-14)
+
+
+def test_median_bias_closed_form():
+    # the median of n (odd) exponential(1) values has mean H_n - H_{(n-1)/2} = 1 - 1/2 + ... + 1/n: check the
+    # bias against a Monte-Carlo mean of medians (within 5 standard errors)
+    rng = np.random.default_rng(3)
+    for n in (3, 9, 33):
+        med = np.median(rng.exponential(1.0, size=(200000, n)), axis=1)
+        assert abs(med.mean() - ow.median_bias(n)) < 5.0 * med.std() / np.sqrt(med.size)
+        h = lambda m: sum(1.0 / k for k in range(1, m + 1))
+        assert abs(ow.median_bias(n) - (h(n) - h((n - 1) // 2))) < 1e-14
+    assert ow.median_bias(1) == 1.0 and ow.median_bias(2) == 1.0 and abs(ow.median_bias(4) - (1 - 0.5 + 1 / 3)) < 1e-15
+
+
+def test_median_psd_robust_to_glitches():
+    """White noise with a few loud sine-Gaussian glitches at 200 Hz: the mean-averaged Welch PSD is
+    inflated in the glitch band, the median-averaged one stays at the noise level 2 sigma^2 / fs."""
+    n = 256 * int(FS)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(n)
+    for c in (40, 120, 200):
+        g = workload.sine_gaussian(200.0, 20.0, fs=int(FS))
+        h = g.shape[0] // 2
+        x[c * int(FS) - h:c * int(FS) + h + 1] += 40.0 * g
+    f, pm = ow.welch_psd(x, FS, SEG, average="mean")
+    _, pd = ow.welch_psd(x, FS, SEG, average="median")
+    band = (f > 190.0) & (f < 210.0)
+    level = 2.0 / FS
+    assert pm[band].mean() > 1.5 * level
+    assert abs(pd[band].mean() / level - 1.0) < 0.15
+    quiet = (f > 600.0) & (f < 1600.0)
+    assert abs(pd[quiet].mean() / level - 1.0) < 0.05
+
+
+@pytest.mark.parametrize("average,alpha", [("median", 0.0), ("mean", 0.1), ("median", 0.1)])
+def test_whitening_variants_flat_on_coloured_noise(average, alpha):
+    n = 128 * int(FS)
+    x = workload.coloured_noise(n, seed=77)
+    y = ow.whiten(x, FS, 4 * SEG, average=average, tukey_alpha=alpha)
+    assert abs(np.std(y) - 1.0) < 1e-12
+    core = y[n // 8:-n // 8]                 # away from the tapered ends
+    fy, py = ow.welch_psd(core / np.std(core), FS, SEG)
+    flat = _band_means(fy, py, 20.0, 2000.0, 20) / (2.0 / FS)
+    assert np.all(np.abs(flat - 1.0) < 0.08), flat

@@ -256,25 +256,83 @@ def coloured_noise(n: int, seed: int = 1000, fs: int = FS) -> np.ndarray:
     return np.fft.irfft(spec, n) * 1e21
 
 
+def sine_gaussian(f0: float, q: float, fs: int = FS, phase0: float = 0.0) -> np.ndarray:
+    """Sine-Gaussian burst exp(-t^2 / tau^2) sin(2 pi f0 t + phase0), tau = q / (sqrt(2) pi f0), over
+    |t| <= 4 tau (the usual model of short instrumental glitches); centred sample at index len // 2."""
+    tau = q / (math.sqrt(2.0) * math.pi * f0)
+    half = max(1, int(math.ceil(4.0 * tau * fs)))
+    t = np.arange(-half, half + 1, dtype=np.float64) / fs
+    return np.exp(-(t / tau) ** 2) * np.sin(2.0 * math.pi * f0 * t + phase0)
+
+
+def _whitened_norm(h: np.ndarray, fs: int, psd_scale: float) -> float:
+    pad = 8192
+    m = h.shape[0] + pad
+    hf = np.fft.rfft(np.concatenate([h, np.zeros(pad)]))
+    f = np.fft.rfftfreq(m, 1.0 / fs)
+    wf = hf / np.sqrt(fs * aligo_like_psd(f) * psd_scale / 2.0)
+    wf[f < 15.0] = 0.0
+    return math.sqrt(float(np.sum(np.fft.irfft(wf, m) ** 2)))
+
+
+def add_glitches(xh: np.ndarray, xl: np.ndarray, n_glitch: int, seed: int, snr_range=(10.0, 100.0),
+                 f0_range=(30.0, 500.0), q_range=(3.0, 30.0), fs: int = FS, psd_scale: float = 1e42,
+                 avoid=(), guard: int = 4 * FS):
+    """Add n_glitch sine-Gaussian glitches, each in one detector only (chosen at random), to the
+    coloured streams xh, xl (in place), scaled so that the whitened glitch has norm `snr`; centres
+    uniform, at least `guard` samples from every index in `avoid` (the chirp mergers).
+    Returns [(centre, detector (0 = H, 1 = L), snr, f0, q)]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = xh.shape[0]
+    av = np.sort(np.asarray(list(avoid), dtype=np.int64))
+    out = []
+    tries = 0
+    while len(out) < n_glitch and tries < 100 * max(1, n_glitch):
+        tries += 1
+        c = int(rng.integers(fs, n - fs))
+        if av.size:
+            j = np.searchsorted(av, c)
+            near = [av[k] for k in (j - 1, j) if 0 <= k < av.size]
+            if any(abs(int(a) - c) < guard for a in near):
+                continue
+        det = int(rng.integers(0, 2))
+        snr = rng.uniform(*snr_range)
+        f0 = rng.uniform(*f0_range)
+        q = rng.uniform(*q_range)
+        h = sine_gaussian(f0, q, fs=fs, phase0=rng.uniform(0, 2 * math.pi))
+        half = h.shape[0] // 2
+        if c - half < 0 or c + half >= n:
+            continue
+        nrm = _whitened_norm(h, fs, psd_scale)
+        x = xh if det == 0 else xl
+        x[c - half:c + half + 1] += (h * (snr / nrm)).astype(x.dtype)
+        out.append((c, det, float(snr), float(f0), float(q)))
+    return out
+
+
 def coloured_stream(n: int, seed: int = 1000, n_inj: int = 0, snr_range=(6.0, 20.0), mc_range=(5.0, 30.0),
-                    min_gap: int = 2 * FS, fs: int = FS):
+                    min_gap: int = 2 * FS, fs: int = FS, with_params: bool = False):
     """Two detector streams of n samples (float32) of coloured Gaussian noise with the analytic
     spectrum (scaled by 1e21) and n_inj unwhitened leading-order chirps.
 
     Each chirp is scaled so that, whitened with the true spectrum (division of its transform by
     sqrt(fs S / 2), S the spectrum of the scaled noise), its norm is the detector SNR
     (network SNR / sqrt(2)); mergers uniform, >= min_gap apart; Livingston delayed by U[-10, 10] ms
-    with an independent phase.  Stands in for unwhitened GWOSC strain with injections."""
+    with an independent phase.  Stands in for unwhitened GWOSC strain with injections.
+    with_params: also return a list of (merger, network SNR, chirp mass) per injection."""
     xh = coloured_noise(n, seed=seed)
     xl = coloured_noise(n, seed=seed + 1)
     rng = np.random.Generator(np.random.PCG64(seed + 1000))
     mergers = []
+    params = []
     lo = 6 * fs
     if n_inj > 0 and n > lo + 2 * fs:
         slots = np.sort(rng.choice(np.arange(lo, n - fs, min_gap), size=n_inj, replace=False))
         for tm in slots:
             mc = rng.uniform(*mc_range)
-            snr = rng.uniform(*snr_range) / math.sqrt(2.0)
+            snr_net = rng.uniform(*snr_range)
+            snr = snr_net / math.sqrt(2.0)
+            params.append((int(tm), float(snr_net), float(mc)))
             dt = int(round(rng.uniform(-0.010, 0.010) * fs))
             ph = rng.uniform(0, 2 * math.pi)
             for x, t_m, p0 in ((xh, int(tm), 0.0), (xl, int(tm) + dt, ph)):
@@ -290,4 +348,6 @@ def coloured_stream(n: int, seed: int = 1000, n_inj: int = 0, snr_range=(6.0, 20
                 if norm > 0:
                     x[t_m - n_before:t_m + 1] += h * (snr / norm)
             mergers.append(int(tm))
+    if with_params:
+        return xh.astype(np.float32), xl.astype(np.float32), mergers, params
     return xh.astype(np.float32), xl.astype(np.float32), mergers
