@@ -611,6 +611,20 @@ int64_t gwe_launch_count(void);
  */
 gwe_status gwe_debug_config(int drop, double wait_seconds);
 
+/*
+ * Address checks of the tensor-core forward (the paper has no counterpart).
+ * The kernel checks every lag-copy source and history-row store it computes
+ * against the size of its lag ring, and every projection store against the
+ * projection buffer; an address outside is not accessed: the kernel records
+ * the site (41: lag source, 42: history store, 43: projection store) in the
+ * handle's error word, stops the copies of the branch concerned, and gwe_sync
+ * returns GWE_ERR_CUDA with the site in gwe_last_error().  Test hook: with
+ * bytes > 0 the checks treat the ring as that many bytes smaller than it is,
+ * so that the path can be exercised without any out-of-range access; 0
+ * restores normal operation.  Process-wide; GWE_ERR_ARG for bytes < 0.
+ */
+gwe_status gwe_debug_ring_margin(int64_t bytes);
+
 /* Thread-local description of the last error ("" if none). */
 const char *gwe_last_error(void);
 

@@ -114,6 +114,7 @@ def load():
             "gwe_sync": (I, [P, P]),
             "gwe_set_cross_window_reuse": (I, [I]),
             "gwe_debug_config": (I, [I, D]),
+            "gwe_debug_ring_margin": (I, [I64]),
             "gwe_forward_static": (I, [P, P, P, I64, I, I, P, P, P]),
             "gwe_plan_create": (I, [P, P, P, P, P, I, I, I, P, I, P, I, P, P]),
             "gwe_plan_execute": (I, [P, P]),
@@ -473,6 +474,11 @@ def gwe_set_cross_window_reuse(enable: bool) -> None:
 def gwe_debug_config(drop: int, wait_seconds: float) -> None:
     """Failure-detection test hook: bound of device waits and a dropped producer (see include/gwe.h)."""
     _check(load().gwe_debug_config(int(drop), float(wait_seconds)), "gwe_debug_config")
+
+
+def gwe_debug_ring_margin(nbytes: int) -> None:
+    """Test hook of the kernel's address checks (see include/gwe.h)."""
+    _check(load().gwe_debug_ring_margin(int(nbytes)), "gwe_debug_ring_margin")
 
 
 def gwe_sync(model: int, stream=None) -> None:

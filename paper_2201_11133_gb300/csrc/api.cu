@@ -502,6 +502,11 @@ gwe_status gwe_debug_config(int drop, double wait_seconds) {
     return debug_config(drop, wait_seconds);
 }
 
+gwe_status gwe_debug_ring_margin(int64_t bytes) {
+    clear_error();
+    return debug_ring_margin(bytes);
+}
+
 gwe_status gwe_whiten_ex(const float *strain, int64_t n, double fs, int seg_len, const gwe_whiten_options *opt,
                          float *out, void *stream) {
     clear_error();

@@ -173,6 +173,11 @@ struct TcParams {
     uint64_t ring_rows;        // lag-history rows per branch (sum of dilations)
     int *err;                  // error word: wait site of the first timeout
     int n16;                   // 16-bit path: layers l < n16 take FP16 conv operands, the others BF16
+    // Allocation sizes of the ring (bytes, all CTAs) and of the projections (FP16 elements): every
+    // computed lag-copy source, history-row store and projection store is checked against them; an
+    // address outside records a site >= 40 in the error word and the access is not made.
+    uint64_t ring_alloc;
+    uint64_t proj_alloc;
     int model0;                // jobs cover models model0 .. model0 + n_models - 1
     // Projection mode (proj != NULL): instead of the head, store per branch the head's first
     // convolution restricted to that branch, P_H = W_h1[:, H] ReLU(s_H) + b_h1 and
@@ -371,22 +376,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 };
                 // lagged rows of layer l for the tile at t0 (ring par of this job, or the previous
                 // job's ring when the source rows were taken over from the previous window)
-                auto issue_lag = [&](int l, int t0, bool ru, uint32_t par) {
+                auto issue_lag = [&](int l, int t0, bool ru, uint32_t par) -> bool {
                     const int d = 1 << (l % lps);
                     const int n = d < kTile ? d : kTile;
                     const uint32_t bytes = (uint32_t)n * 16;
-                    mbar_arrive_expect_tx(&bar[B_LAG + b], bytes * Sh::RC);
                     const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
                     const int ts = t0 / kTile - (d < kTile ? 1 : d / kTile);   // tile holding the source rows
                     const bool prev = ru && ts >= 0 && ts < NT - p.reuse_shift && l <= p.lstar[ts];
                     const uint8_t *src = ring_c + (uint64_t)(par ^ (prev ? 1u : 0u)) * p.ring_pp + roff * Sh::XROW +
                                          (uint64_t)(t0 & (d - 1)) * 16;
+                    if (t0 >= d && (uint64_t)(src - p.ring) + (uint64_t)(Sh::RC - 1) * d * 16 + bytes > p.ring_alloc) {
+                        atomicCAS(p.err, 0, 41);   // a lag source outside the ring: copy nothing, stop
+                        *abort_flag = 1;
+                        return false;
+                    }
+                    mbar_arrive_expect_tx(&bar[B_LAG + b], bytes * Sh::RC);
                     uint8_t *dst0 = smem + Sh::OFF_STAGE + b * Sh::STAGE_BYTES + (kTile - n) * 16;
 #pragma unroll
                     for (int c = 0; c < Sh::RC; ++c)
                         bulk_g2s(dst0 + c * Sh::STAGE_LBO, (t0 < d) ? p.zeros : src + (uint64_t)c * d * 16, bytes,
                                  &bar[B_LAG + b]);
                     ++lag_issued;
+                    return true;
                 };
                 // test hook: branch 0's producer issues nothing, so the MMA warp's first wait runs out
                 if (p.dbg_drop == 1 && b == 0) ok = false;
@@ -417,13 +428,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             // lagged rows: the staging buffer is free once the previous conv completed
                             // (first layer of a tile: once the previous tile's head has read it)
                             if (l > l0 || first) {
-                                issue_lag(l, tt * kTile, ru, par);
+                                if (!(ok = issue_lag(l, tt * kTile, ru, par))) break;
                             } else {
                                 ok = mbar_wait(&bar[B_HREADY + b], ph_h & 1, abort_flag, p.err, 3, p.wait_ns) &&
                                      mbar_wait(&bar[B_HEAD], ph_h & 1, abort_flag, p.err, 4, p.wait_ns);
                                 if (!ok) break;
                                 ++ph_h;
-                                issue_lag(l, tt * kTile, ru, par);
+                                if (!(ok = issue_lag(l, tt * kTile, ru, par))) break;
                             }
                             first = false;
                             // rs entry
@@ -802,9 +813,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                     // gate's hand-off, while the res MMAs run (x still holds x_l, and the FP8 staging
                     // row is rewritten only by the residual below), so that the warps holding the
                     // last rows do not delay the gate.
-                    if ((tt + 1 < NT || cw) && r >= kTile - n) {
-                        const uint64_t roff = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
-                        uint8_t *dst = ring_b + roff * Sh::XROW + (uint64_t)((t0 + r) & (d - 1)) * 16;
+                    const uint64_t roff_h = (uint64_t)(l / lps) * ((1u << lps) - 1) + (uint64_t)(d - 1);
+                    uint8_t *dst = ring_b + roff_h * Sh::XROW + (uint64_t)((t0 + r) & (d - 1)) * 16;
+                    // the last 16-byte chunk this thread stores (chunk columns of its half, d rows apart)
+                    const bool in_ring = (uint64_t)(dst - p.ring) + (uint64_t)(hf * (Sh::RC / 2) + Sh::RC / 2 - 1) * d * 16 +
+                                             16 <= p.ring_alloc;
+                    if ((tt + 1 < NT || cw) && r >= kTile - n && !in_ring) atomicCAS(p.err, 0, 42);
+                    if ((tt + 1 < NT || cw) && r >= kTile - n && in_ring) {
                         if constexpr (F8) {
                             // the quantised row is still in the staging buffer (rewritten after the rs MMA)
 #pragma unroll
@@ -932,6 +947,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                 if (p.proj) {
                     // P_b (+ b_h1 for the Hanford branch), FP16, 16-byte chunks of 8 channels, rows contiguous
                     uint16_t *pw = p.proj + ((uint64_t)b * p.nw + (uint64_t)jb.w) * (uint64_t)HC * p.W;
+                    // the highest element this thread stores: chunk HC/8 - 1 of its row
+                    const bool in_proj = (uint64_t)(pw - p.proj) + ((uint64_t)(HC / 8 - 1) * p.W + t0 + r) * 8 + 8 <=
+                                         p.proj_alloc;
+                    if (!in_proj) atomicCAS(p.err, 0, 43);
                     const uint32_t t_p = tmem + t_lane + b * Sh::TMEM_BSTRIDE;
                     constexpr int HH = HC / 2;       // channels per thread (half)
 #pragma unroll
@@ -948,8 +967,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                                               pack_h2(u[6], u[7]));
                         uint4 v1 = make_uint4(pack_h2(u[8], u[9]), pack_h2(u[10], u[11]), pack_h2(u[12], u[13]),
                                               pack_h2(u[14], u[15]));
-                        *reinterpret_cast<uint4 *>(pw + ((uint64_t)(ch / 8) * p.W + t0 + r) * 8) = v0;
-                        *reinterpret_cast<uint4 *>(pw + ((uint64_t)(ch / 8 + 1) * p.W + t0 + r) * 8) = v1;
+                        if (in_proj) {
+                            *reinterpret_cast<uint4 *>(pw + ((uint64_t)(ch / 8) * p.W + t0 + r) * 8) = v0;
+                            *reinterpret_cast<uint4 *>(pw + ((uint64_t)(ch / 8 + 1) * p.W + t0 + r) * 8) = v1;
+                        }
                     }
                     tc_fence_before();
                     continue;
@@ -1111,6 +1132,7 @@ namespace {
 // Test hooks (gwe_debug_config): limit of every device-side wait, and a dropped producer.
 uint64_t g_wait_ns = kWaitNs;
 int g_dbg_drop = 0;
+uint64_t g_dbg_ring_margin = 0;   // test hook: the address checks see a ring this many bytes smaller
 std::atomic<int> g_reuse{1};   // cross-window reuse on (gwe_set_cross_window_reuse)
 
 // Cross-window reuse plan (fields of TcParams): for stride a multiple of the tile with
@@ -1518,6 +1540,9 @@ gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const
     p.out = out;
     p.logits = logits ? 1 : 0;
     p.ring = wk.ring.as<uint8_t>();
+    p.ring_alloc = n_rings * ring_cta * grid_max;
+    p.ring_alloc = p.ring_alloc > g_dbg_ring_margin ? p.ring_alloc - g_dbg_ring_margin : 0;
+    p.proj_alloc = 0;
     p.ring_cta_bytes = n_rings * ring_cta;
     p.ring_pp = n_rings > 1 ? ring_cta : 0;
     p.zeros = s.zeros.as<uint8_t>();
@@ -1550,6 +1575,7 @@ gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const
         const uint64_t proj_elems = 2ull * (uint64_t)nw * HC * W;
         GWE_CUDA_TRY(wk.proj.ensure(proj_elems * sizeof(uint16_t)));
         L.proj = wk.proj.as<uint16_t>();
+        p.proj_alloc = proj_elems;
     }
     return GWE_OK;
 }
@@ -1933,6 +1959,15 @@ gwe_status debug_config(int drop, double wait_seconds) {
     return GWE_OK;
 }
 
+gwe_status debug_ring_margin(int64_t bytes) {
+    if (bytes < 0) {
+        set_error("gwe_debug_ring_margin: bytes must be >= 0");
+        return GWE_ERR_ARG;
+    }
+    g_dbg_ring_margin = (uint64_t)bytes;
+    return GWE_OK;
+}
+
 gwe_status tc_check(gwe_model *m, cudaStream_t st) {
     TcState *s = reinterpret_cast<TcState *>(m->tc);
     if (!s) return GWE_OK;
@@ -1941,6 +1976,11 @@ gwe_status tc_check(gwe_model *m, cudaStream_t st) {
     GWE_CUDA_TRY(cudaMemcpy(&e, s->err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
     if (e != 0) {
         cudaMemset(s->err.ptr, 0, sizeof(int));
+        if (e >= 40) {
+            set_error("an address check of the tensor-core kernel failed (site " + std::to_string(e) +
+                      "); the access was not made and the outputs are invalid");
+            return GWE_ERR_CUDA;
+        }
         set_error("a device-side wait of the tensor-core kernel timed out (site " + std::to_string(e) + ")");
         return GWE_ERR_TIMEOUT;
     }
@@ -2063,6 +2103,8 @@ gwe_status launch_tc_static(gwe_model *m, TcState &s, uint8_t *scratch, const fl
     p.out = out;
     p.logits = 0;
     p.ring = scratch + kStaticRingOff;
+    p.ring_alloc = (uint64_t)grid * ring_cta;
+    p.proj_alloc = 0;
     p.ring_cta_bytes = ring_cta;
     p.ring_pp = 0;
     p.zeros = scratch + kStaticZeroOff;

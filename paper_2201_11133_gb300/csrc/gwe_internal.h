@@ -161,6 +161,7 @@ gwe_status fp32_act_amax(gwe_model *m, const float *sH, const float *sL, int win
 // branch_tc.cu (tensor-core path: GWE_BF16, GWE_FP8)
 gwe_status tc_check(gwe_model *m, cudaStream_t st);
 gwe_status debug_config(int drop, double wait_seconds);
+gwe_status debug_ring_margin(int64_t bytes);
 void set_cross_window_reuse(int enable);
 // f8: E4M3 convolutions, calibrated on synthetic unit-variance white noise until tc_calibrate runs
 gwe_status tc_prepare(gwe_model *m, const float *host_blob, bool f8);

@@ -97,7 +97,7 @@ class Batches:
 
 
 def train_member(cfg, init_seed: int, data_seed: int, steps: int, batch: int = 256, W: int = 4096,
-                 lr: float = 1e-3, clip: float = 1.0, device=None, log_every: int = 50, verbose: bool = True):
+                 lr: float = 5e-4, clip: float = 1.0, device=None, log_every: int = 50, verbose: bool = True):
     """Train one member (cfg with n_models = 1) from gwe_init_weights(cfg, init_seed); returns
     (FP32 blob [P], loss history)."""
     import torch
@@ -120,6 +120,8 @@ def train_member(cfg, init_seed: int, data_seed: int, steps: int, batch: int = 2
         opt.step()
         if it % log_every == 0 or it == steps - 1:
             lv = float(loss.item())
+            if not math.isfinite(lv):
+                raise FloatingPointError(f"loss is {lv} at step {it}")
             hist.append((it, lv))
             if verbose:
                 print(f"step {it}: loss {lv:.4f} ({time.time() - t0:.1f} s)", flush=True)
@@ -133,7 +135,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--members", type=int, default=4)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--init-seed", type=int, default=3000)
     ap.add_argument("--data-seed", type=int, default=7000)
     ap.add_argument("--out", default="trained.npz")
@@ -147,9 +149,10 @@ def main(argv=None):
         print(f"member {k}", flush=True)
         blobs[k], h = train_member(cfg, a.init_seed + k, a.data_seed + 101 * k, a.steps, a.batch, lr=a.lr)
         hists.append(h)
-    np.savez(a.out, weights=blobs, loss=np.array(hists, dtype=np.float64),
-             meta=np.array([a.steps, a.batch, a.lr, a.init_seed, a.data_seed], dtype=np.float64))
-    print("saved", a.out)
+        # saved after every member (members 0 .. k trained)
+        np.savez(a.out, weights=blobs[:k + 1], loss=np.array(hists, dtype=np.float64),
+                 meta=np.array([a.steps, a.batch, a.lr, a.init_seed, a.data_seed], dtype=np.float64))
+        print("saved", a.out, flush=True)
 
 
 if __name__ == "__main__":

@@ -46,3 +46,36 @@ def test_debug_config_rejects_bad_arguments():
         with pytest.raises(gwe.GweError) as ei:
             gwe.gwe_debug_config(drop, wait)
         assert ei.value.status == 1
+
+
+def test_address_check_stops_the_copies_and_is_reported():
+    """The ring is reported 4 KiB smaller to the kernel's address checks: the lag copies that would
+    reach into the missing part are not made, the site is recorded, gwe_sync reports it, and a normal
+    forward on the same context matches the oracle afterwards.  No access outside the real ring is
+    made at any point (the real ring is larger than the checked size)."""
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    dev = require_gpu()
+    cfg = workload.config("small")
+    W, stride = 1024, 512
+    n = W + 3 * stride
+    sh, sl, _ = workload.stream(n, seed=52)
+    wb = workload.init_weights(cfg, seed=3901, bias_std=0.1)
+    m = gwe.Model(cfg, wb, gwe.GWE_BF16)
+    H, L = torch.from_numpy(sh).to(dev), torch.from_numpy(sl).to(dev)
+    try:
+        gwe.gwe_debug_config(0, 0.2)
+        gwe.gwe_debug_ring_margin(1 << 40)        # every lag source fails the check
+        m.forward(H, L, W, stride)
+        with pytest.raises(gwe.GweError) as ei:
+            m.sync()
+        assert ei.value.status == 2
+        assert "address check" in str(ei.value)
+    finally:
+        gwe.gwe_debug_ring_margin(0)
+        gwe.gwe_debug_config(0, 4.0)
+    out = m.forward(H, L, W, stride)
+    m.sync()
+    ref = oracle.forward_stream(cfg, wb, sh, sl, W, stride)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-2
+    m.close()
