@@ -536,6 +536,26 @@ gwe_status gwe_search_create(gwe_model *model, const gwe_search_config *cfg, gwe
 gwe_status gwe_search_run(gwe_search *search, const void *strain_H, const void *strain_L, int64_t n_samples,
                           int host_input, gwe_trigger *out, int64_t cap, int64_t *n_out, void *stream);
 
+/*
+ * Checkpoint and resume of a long search (a month of data is searched chunk by
+ * chunk; the paper's run spans many nodes and hours, section "Computational
+ * Efficiency").  The chunks' cores partition the stream, so the records of
+ * chunks [a, b) followed by those of [b, c) are exactly the records of [a, c):
+ * a caller that stores the records found so far and the next chunk index can
+ * stop after any range and continue later with the same configuration and
+ * strain.
+ *   gwe_search_chunks     number of chunks of a stream of n_samples samples
+ *                         (0 if the stream is shorter than one window).
+ *   gwe_search_run_range  as gwe_search_run for chunks [chunk_begin,
+ *                         min(chunk_end, gwe_search_chunks)) only; records in
+ *                         chunk order.  GWE_ERR_ARG for a negative or reversed
+ *                         range.
+ */
+int64_t gwe_search_chunks(const gwe_search *search, int64_t n_samples);
+gwe_status gwe_search_run_range(gwe_search *search, const void *strain_H, const void *strain_L, int64_t n_samples,
+                                int host_input, int64_t chunk_begin, int64_t chunk_end, gwe_trigger *out, int64_t cap,
+                                int64_t *n_out, void *stream);
+
 /* Release a search. */
 void gwe_search_destroy(gwe_search *search);
 

@@ -25,7 +25,8 @@ __all__ = [
     "gwe_trigger_sweep", "gwe_trigger_sweep_segments", "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_whiten_ex", "GWE_PSD_MEAN", "GWE_PSD_MEDIAN", "gwe_last_error",
     "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static",
     "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE",
-    "gwe_search_create", "gwe_search_run", "gwe_search_destroy", "GWE_INPUT_F32", "GWE_INPUT_F16", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
+    "gwe_search_create", "gwe_search_run", "gwe_search_run_range", "gwe_search_chunks", "gwe_search_resumable",
+    "gwe_search_destroy", "GWE_INPUT_F32", "GWE_INPUT_F16", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
 
 GWE_FP32, GWE_BF16, GWE_FP8 = 0, 1, 2
@@ -123,6 +124,8 @@ def load():
             "gwe_search_create": (I, [P, P, P]),
             "gwe_search_run": (I, [P, P, P, I64, I, P, I64, P, P]),
             "gwe_search_destroy": (None, [P]),
+            "gwe_search_chunks": (I64, [P, I64]),
+            "gwe_search_run_range": (I, [P, P, P, I64, I, I64, I64, P, I64, P, P]),
             "gwe_profile_enable": (I, [I]),
             "gwe_profile_read": (I, [I, P, I, P, P]),
             "gwe_last_error": (ctypes.c_char_p, []),
@@ -459,6 +462,63 @@ def gwe_search_run(search: int, strain_H, strain_L, n_samples: int, cap: int = 1
     _check(load().gwe_search_run(search, ph, pl, int(n_samples), 0 if dh else 1, out.ctypes.data, int(cap),
                                  ctypes.byref(n_out), _stream(stream)), "gwe_search_run")
     return out[:n_out.value].copy()
+
+
+def gwe_search_chunks(search: int, n_samples: int) -> int:
+    return int(load().gwe_search_chunks(search, int(n_samples)))
+
+
+def _strain_ptrs(strain_H, strain_L):
+    def ptr(x):
+        if hasattr(x, "is_cuda"):
+            if not x.is_contiguous():
+                raise ValueError("expected a contiguous tensor")
+            return x.data_ptr(), bool(x.is_cuda)
+        a = np.ascontiguousarray(x)
+        return a.ctypes.data, False
+    (ph, dh), (pl, dl) = ptr(strain_H), ptr(strain_L)
+    if dh != dl:
+        raise ValueError("strain_H and strain_L must both be on the device or both on the host")
+    return ph, pl, dh
+
+
+def gwe_search_run_range(search: int, strain_H, strain_L, n_samples: int, chunk_begin: int, chunk_end: int,
+                         cap: int = 1 << 20, stream=None) -> np.ndarray:
+    """Records (TRIGGER_DTYPE) of chunks [chunk_begin, chunk_end) of the stream."""
+    ph, pl, dev = _strain_ptrs(strain_H, strain_L)
+    out = np.zeros(max(1, int(cap)), dtype=TRIGGER_DTYPE)
+    n_out = ctypes.c_int64(0)
+    _check(load().gwe_search_run_range(search, ph, pl, int(n_samples), 0 if dev else 1, int(chunk_begin),
+                                       int(chunk_end), out.ctypes.data, int(cap), ctypes.byref(n_out),
+                                       _stream(stream)), "gwe_search_run_range")
+    return out[:n_out.value].copy()
+
+
+def gwe_search_resumable(search: int, strain_H, strain_L, n_samples: int, checkpoint: str, chunks_per_step: int = 1,
+                         max_steps=None, stream=None) -> np.ndarray:
+    """Run a search in ranges of `chunks_per_step` chunks, saving the next chunk index and the records
+    found so far to `checkpoint` (an .npz file) after every range, and continuing from it when it
+    exists.  Returns the records so far (all of them once the last chunk is done); stops early after
+    `max_steps` ranges if given."""
+    import os
+    n_chunks = gwe_search_chunks(search, n_samples)
+    nxt, recs = 0, np.zeros(0, dtype=TRIGGER_DTYPE)
+    if os.path.exists(checkpoint):
+        z = np.load(checkpoint)
+        if int(z["n_samples"]) != int(n_samples) or int(z["n_chunks"]) != n_chunks:
+            raise ValueError("checkpoint belongs to another stream")
+        nxt, recs = int(z["next_chunk"]), z["records"].astype(TRIGGER_DTYPE)
+    steps = 0
+    while nxt < n_chunks and (max_steps is None or steps < max_steps):
+        end = min(n_chunks, nxt + int(chunks_per_step))
+        part = gwe_search_run_range(search, strain_H, strain_L, n_samples, nxt, end, stream=stream)
+        recs = np.concatenate([recs, part])
+        nxt = end
+        steps += 1
+        tmp = checkpoint + ".tmp.npz"
+        np.savez(tmp, next_chunk=nxt, n_chunks=n_chunks, n_samples=int(n_samples), records=recs)
+        os.replace(tmp, checkpoint)
+    return recs
 
 
 def gwe_search_destroy(search: int) -> None:

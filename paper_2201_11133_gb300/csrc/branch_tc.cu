@@ -680,27 +680,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
         // scale (FP32 {scale, bias} pairs).
         auto gate16 = [&](const uint32_t (&fr)[16], const uint32_t (&gr)[16], int ch, uint32_t bslot, uint32_t (&zz)[8]) {
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                float f0, f1, g0, g1;
+            for (int jq = 0; jq < 4; ++jq) {          // four channels (two pairs) per step
+                float f[4], gv[4];
                 if constexpr (F8) {
-                    const uint4 sf = lds128(bslot + (ch + 2 * jj) * 8);          // {s, b} of f channels 2jj, 2jj+1
-                    const uint4 sg4 = lds128(bslot + (R + ch + 2 * jj) * 8);     // same for g
-                    f0 = fmaf(__uint_as_float(fr[2 * jj]), __uint_as_float(sf.x), __uint_as_float(sf.y));
-                    f1 = fmaf(__uint_as_float(fr[2 * jj + 1]), __uint_as_float(sf.z), __uint_as_float(sf.w));
-                    g0 = fmaf(__uint_as_float(gr[2 * jj]), __uint_as_float(sg4.x), __uint_as_float(sg4.y));
-                    g1 = fmaf(__uint_as_float(gr[2 * jj + 1]), __uint_as_float(sg4.z), __uint_as_float(sg4.w));
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int jj = 2 * jq + h;
+                        const uint4 sf = lds128(bslot + (ch + 2 * jj) * 8);          // {s, b} of f channels 2jj, 2jj+1
+                        const uint4 sg4 = lds128(bslot + (R + ch + 2 * jj) * 8);     // same for g
+                        f[2 * h] = fmaf(__uint_as_float(fr[2 * jj]), __uint_as_float(sf.x), __uint_as_float(sf.y));
+                        f[2 * h + 1] = fmaf(__uint_as_float(fr[2 * jj + 1]), __uint_as_float(sf.z), __uint_as_float(sf.w));
+                        gv[2 * h] = fmaf(__uint_as_float(gr[2 * jj]), __uint_as_float(sg4.x), __uint_as_float(sg4.y));
+                        gv[2 * h + 1] = fmaf(__uint_as_float(gr[2 * jj + 1]), __uint_as_float(sg4.z), __uint_as_float(sg4.w));
+                    }
                 } else {
-                    // FP32 biases of f channels ch + 2jj, +1 and of the matching g channels
-                    uint32_t bfv0, bfv1, bgv0, bgv1;
-                    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(bfv0), "=r"(bfv1) : "r"(bslot + (ch + 2 * jj) * 4));
-                    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(bgv0), "=r"(bgv1) : "r"(bslot + (R + ch + 2 * jj) * 4));
-                    f0 = __uint_as_float(fr[2 * jj]) + __uint_as_float(bfv0);
-                    f1 = __uint_as_float(fr[2 * jj + 1]) + __uint_as_float(bfv1);
-                    g0 = __uint_as_float(gr[2 * jj]) + __uint_as_float(bgv0);
-                    g1 = __uint_as_float(gr[2 * jj + 1]) + __uint_as_float(bgv1);
+                    // FP32 biases of f channels ch + 4jq .. + 3 and of the matching g channels
+                    const uint4 bf = lds128(bslot + (ch + 4 * jq) * 4);
+                    const uint4 bg = lds128(bslot + (R + ch + 4 * jq) * 4);
+                    f[0] = __uint_as_float(fr[4 * jq]) + __uint_as_float(bf.x);
+                    f[1] = __uint_as_float(fr[4 * jq + 1]) + __uint_as_float(bf.y);
+                    f[2] = __uint_as_float(fr[4 * jq + 2]) + __uint_as_float(bf.z);
+                    f[3] = __uint_as_float(fr[4 * jq + 3]) + __uint_as_float(bf.w);
+                    gv[0] = __uint_as_float(gr[4 * jq]) + __uint_as_float(bg.x);
+                    gv[1] = __uint_as_float(gr[4 * jq + 1]) + __uint_as_float(bg.y);
+                    gv[2] = __uint_as_float(gr[4 * jq + 2]) + __uint_as_float(bg.z);
+                    gv[3] = __uint_as_float(gr[4 * jq + 3]) + __uint_as_float(bg.w);
                 }
-                const float s0 = fmaf(tanh_f32(g0), 0.5f, 0.5f), s1 = fmaf(tanh_f32(g1), 0.5f, 0.5f);
-                zz[jj] = pack_h2(tanh_f32(f0) * s0, tanh_f32(f1) * s1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float s0 = fmaf(tanh_f32(gv[2 * h]), 0.5f, 0.5f), s1 = fmaf(tanh_f32(gv[2 * h + 1]), 0.5f, 0.5f);
+                    zz[2 * jq + h] = pack_h2(tanh_f32(f[2 * h]) * s0, tanh_f32(f[2 * h + 1]) * s1);
+                }
             }
         };
 
@@ -780,8 +790,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                         for (int k4 = 0; k4 < RH / 4; ++k4)
                             dx[k4] = make_float4(x[4 * k4], x[4 * k4 + 1], x[4 * k4 + 2], x[4 * k4 + 3]);
                     }
-                    if (!warp_wait(B_CONV + b, ph_conv & 1, 30) ||
-                        !warp_wait(B_BIAS + 4 * b + (g & 1), (g >> 1) & 1, 36)) { ok = false; break; }
+                    // the bias slot lands long before the conv MMAs complete: test it first, so that
+                    // only the conv barrier's test stands between the MMAs' completion and the gate
+                    if (!warp_wait(B_BIAS + 4 * b + (g & 1), (g >> 1) & 1, 36) ||
+                        !warp_wait(B_CONV + b, ph_conv & 1, 30)) { ok = false; break; }
                     ++ph_conv;
                     tc_fence_after();
                     // gate: z = tanh(f + b_f) * (0.5 tanh(g/2 + b_g/2) + 0.5), FP32

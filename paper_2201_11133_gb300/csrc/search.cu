@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <string>
 #include <vector>
 
@@ -106,24 +107,33 @@ gwe_status prefetch(SearchImpl &S, const Chunk &k, const void *const in[2], int 
     return GWE_OK;
 }
 
-gwe_status run(SearchImpl &S, const void *sH, const void *sL, int64_t n, int host_input, cudaStream_t st) {
+int64_t chunk_count(const gwe_search_config &c, int64_t n) {
+    if (n < c.window) return 0;
+    const int64_t nw = (n - c.window) / c.stride + 1;
+    return (nw + c.chunk_windows - 1) / c.chunk_windows;
+}
+
+// chunks [c_begin, c_end) of the stream (clipped to the stream's chunks)
+gwe_status run(SearchImpl &S, const void *sH, const void *sL, int64_t n, int host_input, cudaStream_t st,
+               int64_t c_begin, int64_t c_end) {
     const gwe_search_config &c = S.cfg;
     const Dims &d = S.m->dims;
     S.recs.clear();
     if (n < c.window) return GWE_OK;
     const int64_t nw = (n - c.window) / c.stride + 1;
-    const int64_t n_chunks = (nw + c.chunk_windows - 1) / c.chunk_windows;
+    const int64_t n_chunks = std::min<int64_t>(c_end, chunk_count(c, n));
+    if (c_begin >= n_chunks) return GWE_OK;
     const int64_t n_st = (nw - 1) * c.stride + c.window;   // stitched series length
     const void *in[2] = {sH, sL};
     const size_t eb = elem_bytes(c.input_dtype);
     // a device buffer must not be overwritten by the prefetch while a previous chunk still reads it
     for (int b = 0; b < 2; ++b) GWE_CUDA_TRY(cudaEventRecord(S.consumed[b], st));
     if (host_input) {
-        gwe_status r = prefetch(S, chunk_of(c, n, nw, 0), in, 0);
+        gwe_status r = prefetch(S, chunk_of(c, n, nw, c_begin), in, (int)(c_begin & 1));
         if (r != GWE_OK) return r;
     }
     std::vector<gwe_trigger> part;
-    for (int64_t i = 0; i < n_chunks; ++i) {
+    for (int64_t i = c_begin; i < n_chunks; ++i) {
         const Chunk k = chunk_of(c, n, nw, i);
         const int b = (int)(i & 1);
         const int64_t span = k.x_b - k.x_a;
@@ -242,7 +252,7 @@ extern "C" gwe_status gwe_search_run(gwe_search *s, const void *strain_H, const 
     *n_out = 0;
     gwe::SearchImpl &S = *s->impl;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    gwe_status r = gwe::run(S, strain_H, strain_L, n_samples, host_input, st);
+    gwe_status r = gwe::run(S, strain_H, strain_L, n_samples, host_input, st, 0, INT64_MAX);
     // leave no copy in flight on the private stream, whatever happened
     cudaStreamSynchronize(S.copy_st);
     if (r != GWE_OK) return r;
@@ -251,6 +261,36 @@ extern "C" gwe_status gwe_search_run(gwe_search *s, const void *strain_H, const 
     if (k > 0) std::copy(S.recs.begin(), S.recs.begin() + k, out);
     if (*n_out > cap) {
         set_error("gwe_search_run: output capacity too small");
+        return GWE_ERR_CAPACITY;
+    }
+    return GWE_OK;
+}
+
+extern "C" int64_t gwe_search_chunks(const gwe_search *s, int64_t n_samples) {
+    if (!s || !s->impl || n_samples < 0) return 0;
+    return gwe::chunk_count(s->impl->cfg, n_samples);
+}
+
+extern "C" gwe_status gwe_search_run_range(gwe_search *s, const void *strain_H, const void *strain_L,
+                                           int64_t n_samples, int host_input, int64_t chunk_begin, int64_t chunk_end,
+                                           gwe_trigger *out, int64_t cap, int64_t *n_out, void *stream) {
+    clear_error();
+    GWE_ARG_CHECK(s != nullptr && s->impl != nullptr, "search is NULL");
+    GWE_ARG_CHECK(strain_H != nullptr && strain_L != nullptr && n_out != nullptr, "NULL argument");
+    GWE_ARG_CHECK(n_samples >= 0 && (host_input == 0 || host_input == 1), "bad n_samples or host_input");
+    GWE_ARG_CHECK(chunk_begin >= 0 && chunk_end >= chunk_begin, "bad chunk range");
+    GWE_ARG_CHECK(cap >= 0 && (cap == 0 || out != nullptr), "out is NULL with cap > 0");
+    *n_out = 0;
+    gwe::SearchImpl &S = *s->impl;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    gwe_status r = gwe::run(S, strain_H, strain_L, n_samples, host_input, st, chunk_begin, chunk_end);
+    cudaStreamSynchronize(S.copy_st);
+    if (r != GWE_OK) return r;
+    *n_out = (int64_t)S.recs.size();
+    const int64_t k = std::min<int64_t>(cap, *n_out);
+    if (k > 0) std::copy(S.recs.begin(), S.recs.begin() + k, out);
+    if (*n_out > cap) {
+        set_error("gwe_search_run_range: output capacity too small");
         return GWE_ERR_CAPACITY;
     }
     return GWE_OK;

@@ -53,7 +53,7 @@ def _reference(gwe, m, xH, xL, n, W, S, K, M, G, seg, thr, minw, coinc, flags):
 
 
 @pytest.mark.parametrize("dtype,host", [("f16", False), ("f32", True), ("f16", True)])
-def test_search_equals_per_chunk_calls(dtype, host):
+def test_search_equals_per_chunk_calls(dtype, host, tmp_path):
     import torch
     import paper_2201_11133_gb300 as gwe
     dev = require_gpu()
@@ -95,6 +95,19 @@ def test_search_equals_per_chunk_calls(dtype, host):
         # a second run on the same handle gives the same records
         got2 = gwe.gwe_search_run(sr, iH, iL, n)
         np.testing.assert_array_equal(got2, got)
+        # chunk ranges concatenate to the whole run; a checkpointed run stopped after one range and
+        # resumed from its checkpoint gives the same records
+        assert gwe.gwe_search_chunks(sr, n) == 5
+        parts = [gwe.gwe_search_run_range(sr, iH, iL, n, a, b) for a, b in ((0, 2), (2, 3), (3, 99))]
+        np.testing.assert_array_equal(np.concatenate(parts), got)
+        ck = str(tmp_path / "search_checkpoint.npz")
+        first = gwe.gwe_search_resumable(sr, iH, iL, n, ck, chunks_per_step=2, max_steps=1)
+        np.testing.assert_array_equal(first, np.concatenate(parts[:1]))
+        rest = gwe.gwe_search_resumable(sr, iH, iL, n, ck, chunks_per_step=2)
+        np.testing.assert_array_equal(rest, got)
+        with pytest.raises(gwe.GweError) as e:
+            gwe.gwe_search_run_range(sr, iH, iL, n, 3, 2)
+        assert e.value.status == 1
         with pytest.raises(gwe.GweError) as e:
             gwe.gwe_search_run(sr, iH, iL, n, cap=1)
         assert e.value.status == 6

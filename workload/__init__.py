@@ -281,7 +281,7 @@ def add_glitches(xh: np.ndarray, xl: np.ndarray, n_glitch: int, seed: int, snr_r
     """Add n_glitch sine-Gaussian glitches, each in one detector only (chosen at random), to the
     coloured streams xh, xl (in place), scaled so that the whitened glitch has norm `snr`; centres
     uniform, at least `guard` samples from every index in `avoid` (the chirp mergers).
-    Returns [(centre, detector (0 = H, 1 = L), snr, f0, q)]."""
+    Returns [(centre, detector (0 = H, 1 = L), snr, f0, q, phase)]."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n = xh.shape[0]
     av = np.sort(np.asarray(list(avoid), dtype=np.int64))
@@ -299,14 +299,15 @@ def add_glitches(xh: np.ndarray, xl: np.ndarray, n_glitch: int, seed: int, snr_r
         snr = rng.uniform(*snr_range)
         f0 = rng.uniform(*f0_range)
         q = rng.uniform(*q_range)
-        h = sine_gaussian(f0, q, fs=fs, phase0=rng.uniform(0, 2 * math.pi))
+        phase = rng.uniform(0, 2 * math.pi)
+        h = sine_gaussian(f0, q, fs=fs, phase0=phase)
         half = h.shape[0] // 2
         if c - half < 0 or c + half >= n:
             continue
         nrm = _whitened_norm(h, fs, psd_scale)
         x = xh if det == 0 else xl
         x[c - half:c + half + 1] += (h * (snr / nrm)).astype(x.dtype)
-        out.append((c, det, float(snr), float(f0), float(q)))
+        out.append((c, det, float(snr), float(f0), float(q), float(phase)))
     return out
 
 
