@@ -341,8 +341,9 @@ def batched_slides(gwe, cfg, wb, Hw, Lw, n, thr, minutes, dist, dev, stream, wor
            "physical_strain_s_per_s": world * strain_s / (t_step / 1000.0),
            "effective_strain_s_per_s": world * strain_s * k_sl / (t_step / 1000.0),
            "ensemble_triggers": int(np.sum(recs["model"] == -1)) if len(recs) else 0,
-           "plan": {"graph_kernels": shape["n_kernels"], "slide_tile": shape["slide_tile"],
-                    "slides_per_block": shape["slides_per_block"], "slide_heads_ms_tuned": shape["tuned_ms"],
+           "plan": {"graph_kernels": shape["n_kernels"], "slide_window_tile": shape["window_tile"],
+                    "slide_offset_tile": shape["offset_tile"], "slide_pieces_per_block": shape["pieces_per_block"],
+                    "slide_heads_ms_tuned": shape["tuned_ms"],
                     "slide_heads_ms_default": shape["default_ms"], "create_s": t_create},
            "segment_lengths_s": {"min": float(lens.min()) / FS, "median": float(np.median(lens)) / FS,
                                  "max": float(lens.max()) / FS},
@@ -684,7 +685,26 @@ def main():
                     rec_at[f"{tq:g}"] = {"recovered_fraction": float(hit.mean()),
                                          "far_per_hour": float(bg_t) / hours_bg}
                 sweep_res["recovery_at"] = rec_at
-        slides_res = {"offsets": k_sl, "ms_per_step": t_sl, "threshold_sweep": sweep_res if args.sweep_thresholds > 0 else None,
+        # roofline of the slide heads (one launch = one model, all offsets): FP16x2 instructions against the
+        # FP16x2 FMA rate of the SMs (152 SMs x 128 lanes per clock at the 2.07 GHz maximum clock), and the
+        # Livingston-tile bytes the register blocking streams from L2 (default shape: 4 windows x pieces
+        # of 8 offsets in step 2, so 11 tiles per 32 pairs), for context
+        sl_roof = None
+        if "k_slide_head" in prof_sl and prof_sl["k_slide_head"][1] > 0:
+            hc = int(cfg["head_ch"])
+            ms_l = prof_sl["k_slide_head"][0] / prof_sl["k_slide_head"][1]
+            off_samples = k_sl * nw * WINDOW
+            inst = off_samples * hc                                    # Hc/2 ReLU-adds + Hc/2 FMAs, FP16x2
+            peak = 152 * 128 * 2.07e9
+            l2_bytes = off_samples * (2 * hc) * 11 / 32 + nw * WINDOW * 2 * hc
+            sl_roof = {"kernel": "k_slide_head", "bound": "alu", "achieved": inst / (ms_l / 1e3) / 1e12,
+                       "peak": peak / 1e12, "unit": "T FP16x2 inst/s", "frac": inst / (ms_l / 1e3) / peak,
+                       "peak_source": "derived: 152 SMs x 128 FP16x2 FMA lanes/clk x 2.07 GHz",
+                       "ms_per_launch": ms_l, "offset_samples_per_launch": off_samples,
+                       "l2_bytes_per_launch": l2_bytes, "l2_gbs": l2_bytes / (ms_l / 1e3) / 1e9,
+                       "traffic": None}
+        slides_res = {"offsets": k_sl, "ms_per_step": t_sl, "roofline": sl_roof,
+                      "threshold_sweep": sweep_res if args.sweep_thresholds > 0 else None,
                       "physical_strain_s_per_s": world * strain_s / (t_sl / 1000.0),
                       "effective_strain_s_per_s": world * strain_s * k_sl / (t_sl / 1000.0),
                       "ensemble_triggers": int(np.sum(recs["model"] == -1)) if len(recs) else 0,

@@ -370,11 +370,15 @@ typedef struct gwe_plan gwe_plan;
  *                    multiple of 128.
  *   flags            0 or GWE_PLAN_AUTOTUNE.  With GWE_PLAN_AUTOTUNE and
  *                    n_slides > 0 the plan times every candidate launch shape of
- *                    the slide heads (64, 128 or 256 samples per block; all
- *                    offsets per block or a quarter of them) on these buffers
- *                    with CUDA events and keeps the fastest; the choice is
- *                    cached per geometry for the process.  Without it, 128
- *                    samples and all offsets per block.
+ *                    the slide heads (2 or 4 Hanford windows per block; pieces
+ *                    of up to 4 or 8 consecutive offsets; all pieces per block
+ *                    or a quarter of them) on these buffers with CUDA events
+ *                    and keeps the fastest; the choice is cached per geometry
+ *                    for the process.  Without it, the shape set by
+ *                    gwe_set_slide_shape (4 windows, pieces of up to 8
+ *                    offsets, all pieces per block unless changed).  Every shape computes
+ *                    the same sums in the same order: the output does not
+ *                    depend on the shape.
  *   stream           creation runs (and synchronises) on this stream; the graph
  *                    is recorded on a private stream.
  *   out              receives the plan.
@@ -393,13 +397,25 @@ gwe_status gwe_plan_create(gwe_model *model, const float *strain_H, const float 
 gwe_status gwe_plan_execute(gwe_plan *plan, void *stream);
 
 /*
- * The launch shape the plan uses: samples per block and offsets per block of
- * the slide heads, the number of kernels in its graph, and (after autotuning)
- * the time of one model's slide heads with the chosen shape and with the
- * default shape, in milliseconds (0 when not tuned).  NULL outputs are skipped.
+ * The launch shape the plan uses for the slide heads: Hanford windows per
+ * block, the longest run of consecutive offsets a block pairs with them (a
+ * piece), and pieces per block; the number of kernels in its graph; and
+ * (after autotuning) the time of one model's slide heads with the chosen shape
+ * and with the default shape, in milliseconds (0 when not tuned).  NULL
+ * outputs are skipped.
  */
-gwe_status gwe_plan_shape(const gwe_plan *plan, int *slide_tile, int *slides_per_block, int *n_kernels,
-                          double *tuned_ms, double *default_ms);
+gwe_status gwe_plan_shape(const gwe_plan *plan, int *window_tile, int *offset_tile, int *pieces_per_block,
+                          int *n_kernels, double *tuned_ms, double *default_ms);
+
+/*
+ * Slide-head launch shape of the launches that are not autotuned, from now on
+ * (process-wide): gwe_forward and gwe_forward_segments with slides, and plans
+ * created without GWE_PLAN_AUTOTUNE.  Hanford windows per block (2 or 4), the
+ * longest offset piece (4 or 8) and pieces per block (0: all).  The default is
+ * (4, 8, 0).  The output does not depend on the shape.  GWE_ERR_ARG for other
+ * values.
+ */
+gwe_status gwe_set_slide_shape(int window_tile, int offset_tile, int pieces_per_block);
 
 /* Release a plan (after its executions have completed). */
 void gwe_plan_destroy(gwe_plan *plan);

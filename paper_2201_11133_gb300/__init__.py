@@ -24,7 +24,7 @@ __all__ = [
     "gwe_model_destroy",
     "gwe_trigger_sweep", "gwe_trigger_sweep_segments", "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_whiten_ex", "GWE_PSD_MEAN", "GWE_PSD_MEDIAN", "gwe_last_error",
     "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static",
-    "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE",
+    "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_set_slide_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE",
     "gwe_search_create", "gwe_search_run", "gwe_search_run_range", "gwe_search_chunks", "gwe_search_resumable",
     "gwe_search_destroy", "GWE_INPUT_F32", "GWE_INPUT_F16", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
@@ -119,7 +119,8 @@ def load():
             "gwe_forward_static": (I, [P, P, P, I64, I, I, P, P, P]),
             "gwe_plan_create": (I, [P, P, P, P, P, I, I, I, P, I, P, I, P, P]),
             "gwe_plan_execute": (I, [P, P]),
-            "gwe_plan_shape": (I, [P, P, P, P, P, P]),
+            "gwe_plan_shape": (I, [P, P, P, P, P, P, P]),
+            "gwe_set_slide_shape": (I, [I, I, I]),
             "gwe_plan_destroy": (None, [P]),
             "gwe_search_create": (I, [P, P, P]),
             "gwe_search_run": (I, [P, P, P, I64, I, P, I64, P, P]),
@@ -417,13 +418,21 @@ def gwe_plan_execute(plan: int, stream=None) -> None:
 
 
 def gwe_plan_shape(plan: int) -> dict:
-    """Launch shape of a plan: slide-head samples and offsets per block, kernels in the graph, tuning times (ms)."""
-    tile, spb, nk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    """Launch shape of a plan's slide heads (Hanford windows per block, offsets per piece, pieces per
+    block), kernels in the graph, tuning times (ms)."""
+    wt, ot, ppb, nk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     t_ms, d_ms = ctypes.c_double(), ctypes.c_double()
-    _check(load().gwe_plan_shape(plan, ctypes.byref(tile), ctypes.byref(spb), ctypes.byref(nk), ctypes.byref(t_ms),
-                                 ctypes.byref(d_ms)), "gwe_plan_shape")
-    return {"slide_tile": tile.value, "slides_per_block": spb.value, "n_kernels": nk.value,
+    _check(load().gwe_plan_shape(plan, ctypes.byref(wt), ctypes.byref(ot), ctypes.byref(ppb), ctypes.byref(nk),
+                                 ctypes.byref(t_ms), ctypes.byref(d_ms)), "gwe_plan_shape")
+    return {"window_tile": wt.value, "offset_tile": ot.value, "pieces_per_block": ppb.value, "n_kernels": nk.value,
             "tuned_ms": t_ms.value, "default_ms": d_ms.value}
+
+
+def gwe_set_slide_shape(window_tile: int = 4, offset_tile: int = 8, pieces_per_block: int = 0) -> None:
+    """Slide-head shape of launches that are not autotuned (forward calls with slides and plans created
+    without GWE_PLAN_AUTOTUNE), process-wide, from now on."""
+    _check(load().gwe_set_slide_shape(int(window_tile), int(offset_tile), int(pieces_per_block)),
+           "gwe_set_slide_shape")
 
 
 def gwe_plan_destroy(plan: int) -> None:

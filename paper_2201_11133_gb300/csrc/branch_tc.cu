@@ -1028,109 +1028,215 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
 }
 
 // Time slides on the branch projections: for each slide k, Hanford window w is paired with
-// Livingston window (w + k) mod n_w, and
+// Livingston window (w + k) mod n_w (within w's segment), and
 //   out[slide][w][t] = sigmoid(b_h2 + sum_j w_h2[j] ReLU(P_H[w][t][j] + P_L[w'][t][j]))
 // (the head's first convolution is linear in [s_H ; s_L], so the branch pass runs once per window
-// and a slide costs 3 Hc operations per sample).  FP16x2 ReLU-add and products with FP16 partial
-// sums over 16 channels, FP32 across partials, FP32 logit and sigmoid.
-// Grid: x = window (fast, so that concurrent blocks share the Livingston tiles in L2), y = T-sample
-// tile, z = group of `spb` offsets; T threads, thread = sample; the block's Hanford tile is staged
-// in shared memory.  T and spb are the launch shape the plan autotuner chooses.
-template <int HC, int T>
-__global__ void __launch_bounds__(T) k_slide_head(const uint16_t *__restrict__ proj, int64_t nw, int W,
-                                                  const int32_t *__restrict__ koff, int n_slides, int spb, int n_seg,
-                                                  const int64_t *__restrict__ seg_w0,
-                                                  const float *__restrict__ w2, const float *__restrict__ b2p,
-                                                  float *__restrict__ out,
-                                                  int64_t slide_stride, int logits) {
-    constexpr int NC = HC / 8;                    // 16-byte chunks per sample
-    extern __shared__ uint4 ph_s[];               // [NC][T]
-    __shared__ uint32_t w2h[HC / 2];
-    const int64_t w = blockIdx.x;
-    const int t0 = blockIdx.y * T, t = threadIdx.x;
-    const int s_begin = blockIdx.z * spb;
-    const int s_end = min(n_slides, s_begin + spb);
-    // the window's segment: Livingston windows wrap within it
-    int64_t sw0 = 0, snw = nw;
-    if (n_seg > 1) {
-        const int g = find_segment(seg_w0, n_seg, w);
-        sw0 = seg_w0[g];
-        snw = seg_w0[g + 1] - sw0;
+// and a slide costs 3 Hc operations per sample).
+//
+// Arithmetic (identical for every launch shape, so that all shapes give the same bits): the Hc
+// channels form Hc/16 pairs of 16-byte chunks; per pair, FP16x2 ReLU-adds and products accumulate
+// in one FP16x2 word over its 16 channels, which is widened to FP32 and summed (x + y); the pair
+// sums are added in a balanced binary tree in pair order; b_h2 is added last, then the sigmoid.
+//
+// Register blocking: the offsets are taken in pieces of up to B values in arithmetic progression
+// k0, k0 + dw, ..., k0 + (nb - 1) dw (dw: the offset list's most common step), and a block pairs
+// a piece with A Hanford windows of one segment spaced by the same step, w0 + a dw.  Pair (a, b)
+// reads Livingston window (w0 + k0 + (a + b) dw) mod n_w, which depends on s = a + b only, so the
+// block streams the A + B - 1 Livingston tiles through registers once each and every tile serves
+// up to min(A, B) pairs: the L2 -> SM traffic per offset-sample is (A + B - 1) / (A B) of the tile
+// bytes (7/16 at 4 x 4, 11/32 at 4 x 8).  Offsets outside a progression form pieces of one.
+// Threads: one chunk pair per thread; a warp holds QL pairs of SPW samples (lane = pair-in-warp x
+// SPW + sample, so every load request reads whole 128-byte lines), QH warps hold the other pairs.
+// The pair sums are reduced by recursive halving across the warp's lanes (shuffles) and then
+// across the warps through shared memory.
+template <int HC>
+struct SlideGeo {
+    static constexpr int NP = HC / 16;             // chunk pairs (leaves of the summation tree)
+    static constexpr int QL = NP < 4 ? NP : 4;     // pairs per warp
+    static constexpr int QH = NP / QL;             // warps per block
+    static constexpr int SPB = 32 / QL;            // samples per block
+    static constexpr int THREADS = 32 * QH;
+    static constexpr int MIN_BLOCKS = 512 / THREADS;   // at most 128 registers per thread
+    static_assert(NP >= 1 && NP % QL == 0 && (QH & (QH - 1)) == 0, "pair layout");
+};
+
+template <int N>
+__device__ __forceinline__ float tree_sum(const float *x) {
+    if constexpr (N == 1) {
+        return x[0];
+    } else {
+        return tree_sum<N / 2>(x) + tree_sum<N / 2>(x + N / 2);
     }
-    const uint64_t bstride = (uint64_t)nw * HC * W;   // elements per branch block
-    const uint4 *pH = reinterpret_cast<const uint4 *>(proj + (uint64_t)w * HC * W);
-    for (int c = 0; c < NC; ++c) ph_s[c * T + t] = pH[(uint64_t)c * W + t0 + t];
-    for (int j = t; j < HC / 2; j += T) w2h[j] = pack_h2(w2[2 * j], w2[2 * j + 1]);
-    const float b2 = __ldg(b2p);
-    __syncthreads();
+}
+
+// one pair's sum for Hanford chunks h[0..1] and Livingston chunks l0, l1 with head weights wv
+__device__ __forceinline__ float slide_pair(const uint4 (&h)[2], const uint4 &l0, const uint4 &l1,
+                                            const uint32_t (&wv)[8]) {
     const uint32_t one2 = 0x3C003C00u;            // (1, 1) in FP16x2
-    // Livingston window of slide si (wrapping within the segment)
-    auto lwin = [&](int si) -> const uint4 * {
-        int64_t wl = (w - sw0 + koff[si]) % snw;   // koff[si]: slide offset in windows
-        if (wl < 0) wl += snw;
-        wl += sw0;
-        return reinterpret_cast<const uint4 *>(proj + bstride + (uint64_t)wl * HC * W);
-    };
-    auto finish = [&](int si, float acc) {
-        const float lg = acc + b2;
-        out[(uint64_t)si * slide_stride + (uint64_t)w * W + t0 + t] = logits ? lg : 1.f / (1.f + expf(-lg));
-    };
-    // two offsets per pass: one shared-memory read of the Hanford chunk serves both, and the two
-    // Livingston streams give twice the loads in flight (the per-offset arithmetic is unchanged)
-    int si = s_begin;
-    for (; si + 1 < s_end; si += 2) {
-        const uint4 *pL0 = lwin(si), *pL1 = lwin(si + 1);
-        float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll 2
-        for (int c = 0; c < NC; c += 2) {
-            uint32_t h0 = 0u, h1 = 0u;
+    const uint32_t hv[8] = {h[0].x, h[0].y, h[0].z, h[0].w, h[1].x, h[1].y, h[1].z, h[1].w};
+    const uint32_t lv[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+    uint32_t acc = 0u;
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                const uint4 a = ph_s[(c + cc) * T + t];
-                const uint4 l0 = __ldg(pL0 + (uint64_t)(c + cc) * W + t0 + t);
-                const uint4 l1 = __ldg(pL1 + (uint64_t)(c + cc) * W + t0 + t);
-                const uint32_t av[4] = {a.x, a.y, a.z, a.w};
-                const uint32_t lv0[4] = {l0.x, l0.y, l0.z, l0.w}, lv1[4] = {l1.x, l1.y, l1.z, l1.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t r0, r1;
-                    asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(r0) : "r"(av[q]), "r"(one2), "r"(lv0[q]));
-                    asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(r1) : "r"(av[q]), "r"(one2), "r"(lv1[q]));
-                    h0 = hfma2(r0, w2h[(c + cc) * 4 + q], h0);
-                    h1 = hfma2(r1, w2h[(c + cc) * 4 + q], h1);
-                }
-            }
-            const float2 f0 = __half22float2(*reinterpret_cast<__half2 *>(&h0));
-            const float2 f1 = __half22float2(*reinterpret_cast<__half2 *>(&h1));
-            acc0 += f0.x + f0.y;
-            acc1 += f1.x + f1.y;
-        }
-        finish(si, acc0);
-        finish(si + 1, acc1);
+    for (int j = 0; j < 8; ++j) {
+        uint32_t r;
+        asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(hv[j]), "r"(one2), "r"(lv[j]));
+        acc = hfma2(r, wv[j], acc);
     }
-    if (si < s_end) {
-        const uint4 *pL = lwin(si);
-        float acc = 0.f;
-#pragma unroll 4
-        for (int c = 0; c < NC; c += 2) {
-            uint32_t hacc = 0u;
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&acc));
+    return f.x + f.y;
+}
+
+// Grid: x = run of A dw windows (taken as dw residues of A windows each, and split where a segment
+// ends), y = 32-sample tile, z = group of `ppb` pieces.  pieces[i] = (first slide index, count).
+template <int HC, int A, int B>
+__global__ void __launch_bounds__(SlideGeo<HC>::THREADS, SlideGeo<HC>::MIN_BLOCKS) k_slide_head(
+    const uint16_t *__restrict__ proj, int64_t nw, int W, const int32_t *__restrict__ koff,
+    const int2 *__restrict__ pieces, int n_pieces, int ppb, int dw, int n_seg, const int64_t *__restrict__ seg_w0,
+    const float *__restrict__ w2, const float *__restrict__ b2p, float *__restrict__ out, int64_t slide_stride,
+    int logits) {
+    using G = SlideGeo<HC>;
+    constexpr int V = A * B;                       // pair values per thread and piece
+    constexpr int NS = A + B - 1;                  // Livingston tiles per piece
+    constexpr int PF = NS < 4 ? NS : 4;            // tiles in flight
+    constexpr int VL = V / G::QL;                  // values a lane holds after the in-warp halving
+    static_assert(V % G::QL == 0, "values per lane");
+    __shared__ float part[G::QH > 1 ? G::QH * V * G::SPB : 1];
+    const int lane = threadIdx.x & 31, qh = threadIdx.x >> 5;
+    const int qlo = lane / G::SPB, ts = lane % G::SPB;
+    const int q = qh * G::QL + qlo;                // this thread's chunk pair
+    const int tb = blockIdx.y * G::SPB;
+    const int pc0 = blockIdx.z * ppb;
+    const int pc1 = min(n_pieces, pc0 + ppb);
+    uint32_t wv[8];
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                const uint4 a = ph_s[(c + cc) * T + t];
-                const uint4 l = __ldg(pL + (uint64_t)(c + cc) * W + t0 + t);
-                const uint32_t av[4] = {a.x, a.y, a.z, a.w}, lv[4] = {l.x, l.y, l.z, l.w};
+    for (int j = 0; j < 8; ++j) wv[j] = pack_h2(__ldg(w2 + 16 * q + 2 * j), __ldg(w2 + 16 * q + 2 * j + 1));
+    const float b2 = __ldg(b2p);
+    const uint64_t wst = (uint64_t)HC * W / 8;     // 16-byte chunks per window
+    // this thread's first chunk in Hanford window 0 and in Livingston window 0 (the second chunk of
+    // the pair is W chunks further)
+    const uint4 *Hp = reinterpret_cast<const uint4 *>(proj) + (uint64_t)(2 * q) * W + tb + ts;
+    const uint4 *Lp = Hp + (uint64_t)nw * wst;
+    // offset of this lane's values after the halving: level l keeps the upper half on bit l of qlo
+    int voff = 0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t rl;
-                    asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(rl) : "r"(av[q]), "r"(one2), "r"(lv[q]));
-                    hacc = hfma2(rl, w2h[(c + cc) * 4 + q], hacc);
+    for (int l = 0; (1 << l) < G::QL; ++l) voff += ((qlo >> l) & 1) * (V >> (l + 1));
+    const int64_t wrun = (int64_t)blockIdx.x * A * dw;
+    const int64_t wend = min(nw, wrun + (int64_t)A * dw);
+    for (int64_t wa = wrun, rho = 0; rho < dw; wa = wrun + ++rho) {
+      while (wa < wend) {
+        // windows wa + a dw, a < na, all in wa's segment
+        int64_t sw0 = 0, snw = nw;
+        if (n_seg > 1) {
+            const int g = find_segment(seg_w0, n_seg, wa);
+            sw0 = seg_w0[g];
+            snw = seg_w0[g + 1] - sw0;
+        }
+        const int na = (int)((min(wend, sw0 + snw) - wa + dw - 1) / dw);
+        uint4 h[A][2];
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+            if (a < na) {
+                const uint4 *hp = Hp + (uint64_t)(wa + (int64_t)a * dw) * wst;
+                h[a][0] = __ldg(hp);
+                h[a][1] = __ldg(hp + W);
+            } else {
+                h[a][0] = h[a][1] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        const uint4 *Ls = Lp + (uint64_t)sw0 * wst;    // Livingston window 0 of the segment
+        const int sn = (int)snw;
+        for (int pc = pc0; pc < pc1; ++pc) {
+            const int2 pe = pieces[pc];
+            const int nb = pe.y;
+            const int ns = na + nb - 1;
+            // Livingston row of step s: (r0 + s dw) mod n_w; the loads run through s = 0, 1, ... in
+            // order, so the row advances by dw per load (no division in the loop)
+            const int64_t t0 = (wa - sw0) + (int64_t)koff[pe.x];
+            int rl;
+            if (t0 >= 0 && t0 < snw) {
+                rl = (int)t0;
+            } else if (t0 >= snw && t0 < 2 * snw) {
+                rl = (int)(t0 - snw);
+            } else {
+                const int64_t m = t0 % snw;
+                rl = (int)(m < 0 ? m + snw : m);
+            }
+            auto next_row = [&]() -> const uint4 * {
+                const uint4 *lp = Ls + (uint64_t)rl * wst;
+                rl += dw;
+                while (rl >= sn) rl -= sn;
+                return lp;
+            };
+            uint4 lr[PF][2];
+#pragma unroll
+            for (int s = 0; s < PF; ++s) {
+                if (s < ns) {
+                    const uint4 *lp = next_row();
+                    lr[s][0] = __ldg(lp);
+                    lr[s][1] = __ldg(lp + W);
                 }
             }
-            const __half2 hh = *reinterpret_cast<__half2 *>(&hacc);
-            const float2 f2 = __half22float2(hh);
-            acc += f2.x + f2.y;
+            float v[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) v[i] = 0.f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                if (s < ns) {
+                    const uint4 l0 = lr[s % PF][0], l1 = lr[s % PF][1];
+                    if (s + PF < ns) {
+                        const uint4 *lp = next_row();
+                        lr[s % PF][0] = __ldg(lp);
+                        lr[s % PF][1] = __ldg(lp + W);
+                    }
+#pragma unroll
+                    for (int a = 0; a < A; ++a) {
+                        const int b = s - a;
+                        if (b >= 0 && b < B) {
+                            if (a < na && b < nb) v[a * B + b] = slide_pair(h[a], l0, l1, wv);
+                        }
+                    }
+                }
+            }
+            // recursive halving over the warp's pairs: level l adds the pair groups that differ in
+            // bit l of qlo (pair-sum order of the balanced tree); each lane keeps half the values
+#pragma unroll
+            for (int l = 0; (1 << l) < G::QL; ++l) {
+                const int n = V >> l, hh = n >> 1;
+                const bool up = (qlo >> l) & 1;
+#pragma unroll
+                for (int j = 0; j < hh; ++j) {
+                    const float send = up ? v[j] : v[j + hh];
+                    const float keep = up ? v[j + hh] : v[j];
+                    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, G::SPB << l);
+                }
+            }
+            auto emit = [&](int vi, int tt, float sum) {
+                const int a = vi / B, b = vi % B;
+                if (a < na && b < nb) {
+                    const float lg = sum + b2;
+                    out[(uint64_t)(pe.x + b) * slide_stride + (uint64_t)(wa + (int64_t)a * dw) * W + tb + tt] =
+                        logits ? lg : 1.f / (1.f + expf(-lg));
+                }
+            };
+            if constexpr (G::QH == 1) {
+#pragma unroll
+                for (int j = 0; j < VL; ++j) emit(voff + j, ts, v[j]);
+            } else {
+                // then across the warps: one thread per (value, sample) adds the QH partial sums
+#pragma unroll
+                for (int j = 0; j < VL; ++j) part[(qh * V + voff + j) * G::SPB + ts] = v[j];
+                __syncthreads();
+                for (int i = threadIdx.x; i < V * G::SPB; i += G::THREADS) {
+                    float x[G::QH];
+#pragma unroll
+                    for (int k = 0; k < G::QH; ++k) x[k] = part[k * V * G::SPB + i];
+                    emit(i / G::SPB, i % G::SPB, tree_sum<G::QH>(x));
+                }
+                __syncthreads();
+            }
         }
-        finish(si, acc);
+        wa += (int64_t)na * dw;
+      }
     }
 }
 
@@ -1196,11 +1302,12 @@ struct TcWork {
     }
 };
 
-// Launch shape of the slide heads: samples per block (64, 128 or 256) and offsets per block
-// (0: all offsets in one block).
+// Launch shape of the slide heads: Hanford windows per block (A), consecutive offsets per piece
+// (B: 4 or 8) and pieces per block (0: all pieces in one block).
 struct SlideShape {
-    int tile = 128;
-    int spb = 0;
+    int a = 4;
+    int b = 8;
+    int ppb = 0;
 };
 
 struct TcState {
@@ -1470,12 +1577,7 @@ cudaError_t set_tc_attr() {
                                  (int)TcShape<R, S, HC, false>::SMEM);
         if (e != cudaSuccess) return e;
     }
-    e = cudaFuncSetAttribute(k_slide_head<HC, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (HC / 8) * 64 * 16);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_slide_head<HC, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (HC / 8) * 128 * 16);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_slide_head<HC, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (HC / 8) * 256 * 16);
+    return cudaSuccess;
 }
 
 // Everything one forward needs on the device, prepared by setup_tc (buffers grown, tables
@@ -1488,12 +1590,36 @@ struct TcLaunch {
     int64_t nw = 0;
     int n_slides = 0;
     const int32_t *dsl = nullptr;
+    const int2 *dpieces[2] = {nullptr, nullptr};   // offset pieces of at most 4 / 8 offsets in step dwin
+    int n_pieces[2] = {0, 0};
+    int dwin = 1;
     const int64_t *d_w0 = nullptr;
     float *out = nullptr;
     bool logits = false;
     uint16_t *proj = nullptr;
     SlideShape shape;
 };
+
+// the slide-head shape of launches that are not autotuned (gwe_forward, gwe_forward_segments and
+// plans created without GWE_PLAN_AUTOTUNE)
+std::mutex g_plan_shape_mu;
+SlideShape g_plan_shape;
+
+// Window step of the slide heads' register blocking: the most common positive difference of
+// consecutive offsets (the smaller one on a tie), 1 when there is none or it is not below the
+// window count.
+int slide_step(const int32_t *k, int n, int64_t nw) {
+    std::map<int64_t, int> cnt;
+    for (int i = 1; i < n; ++i) {
+        const int64_t d = (int64_t)k[i] - k[i - 1];
+        if (d > 0 && d < nw && d <= (1 << 20)) ++cnt[d];
+    }
+    int64_t best = 1;
+    int nb = 0;
+    for (const auto &kv : cnt)
+        if (kv.second > nb) best = kv.first, nb = kv.second;
+    return (int)best;
+}
 
 template <int R, int S, int HC, bool F8>
 gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const float *sL, const Segments &sg,
@@ -1515,11 +1641,34 @@ gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const
     GWE_CUDA_TRY(wk.ring.ensure(n_rings * ring_cta * grid_max));
     // small host tables go up with cudaMemcpyAsync from pageable memory, which stages them before
     // returning; the slide offsets stay raw (they wrap within each window's segment on the device)
+    // The slide heads take the offsets in pieces of values in arithmetic progression with the list's
+    // most common positive step dwin (k, k + dwin, ...), at most 4 or 8 long: table [offsets, padded
+    // to 8 bytes][pieces of <= 4][pieces of <= 8], (first index, count).
     const int32_t *dsl = nullptr;
     if (n_slides > 0) {
-        GWE_CUDA_TRY(wk.koff.ensure(sizeof(int32_t) * n_slides));
-        GWE_CUDA_TRY(cudaMemcpyAsync(wk.koff.ptr, slides_host, sizeof(int32_t) * n_slides, cudaMemcpyHostToDevice, st));
+        L.dwin = slide_step(slides_host, n_slides, nw);
+        const int64_t dwin = L.dwin;
+        std::vector<int32_t> tab((size_t)n_slides + (n_slides & 1));
+        std::copy(slides_host, slides_host + n_slides, tab.begin());
+        const size_t pc_at = tab.size();
+        for (int bi = 0; bi < 2; ++bi) {
+            const int bmax = bi == 0 ? 4 : 8;
+            int np = 0;
+            for (int i = 0; i < n_slides;) {
+                int j = i + 1;
+                while (j < n_slides && j - i < bmax && (int64_t)slides_host[j] == (int64_t)slides_host[j - 1] + dwin) ++j;
+                tab.push_back(i);
+                tab.push_back(j - i);
+                ++np;
+                i = j;
+            }
+            L.n_pieces[bi] = np;
+        }
+        GWE_CUDA_TRY(wk.koff.ensure(sizeof(int32_t) * tab.size()));
+        GWE_CUDA_TRY(cudaMemcpyAsync(wk.koff.ptr, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, st));
         dsl = wk.koff.as<int32_t>();
+        L.dpieces[0] = reinterpret_cast<const int2 *>(dsl + pc_at);
+        L.dpieces[1] = L.dpieces[0] + L.n_pieces[0];
     }
     const int n_seg = (int)sg.s0.size();
     const int64_t *d_w0 = nullptr, *d_s0 = nullptr;
@@ -1578,6 +1727,10 @@ gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const
     L.grid_max = grid_max;
     L.grid_slide = (int)std::min<int64_t>(s.sms, nw);
     L.n_slides = n_slides;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_shape_mu);
+        L.shape = g_plan_shape;
+    }
     L.dsl = dsl;
     L.d_w0 = d_w0;
     L.out = out;
@@ -1592,13 +1745,18 @@ gwe_status setup_tc(gwe_model *m, TcState &s, TcWork &wk, const float *sH, const
     return GWE_OK;
 }
 
-template <int HC, int T>
+template <int HC, int A, int B>
 void launch_slide_head(const TcLaunch &L, const float *w2, const float *b2, float *out, cudaStream_t st) {
-    const int spb = L.shape.spb > 0 ? L.shape.spb : L.n_slides;
-    dim3 g2((unsigned)L.nw, (unsigned)(L.p.W / T), (unsigned)((L.n_slides + spb - 1) / spb));
-    k_slide_head<HC, T><<<g2, T, (HC / 8) * T * 16, st>>>(L.proj, L.nw, L.p.W, L.dsl, L.n_slides, spb, L.p.n_seg,
-                                                          L.d_w0, w2, b2, out, (int64_t)L.p.n_models * L.nw * L.p.W,
-                                                          L.logits ? 1 : 0);
+    using G = SlideGeo<HC>;
+    const int bi = B == 4 ? 0 : 1;
+    const int np = L.n_pieces[bi];
+    const int ppb = L.shape.ppb > 0 ? std::min(L.shape.ppb, np) : np;
+    const int64_t run = (int64_t)A * L.dwin;
+    dim3 g2((unsigned)((L.nw + run - 1) / run), (unsigned)(L.p.W / G::SPB), (unsigned)((np + ppb - 1) / ppb));
+    k_slide_head<HC, A, B><<<g2, G::THREADS, 0, st>>>(L.proj, L.nw, L.p.W, L.dsl, L.dpieces[bi], np, ppb, L.dwin,
+                                                       L.p.n_seg,
+                                                       L.d_w0, w2, b2, out, (int64_t)L.p.n_models * L.nw * L.p.W,
+                                                       L.logits ? 1 : 0);
 }
 
 // the slide heads of model mi (projections already in L.proj)
@@ -1611,10 +1769,12 @@ gwe_status issue_slide_heads(gwe_model *m, TcState &s, const TcLaunch &L, int mi
     const float *b2 = m->w32.as<float>() + (int64_t)mi * d.P + off_bh2(d);
     float *out = L.out + (int64_t)mi * L.nw * L.p.W;
     ProfScope prof("k_slide_head", st);
-    switch (L.shape.tile) {
-        case 64: launch_slide_head<HC, 64>(L, w2, b2, out, st); break;
-        case 256: launch_slide_head<HC, 256>(L, w2, b2, out, st); break;
-        default: launch_slide_head<HC, 128>(L, w2, b2, out, st); break;
+    if (L.shape.b == 8) {
+        if (L.shape.a == 2) launch_slide_head<HC, 2, 8>(L, w2, b2, out, st);
+        else launch_slide_head<HC, 4, 8>(L, w2, b2, out, st);
+    } else {
+        if (L.shape.a == 2) launch_slide_head<HC, 2, 4>(L, w2, b2, out, st);
+        else launch_slide_head<HC, 4, 4>(L, w2, b2, out, st);
     }
     note_launch();
     GWE_CUDA_TRY(cudaGetLastError());
@@ -2238,11 +2398,13 @@ gwe_status autotune_slides(gwe_model *m, TcState &s, PlanImpl &P, cudaStream_t s
     k_branch_tc<R, S, HC, F8><<<L.grid_slide, kThreads, Sh::SMEM, st>>>(q);
     GWE_CUDA_TRY(cudaGetLastError());
     std::vector<SlideShape> cands;
-    const int quarter = std::max(1, (L.n_slides + 3) / 4);
-    for (int tile : {64, 128, 256}) {
-        if (L.p.W % tile) continue;
-        cands.push_back(SlideShape{tile, 0});
-        if (quarter < L.n_slides) cands.push_back(SlideShape{tile, quarter});
+    for (int a : {2, 4}) {
+        for (int b : {4, 8}) {
+            cands.push_back(SlideShape{a, b, 0});
+            const int np = L.n_pieces[b == 4 ? 0 : 1];
+            const int quarter = std::max(1, (np + 3) / 4);
+            if (quarter < np) cands.push_back(SlideShape{a, b, quarter});
+        }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GWE_CUDA_TRY(cudaEventCreate(&e0));
@@ -2271,7 +2433,7 @@ gwe_status autotune_slides(gwe_model *m, TcState &s, PlanImpl &P, cudaStream_t s
             if (rep > 0) t_min = std::min(t_min, (double)ms);   // the first run warms up
         }
         if (r != GWE_OK) break;
-        if (c.tile == 128 && c.spb == 0) dflt = t_min;
+        if (c.a == 4 && c.b == 8 && c.ppb == 0) dflt = t_min;
         if (t_min < best) {
             best = t_min;
             best_shape = c;
@@ -2293,7 +2455,6 @@ gwe_status plan_build(gwe_model *m, TcState &s, PlanImpl &P, const float *sH, co
                       int W, int stride, const int32_t *slides, int n_slides, float *out, int flags, cudaStream_t st) {
     gwe_status r = setup_tc<R, S, HC, F8>(m, s, P.work, sH, sL, sg, W, stride, slides, n_slides, out, false, st, P.L);
     if (r != GWE_OK) return r;
-    P.L.shape = SlideShape();
     if ((flags & GWE_PLAN_AUTOTUNE) && n_slides > 0 && P.L.nw > 0) {
         r = autotune_slides<R, S, HC, F8>(m, s, P, st);
         if (r != GWE_OK) return r;
@@ -2397,16 +2558,28 @@ extern "C" gwe_status gwe_plan_execute(gwe_plan *plan, void *stream) {
     return GWE_OK;
 }
 
-extern "C" gwe_status gwe_plan_shape(const gwe_plan *plan, int *slide_tile, int *slides_per_block, int *n_kernels,
-                                     double *tuned_ms, double *default_ms) {
+extern "C" gwe_status gwe_plan_shape(const gwe_plan *plan, int *window_tile, int *offset_tile, int *pieces_per_block,
+                                     int *n_kernels, double *tuned_ms, double *default_ms) {
     clear_error();
     GWE_ARG_CHECK(plan != nullptr && plan->impl != nullptr, "plan is NULL");
     const gwe::PlanImpl &P = *plan->impl;
-    if (slide_tile) *slide_tile = P.L.shape.tile;
-    if (slides_per_block) *slides_per_block = P.L.shape.spb > 0 ? P.L.shape.spb : P.L.n_slides;
+    const int np = P.L.n_pieces[P.L.shape.b == 4 ? 0 : 1];
+    if (window_tile) *window_tile = P.L.shape.a;
+    if (offset_tile) *offset_tile = P.L.shape.b;
+    if (pieces_per_block) *pieces_per_block = P.L.shape.ppb > 0 ? std::min(P.L.shape.ppb, np) : np;
     if (n_kernels) *n_kernels = P.n_kernels;
     if (tuned_ms) *tuned_ms = P.tuned_ms;
     if (default_ms) *default_ms = P.default_ms;
+    return GWE_OK;
+}
+
+extern "C" gwe_status gwe_set_slide_shape(int window_tile, int offset_tile, int pieces_per_block) {
+    clear_error();
+    GWE_ARG_CHECK(window_tile == 2 || window_tile == 4, "window_tile must be 2 or 4");
+    GWE_ARG_CHECK(offset_tile == 4 || offset_tile == 8, "offset_tile must be 4 or 8");
+    GWE_ARG_CHECK(pieces_per_block >= 0, "pieces_per_block must be >= 0");
+    std::lock_guard<std::mutex> lk(gwe::g_plan_shape_mu);
+    gwe::g_plan_shape = gwe::SlideShape{window_tile, offset_tile, pieces_per_block};
     return GWE_OK;
 }
 

@@ -170,17 +170,116 @@ def replay(R, S, HC, f8, stacks, lps, W, stride, n, n_models, slides, sms=152, r
                                     inside(pw + ((ch // 8 + 1) * W + t0 + r) * 8, 8, proj_alloc, "projection store")
                         elif b == 0:
                             inside(((m - la["model0"]) * nw + w) * W + t0, KT, out_alloc, "probability store")
-    # slide heads: block (w, tile, offset group); Hanford rows of window w, Livingston rows of (w + k) mod nw
+    # slide heads: every launch shape the autotuner can choose
     if n_sl:
-        bstride = nw * HC * W
-        for w in range(nw):
-            for k in slides:
-                wl = (w + k) % nw
-                inside(w * HC * W, HC * W, proj_alloc, "Hanford projections")
-                inside(bstride + wl * HC * W, HC * W, proj_alloc, "Livingston projections")
-            for si in range(n_sl):
-                for mi in range(n_models):
-                    inside(mi * nw * W + si * (n_models * nw * W) + w * W, W, out_alloc, "slide-head store")
+        for A, B, ppb in SLIDE_SHAPES:
+            checks += replay_slide_heads(HC, W, [nw], n_models, slides, A, B, ppb, proj_alloc, out_alloc)
+    return checks
+
+
+# (Hanford windows per block, offsets per piece, pieces per block; 0 = all, -1 = a quarter)
+SLIDE_SHAPES = [(a, b, ppb) for a in (2, 4) for b in (4, 8) for ppb in (0, -1)]
+
+
+def slide_step(slides, nw):
+    """The offsets' most common positive step (smaller on a tie), 1 when none is below nw."""
+    cnt = {}
+    for a, b in zip(slides[:-1], slides[1:]):
+        d = b - a
+        if 0 < d < nw and d <= 1 << 20:
+            cnt[d] = cnt.get(d, 0) + 1
+    best, nb = 1, 0
+    for d in sorted(cnt):
+        if cnt[d] > nb:
+            best, nb = d, cnt[d]
+    return best
+
+
+def slide_pieces(slides, bmax, step=1):
+    """Pieces of offsets in arithmetic progression with `step` (first index, count), at most bmax long,
+    as the host builds them."""
+    out, i, n = [], 0, len(slides)
+    while i < n:
+        j = i + 1
+        while j < n and j - i < bmax and slides[j] == slides[j - 1] + step:
+            j += 1
+        out.append((i, j - i))
+        i = j
+    return out
+
+
+def replay_slide_heads(HC, W, seg_nw, n_models, slides, A, B, ppb, proj_alloc, out_alloc):
+    """Walk the slide heads' loads and stores for one launch shape (all models); returns the count.
+
+    Block (x, y, z): windows [x A dw, (x + 1) A dw) taken per residue mod dw in passes of windows
+    wa + a dw that stay within one segment, samples [y SPW, y SPW + SPW), pieces [z ppb, z ppb + ppb).
+    Each thread reads chunks 2q and 2q + 1 of the Hanford windows and of the Livingston windows
+    (r0 + s dw) mod n_seg_w, s < na + nb - 1, and the block stores (slide first + b, window
+    wa + a dw) for a < na, b < nb.  Every window of every slide is stored exactly once."""
+    NP = HC // 16
+    SPW = 32 // min(NP, 4)                  # samples per block (pairs per warp x samples = 32 lanes)
+    nw = int(sum(seg_nw))
+    seg_w0 = np.concatenate([[0], np.cumsum(seg_nw)]).astype(np.int64)
+    dw = slide_step(slides, nw)
+    pieces = slide_pieces(slides, B, dw)
+    np_ = len(pieces)
+    if ppb == -1:
+        ppb = max(1, (np_ + 3) // 4)
+    ppb = min(ppb, np_) if ppb > 0 else np_
+    wst = HC * W // 8                      # 16-byte chunks per window
+    alloc16 = proj_alloc // 8               # the projections in 16-byte chunks
+    slide_stride = n_models * nw * W
+    checks = 0
+    ys = sorted({0, W // SPW - 1})
+    zs = range((np_ + ppb - 1) // ppb)
+
+    def load(chunk_index):
+        nonlocal checks
+        checks += 1
+        assert 0 <= chunk_index < alloc16, ("slide-head load", chunk_index, alloc16)
+
+    stored = np.zeros((len(slides), nw), dtype=np.int64)
+    for mi in range(n_models):
+        for x in range((nw + A * dw - 1) // (A * dw)):
+            wrun, wend = x * A * dw, min(nw, (x + 1) * A * dw)
+            for rho in range(dw):
+                wa = wrun + rho
+                while wa < wend:
+                    g = int(np.searchsorted(seg_w0, wa, side="right") - 1)
+                    sw0, snw = int(seg_w0[g]), int(seg_w0[g + 1] - seg_w0[g])
+                    na = (min(wend, sw0 + snw) - wa + dw - 1) // dw
+                    assert 1 <= na <= A
+                    assert wa + (na - 1) * dw < sw0 + snw          # the pass stays in its segment
+                    for y in ys:
+                        for q in (0, NP - 1):
+                            base = 2 * q * W + y * SPW
+                            for ts in (0, SPW - 1):
+                                for a in range(na):
+                                    load((wa + a * dw) * wst + base + ts)
+                                    load((wa + a * dw) * wst + base + W + ts)
+                        for z in zs:
+                            for pc in range(z * ppb, min(np_, z * ppb + ppb)):
+                                i0, nb = pieces[pc]
+                                r0 = (wa - sw0 + slides[i0]) % snw
+                                for s in range(na + nb - 1):
+                                    wl = sw0 + (r0 + s * dw) % snw
+                                    # the Livingston window of pair (a, s - a) is the plain definition's
+                                    for a in range(max(0, s - nb + 1), min(na, s + 1)):
+                                        b = s - a
+                                        assert wl == sw0 + (wa + a * dw - sw0 + slides[i0 + b]) % snw
+                                    for q in (0, NP - 1):
+                                        base = nw * wst + wl * wst + 2 * q * W + y * SPW
+                                        load(base)
+                                        load(base + W + SPW - 1)
+                                for a in range(na):
+                                    for b in range(nb):
+                                        o = mi * nw * W + (i0 + b) * slide_stride + (wa + a * dw) * W + y * SPW
+                                        checks += 1
+                                        assert 0 <= o and o + SPW <= out_alloc, ("slide-head store", o, out_alloc)
+                                        if mi == 0 and y == 0:
+                                            stored[i0 + b, wa + a * dw] += 1
+                    wa += na * dw
+    assert np.all(stored == 1), "every (slide, window) stored exactly once"
     return checks
 
 
@@ -221,3 +320,30 @@ def test_replay_catches_undersized_allocations():
         replay(R, S, HC, False, stacks, lps, W, stride, n16, nm, None, sms=8, ring_short=128)
     with pytest.raises(AssertionError):
         replay(R, S, HC, False, stacks, lps, W, stride, n, nm, slides, proj_short=1)
+
+
+@pytest.mark.parametrize("A,B,ppb", SLIDE_SHAPES)
+def test_slide_heads_on_uneven_segments(A, B, ppb):
+    """Segments of 1, 3, 6 and 13 windows (tiles straddle the boundaries), offsets with runs, gaps,
+    negative values and offsets larger than a segment."""
+    HC, W, nm = 256, 1024, 2
+    seg_nw = [13, 1, 6, 3]
+    slides = [1, 2, 3, 4, 5, 9, -3, -2, 0, 40, 41, 7]
+    nw = sum(seg_nw)
+    for sl in (slides, [2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 3, -7], [3, 6, 9, 12, 0]):
+        replay_slide_heads(256, W, seg_nw, nm, sl, A, B, ppb, 2 * nw * 256 * W, len(sl) * nm * nw * W)
+    nw = sum(seg_nw)
+    got = replay_slide_heads(HC, W, seg_nw, nm, slides, A, B, ppb, 2 * nw * HC * W, len(slides) * nm * nw * W)
+    assert got > 0
+    with pytest.raises(AssertionError):
+        replay_slide_heads(HC, W, seg_nw, nm, slides, A, B, ppb, 2 * nw * HC * W - 8, len(slides) * nm * nw * W)
+
+
+def test_slide_pieces():
+    assert slide_pieces([1, 2, 3, 4, 5, 9, -3, -2, 0], 4) == [(0, 4), (4, 1), (5, 1), (6, 2), (8, 1)]
+    assert slide_pieces(list(range(1, 65)), 8) == [(8 * i, 8) for i in range(8)]
+    assert slide_pieces([], 4) == []
+    offs = [2 * (k + 1) for k in range(64)]                 # 1 .. 64 s at 0.5 s stride
+    assert slide_step(offs, 7199) == 2
+    assert slide_pieces(offs, 4, 2) == [(4 * i, 4) for i in range(16)]
+    assert slide_step([5, 1, 3], 100) == 2 and slide_step([4, 1], 100) == 1 and slide_step([1, 50], 40) == 1

@@ -50,8 +50,8 @@ def test_plan_equals_segments_forward(prec):
     plan = gwe.gwe_plan_create(m.handle, th, tl, starts, lens, W, STRIDE, slides, out, gwe.GWE_PLAN_AUTOTUNE)
     try:
         info = gwe.gwe_plan_shape(plan)
-        assert info["slide_tile"] in (64, 128, 256)
-        assert 1 <= info["slides_per_block"] <= len(slides)
+        assert info["window_tile"] in (2, 4) and info["offset_tile"] in (4, 8)
+        assert 1 <= info["pieces_per_block"] <= len(slides)
         assert info["n_kernels"] == 2 * cfg["n_models"]       # per model: branch pass + slide heads
         assert info["tuned_ms"] > 0 and info["tuned_ms"] <= info["default_ms"] * 1.0001
         gwe.gwe_plan_execute(plan)
@@ -84,41 +84,115 @@ def test_plan_equals_segments_forward(prec):
 
 
 def test_every_candidate_shape_gives_the_same_output():
-    """The shapes the autotuner chooses from are all exact: force each by planning without tuning
-    after seeding the process cache is impossible from outside, so compare the tuned plan and the
-    untuned (default-shape) plan with a geometry whose candidates differ."""
+    """Every slide-head launch shape the autotuner chooses from computes the same sums in the same
+    order: plans forced to each shape equal gwe_forward_segments bit for bit, on segments whose window
+    tiles straddle the segment boundaries, with offsets in runs of step 1 and 2, gaps, negative
+    offsets and offsets longer than a segment; then the oracle on the first segment's slid windows."""
     import torch
     import paper_2201_11133_gb300 as gwe
     dev = require_gpu()
     cfg = workload.config("small")
     Ws, Ss = 1024, 512
-    lens = np.array([Ws + 30 * Ss, Ws + 7 * Ss + 100, Ws], dtype=np.int64)
-    starts = np.array([0, int(lens[0]) + 50, int(lens[0] + lens[1]) + 99], dtype=np.int64)
+    lens = np.array([Ws + 30 * Ss, Ws + 7 * Ss + 100, Ws, Ws + 2 * Ss], dtype=np.int64)
+    starts = np.array([0, int(lens[0]) + 50, int(lens[0] + lens[1]) + 99, int(lens[:3].sum()) + 200],
+                      dtype=np.int64)
     n = int(starts[-1] + lens[-1])
     sh, sl, _ = workload.stream(n, seed=79)
     wb = workload.init_weights(cfg, seed=3000, bias_std=0.1)
     m = gwe.Model(cfg, wb, gwe.GWE_BF16)
     th, tl = torch.from_numpy(sh).to(dev), torch.from_numpy(sl).to(dev)
     nws = gwe.segment_windows(lens, Ws, Ss)
-    slides = list(range(1, 14))
-    shape = (len(slides), 1, int(nws.sum()), Ws)
-    a = torch.empty(shape, dtype=torch.float32, device=dev)
-    b = torch.empty(shape, dtype=torch.float32, device=dev)
-    pa = gwe.gwe_plan_create(m.handle, th, tl, starts, lens, Ws, Ss, slides, a, gwe.GWE_PLAN_AUTOTUNE)
-    pb = gwe.gwe_plan_create(m.handle, th, tl, starts, lens, Ws, Ss, slides, b, 0)
-    try:
-        assert gwe.gwe_plan_shape(pb)["slide_tile"] == 128
-        gwe.gwe_plan_execute(pa)
-        gwe.gwe_plan_execute(pb)
+    slide_sets = [list(range(1, 14)), [2, 4, 6, 8, 10, 12, 14, 16, 18, 3, -5, 0, 40, 41]]
+    for slides in slide_sets:
+        shape = (len(slides), 1, int(nws.sum()), Ws)
+        ref = torch.empty(shape, dtype=torch.float32, device=dev)
+        gwe.gwe_forward_segments(m.handle, th, tl, starts, lens, Ws, Ss, slides, ref)
         m.sync()
-        assert torch.equal(a, b)
+        try:
+            for a in (2, 4):
+                for b in (4, 8):
+                    for ppb in (0, 1, 3):
+                        gwe.gwe_set_slide_shape(a, b, ppb)
+                        out = torch.full(shape, -1.0, dtype=torch.float32, device=dev)
+                        plan = gwe.gwe_plan_create(m.handle, th, tl, starts, lens, Ws, Ss, slides, out, 0)
+                        try:
+                            info = gwe.gwe_plan_shape(plan)
+                            assert (info["window_tile"], info["offset_tile"]) == (a, b)
+                            gwe.gwe_plan_execute(plan)
+                            m.sync()
+                            assert torch.equal(out, ref), (slides, a, b, ppb)
+                        finally:
+                            gwe.gwe_plan_destroy(plan)
+        finally:
+            gwe.gwe_set_slide_shape(4, 8, 0)
         # and the oracle on the whole batch of slid windows of the first segment, model 0
-        ref = oracle.forward_stream(cfg, wb, sh[:lens[0]], sl[:lens[0]], Ws, Ss, slides=slides)
-        got = a[:, :, :int(nws[0])].cpu().numpy().astype(np.float64)
-        assert np.max(np.abs(got - ref)) <= 1e-2
+        ref_o = oracle.forward_stream(cfg, wb, sh[:lens[0]], sl[:lens[0]], Ws, Ss, slides=slides)
+        got = ref[:, :, :int(nws[0])].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(got - ref_o)) <= 1e-2
+    # the tuned plan picks one of the candidates and gives the same output
+    slides = slide_sets[1]
+    shape = (len(slides), 1, int(nws.sum()), Ws)
+    ref = torch.empty(shape, dtype=torch.float32, device=dev)
+    gwe.gwe_forward_segments(m.handle, th, tl, starts, lens, Ws, Ss, slides, ref)
+    out = torch.empty(shape, dtype=torch.float32, device=dev)
+    plan = gwe.gwe_plan_create(m.handle, th, tl, starts, lens, Ws, Ss, slides, out, gwe.GWE_PLAN_AUTOTUNE)
+    try:
+        gwe.gwe_plan_execute(plan)
+        m.sync()
+        assert torch.equal(out, ref)
     finally:
-        gwe.gwe_plan_destroy(pa)
-        gwe.gwe_plan_destroy(pb)
+        gwe.gwe_plan_destroy(plan)
+    with pytest.raises(gwe.GweError):
+        gwe.gwe_set_slide_shape(3, 4, 0)
+    with pytest.raises(gwe.GweError):
+        gwe.gwe_set_slide_shape(4, 5, 0)
+
+
+def test_every_candidate_shape_ensemble_width():
+    """The same for the 256-channel head (four warps per block, shared-memory reduction)."""
+    import torch
+    import paper_2201_11133_gb300 as gwe
+    dev = require_gpu()
+    cfg = workload.config("ensemble", n_models=1)
+    lens = np.array([W + 21 * STRIDE, W + 2 * STRIDE + 7, W + 9 * STRIDE], dtype=np.int64)
+    starts = np.array([0, int(lens[0]) + 10, int(lens[:2].sum()) + 20], dtype=np.int64)
+    n = int(starts[-1] + lens[-1])
+    sh, sl, _ = workload.stream(n, seed=80)
+    wb = workload.init_weights(cfg, seed=3000, bias_std=0.05)
+    m = gwe.Model(cfg, wb, gwe.GWE_BF16)
+    th, tl = torch.from_numpy(sh).to(dev), torch.from_numpy(sl).to(dev)
+    nws = gwe.segment_windows(lens, W, STRIDE)
+    slides = [2 * (k + 1) for k in range(11)] + [1, -3, 30]
+    shape = (len(slides), 1, int(nws.sum()), W)
+    ref = torch.empty(shape, dtype=torch.float32, device=dev)
+    gwe.gwe_forward_segments(m.handle, th, tl, starts, lens, W, STRIDE, slides, ref)
+    m.sync()
+    try:
+        for a in (2, 4):
+            for b in (4, 8):
+                for ppb in (0, 2):
+                    gwe.gwe_set_slide_shape(a, b, ppb)
+                    out = torch.full(shape, -1.0, dtype=torch.float32, device=dev)
+                    plan = gwe.gwe_plan_create(m.handle, th, tl, starts, lens, W, STRIDE, slides, out, 0)
+                    try:
+                        gwe.gwe_plan_execute(plan)
+                        m.sync()
+                        assert torch.equal(out, ref), (a, b, ppb)
+                    finally:
+                        gwe.gwe_plan_destroy(plan)
+    finally:
+        gwe.gwe_set_slide_shape(4, 8, 0)
+    # a sampled slid window of the last segment against the oracle
+    g, si = 2, 3
+    w = int(nws[g]) - 1
+    k = slides[si]
+    wl = (w + k) % int(nws[g])
+    s0 = int(starts[g])
+    xh = sh[None, s0 + w * STRIDE:s0 + w * STRIDE + W].astype(np.float64)
+    xl = sl[None, s0 + wl * STRIDE:s0 + wl * STRIDE + W].astype(np.float64)
+    lg = oracle.forward_windows(cfg, wb[0], xh, xl)
+    got = ref[si, 0, int(nws[:g].sum()) + w].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - sigmoid(lg[0]))) <= 1e-2
 
 
 def test_zero_lag_plan_and_bad_arguments():
