@@ -984,7 +984,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_branch_tc(const TcParams p) {
                             *reinterpret_cast<uint4 *>(pw + ((uint64_t)(ch / 8 + 1) * p.W + t0 + r) * 8) = v1;
                         }
                     }
+                    // P overlaps the skip columns: no thread restores the next tile's carried skip sum
+                    // (cross-window reuse) before every thread of both branches has read its P
                     tc_fence_before();
+                    warp_arrive(B_PAIR);
+                    if (!warp_wait(B_PAIR, ph_pair & 1, 34)) { ok = false; break; }
+                    ++ph_pair;
                     continue;
                 }
                 float acc = 0.f;
