@@ -395,13 +395,18 @@ def training_roofline(cfg1, B, W, kernels, peaks, peak_kind):
     step.  Algorithmic bytes per row (one sample of one branch) and layer, with the stack inputs
     and skip sums taken from the fused forward (BF16 handles, W a multiple of 128): recomputed
     conv 8R (x in, gate cache and z out), residual 12R (z, x in; x FP32 and BF16 out), dz 10R + 2S
-    (dL/dx, dL/dskip, gate cache in; da out), dgrad 14R (da, dL/dx in; dL/dx FP32 and BF16 out)."""
+    (dL/dx, dL/dskip, gate cache in; da out), dgrad 14R (da, dL/dx in; dL/dx FP32 and BF16 out).
+    The head's two row GEMMs (timed as k_tc_rows:head_u and k_tc_rows:head_dh) are not counted."""
     kr = kernels.get("k_tc_rows")
     if not kr or kr["ms_per_step"] <= 0:
         return None
+    ms = kr["ms_per_step"] - sum(kernels.get(k, {}).get("ms_per_step", 0.0)
+                                 for k in ("k_tc_rows:head_u", "k_tc_rows:head_dh"))
+    if ms <= 0:
+        return None
     R, S, L = cfg1["r_ch"], cfg1["s_ch"], workload.n_layers(cfg1)
     bytes_step = 2 * B * W * L * (44 * R + 2 * S)
-    ach = bytes_step / (kr["ms_per_step"] / 1000.0) / 1e9
+    ach = bytes_step / (ms / 1000.0) / 1e9
     return {"kernel": "k_tc_rows", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": ach / peaks["hbm_gbs"], "peak_source": f"of {peak_kind}", "bytes_per_step": bytes_step}
 

@@ -7,8 +7,12 @@ module states the reading the tensor-core backward implements: FP64 arithmetic
 everywhere, except that the two operands of every contraction of the branches
 (the dilated convolution, the residual and skip projections, and in the
 backward the dz, dgrad and weight-gradient contractions) are rounded to BF16
-(round to nearest even) first.  The head, the biases, the input projection and
-every elementwise step are exact.  With rounding switched off it is the plain
+(round to nearest even) first.  The head's contractions take their operands
+rounded as the kernels do: u = h . W_h1^T from FP16 h and W_h1 (the forward
+kernel's head operands), dh = du . W_h1 from BF16 du and W_h1, and
+dW_h1 = du^T h from the BF16 splits x = hi + lo (hi = BF16(x), lo = BF16(x - hi))
+of du and h as hi.hi + hi.lo + lo.hi.  The biases, the input projection and every elementwise step are
+exact.  With rounding switched off it is the plain
 reverse-mode gradient of the network (pinned against the C oracle's
 `backward`, which is pinned by finite differences).
 
@@ -31,6 +35,11 @@ def bf16_round(x) -> np.ndarray:
     return out
 
 
+def f16_round(x) -> np.ndarray:
+    """Round to the nearest FP16 value, ties to even (float64 in, float64 out)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
 def _lag(x, s, W):
     """Row t of the result is row t + s of x within each window (zero outside [0, W)); x [B, W, C]."""
     out = np.zeros_like(x)
@@ -48,6 +57,7 @@ def backward(cfg, offsets, blob, xh, xl, dlogit, rounding: bool = True):
 
     offsets: {name: (offset, shape)} of the blob (workload.param_offsets)."""
     q = bf16_round if rounding else (lambda v: np.asarray(v, dtype=np.float64))
+    q16 = f16_round if rounding else (lambda v: np.asarray(v, dtype=np.float64))
     R, S = int(cfg["r_ch"]), int(cfg["s_ch"])
     lps = int(cfg["layers_per_stack"])
     L = int(cfg["stacks"]) * lps
@@ -79,15 +89,17 @@ def backward(cfg, offsets, blob, xh, xl, dlogit, rounding: bool = True):
             x = x + zq @ q(par(f"{br}.{l}.w_res")).T + par(f"{br}.{l}.b_res")
             skip = skip + zq @ q(par(f"{br}.{l}.w_skip")).T + par(f"{br}.{l}.b_skip")
         saved[br], skips[br] = keep, skip
-    # head (exact)
+    # head: u from FP16 operands, dh from BF16 operands, dW_h1 from BF16 hi/lo splits
     h = np.concatenate([np.maximum(skips["H"], 0.0), np.maximum(skips["L"], 0.0)], -1)
-    u = h @ par("w_h1").T + par("b_h1")
+    u = q16(h) @ q16(par("w_h1")).T + par("b_h1")
     du = dlogit[..., None] * par("w_h2") * (u > 0)
     grad["w_h2"] = np.einsum("bt,btj->j", dlogit, np.maximum(u, 0.0))
     grad["b_h2"] = np.array([dlogit.sum()])
-    grad["w_h1"] = np.einsum("btj,btk->jk", du, h)
+    lo = lambda v: q(v - q(v))
+    grad["w_h1"] = (np.einsum("btj,btk->jk", q(du), q(h)) + np.einsum("btj,btk->jk", q(du), lo(h)) +
+                    np.einsum("btj,btk->jk", lo(du), q(h)))
     grad["b_h1"] = du.sum((0, 1))
-    dh = du @ par("w_h1")
+    dh = q(du) @ q(par("w_h1"))
     dstrain = []
     for bi, (br, s) in enumerate((("H", xh), ("L", xl))):
         dskip = dh[..., bi * S:(bi + 1) * S] * (skips[br] > 0)

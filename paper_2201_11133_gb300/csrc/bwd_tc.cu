@@ -51,7 +51,9 @@ struct RowSeg {
     int shift;
 };
 
-enum { EPI_CONV = 0, EPI_RES = 1, EPI_DZ = 2, EPI_DGRAD = 3 };
+// EPI_HEAD_U: u = [h_H | h_L] . W_h1^T (N = Hc, K = 2S), du = (u + b_h1 > 0) ? dlogit w_h2 : 0, ReLU(u + b_h1);
+// EPI_HEAD_DH: dh = du . W_h1 (N = 2S, K = Hc), dskip_b = (h_b > 0) ? dh_b : 0 (thread half = branch)
+enum { EPI_CONV = 0, EPI_RES = 1, EPI_DZ = 2, EPI_DGRAD = 3, EPI_HEAD_U = 4, EPI_HEAD_DH = 5 };
 
 struct RowGemm {
     RowSeg seg[2];
@@ -81,6 +83,9 @@ struct RowGemm {
     float *skip;                      // EPI_RES with N > R: skip sum [row][S] (accumulated)
     int64_t skip_boff;
     int skip_init;                    // 1: skip = q + b_skip (first layer)
+    const __nv_bfloat16 *mask16;      // EPI_HEAD_DH: h = ReLU(skip) [branch][row][S] (BF16)
+    __nv_bfloat16 *o16_lo;            // EPI_HEAD_U: du - BF16(du) in BF16
+    int64_t mask_boff;
 };
 
 struct WgGemm {
@@ -97,6 +102,7 @@ struct WgGemm {
     int ldw;
     int64_t w_boff;
     float *db;                        // or null: db[m] += sum over rows of G[row][m] (column nx of X is 1)
+    int db_nb;                        // branches that add their sums to db (at db + b * w_boff); 0 = all
     int nx;                           // columns of X from the segments (N = nx, or nx + 16 with db)
     int *err;
 };
@@ -107,7 +113,11 @@ __device__ __forceinline__ uint32_t tmem_cols_for(int n) {
     return c;
 }
 
-__device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // 16-byte global -> shared copy in flight until cp_async_wait_all; zero-filled when !valid
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
@@ -219,7 +229,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
     if (blockIdx.x < p.n_tiles) issue_tile(blockIdx.x);
     uint32_t ph = 0;
     bool ok = true;
-    const uint32_t idesc = idesc_f16(128, p.N, 1);
+    const uint32_t idesc = idesc_f16(128, p.N, EPI == EPI_HEAD_U ? 0 : 1);   // u: FP16 operands, else BF16
     const int R = p.R, hr = R / 2, ch0 = h * hr;   // this thread's channels [ch0, ch0 + hr), hr <= 32
     const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     for (int64_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
@@ -280,10 +290,11 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
                 tmem_ld_wait();
                 if (!live) continue;
                 float th[16], sg[16], z[16];
+                // the forward kernel's gate arithmetic: tanh.approx, and sigmoid(g) = 0.5 tanh(g/2) + 0.5
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    th[j] = tanhf(__uint_as_float(fr[j]) + __ldg(bc + c0 + j));
-                    sg[j] = sigm(__uint_as_float(gr[j]) + __ldg(bc + R + c0 + j));
+                    th[j] = tanh_approx(__uint_as_float(fr[j]) + __ldg(bc + c0 + j));
+                    sg[j] = fmaf(tanh_approx(0.5f * (__uint_as_float(gr[j]) + __ldg(bc + R + c0 + j))), 0.5f, 0.5f);
                     z[j] = th[j] * sg[j];
                 }
                 if (p.gate_out) {   // the backward's gate cache: tanh(f), sigmoid(g) in FP16
@@ -378,6 +389,50 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
                 __nv_bfloat16 *d16 = p.o16 + b * p.o16_boff + row * 2 * R;
                 st16_bf16(d16 + c0, df);
                 st16_bf16(d16 + R + c0, dg);
+            }
+        } else if (EPI == EPI_HEAD_U) {
+            // this thread's u channels [h N/2, h N/2 + N/2) of its row
+            const int hn = p.N / 2, u0 = h * hn;
+            const float dl = live ? __ldg(p.aux + row) : 0.f;
+            for (int g = 0; g < hn / 16; ++g) {
+                const int c0 = u0 + 16 * g;
+                uint32_t ur[16];
+                tmem_ld16(tl + c0, ur);
+                tmem_ld_wait();
+                if (!live) continue;
+                float du[16], ru[16], lo[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float u = __uint_as_float(ur[j]) + __ldg(p.bias + c0 + j);
+                    du[j] = u > 0.f ? dl * __ldg(p.bias2 + c0 + j) : 0.f;
+                    ru[j] = fmaxf(u, 0.f);
+                    lo[j] = du[j] - __bfloat162float(__float2bfloat16_rn(du[j]));
+                }
+                st16_bf16(p.o16 + row * p.N + c0, du);
+                st16_bf16(p.o16_lo + row * p.N + c0, lo);
+                st16_f32(p.o32 + row * p.N + c0, ru);
+            }
+        } else if (EPI == EPI_HEAD_DH) {
+            // thread half h = branch h: dskip_h[row][c] for c < S = N / 2
+            const int S = p.N / 2;
+            for (int g = 0; g < S / 16; ++g) {
+                const int c0 = 16 * g;
+                uint32_t dr[16];
+                tmem_ld16(tl + h * S + c0, dr);
+                tmem_ld_wait();
+                if (!live) continue;
+                const __nv_bfloat16 *mk = p.mask16 + h * p.mask_boff + row * S + c0;
+                const uint4 m0 = *reinterpret_cast<const uint4 *>(mk), m1 = *reinterpret_cast<const uint4 *>(mk + 8);
+                const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float2 hv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&mw[q]));
+                    v[2 * q] = hv.x > 0.f ? __uint_as_float(dr[2 * q]) : 0.f;
+                    v[2 * q + 1] = hv.y > 0.f ? __uint_as_float(dr[2 * q + 1]) : 0.f;
+                }
+                st16_f32(p.o32 + h * p.o32_boff + row * S + c0, v);
+                st16_bf16(p.o16 + h * p.o16_boff + row * S + c0, v);
             }
         } else {   // EPI_DGRAD
 #pragma unroll
@@ -539,7 +594,7 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
                 for (int j = 0; j < 16; ++j) {
                     if (c0 + j < p.nx)
                         atomicAdd(dw + j, __uint_as_float(v[j]));
-                    else if (c0 + j == p.nx && p.db)
+                    else if (c0 + j == p.nx && p.db && (p.db_nb == 0 || b < p.db_nb))
                         atomicAdd(p.db + b * p.w_boff + m, __uint_as_float(v[j]));
                 }
             }
@@ -551,6 +606,40 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
         tc_fence_after();
         tmem_dealloc(tmem, NCOLS);
     }
+}
+
+// h = ReLU(skip) (skip: the pre-ReLU skip sums with their biases, both branches) in FP16, the
+// forward kernel's head operand, and in BF16 (hi, and lo = BF16(h - hi)), the weight-gradient
+// operands; hi is also the dskip mask
+__global__ void k_relu_h(const float *__restrict__ in, __half *__restrict__ hf, __nv_bfloat16 *__restrict__ hb,
+                         __nv_bfloat16 *__restrict__ hb_lo, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = reinterpret_cast<const float4 *>(in)[i];
+        const float a0 = fmaxf(v.x, 0.f), a1 = fmaxf(v.y, 0.f), a2 = fmaxf(v.z, 0.f), a3 = fmaxf(v.w, 0.f);
+        const __half2 f0 = __floats2half2_rn(a0, a1), f1 = __floats2half2_rn(a2, a3);
+        const __nv_bfloat162 b0 = __floats2bfloat162_rn(a0, a1), b1 = __floats2bfloat162_rn(a2, a3);
+        reinterpret_cast<uint2 *>(hf)[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&f0),
+                                                      *reinterpret_cast<const uint32_t *>(&f1));
+        reinterpret_cast<uint2 *>(hb)[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&b0),
+                                                      *reinterpret_cast<const uint32_t *>(&b1));
+        // the rounding remainders h - BF16(h), in BF16 (the lo term of the weight gradient's split)
+        const float2 r0 = __bfloat1622float2(b0), r1 = __bfloat1622float2(b1);
+        const __nv_bfloat162 l0 = __floats2bfloat162_rn(a0 - r0.x, a1 - r0.y), l1 = __floats2bfloat162_rn(a2 - r1.x, a3 - r1.y);
+        reinterpret_cast<uint2 *>(hb_lo)[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&l0),
+                                                         *reinterpret_cast<const uint32_t *>(&l1));
+    }
+}
+
+// B images of the head's first convolution W_h1 [Hc][2S] (chunk-column layout): the u image
+// [Hc rows: u channel j][2S K: h channel c] in FP16 (the forward kernel's head operands) and the dh
+// image [2S rows: c][Hc K: j] in BF16
+__global__ void k_pack_head(const float *__restrict__ w1, int Hc, int S2, __half *__restrict__ u_img,
+                            __nv_bfloat16 *__restrict__ dh_img) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)Hc * S2) return;
+    const int j = (int)(e / S2), c = (int)(e % S2);
+    u_img[((size_t)(c / 8) * Hc * 16 + (size_t)j * 16 + (c % 8) * 2) / 2] = __float2half_rn(w1[e]);
+    dh_img[((size_t)(j / 8) * S2 * 16 + (size_t)c * 16 + (j % 8) * 2) / 2] = __float2bfloat16_rn(w1[e]);
 }
 
 __global__ void k_f32_to_bf16(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, int64_t n) {
@@ -572,6 +661,7 @@ struct TcBwd {
     int model = -1;
     uint64_t stamp = 0;
     DevBuf xsave, skip, dskip32, dskip16, x32, x16, gate16, z16, dx32[2], dx16[2], da16, err;
+    DevBuf head_img, hf16, hb16, hblo16, du16, dulo16, ru32;   // tensor-core head backward
 };
 
 __host__ __device__ inline size_t choff(int rows, int n, int k) { return (size_t)(k / 8) * rows * 16 + (size_t)n * 16 + (k % 8) * 2; }
@@ -634,6 +724,8 @@ gwe_status set_attrs() {
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_DZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_HEAD_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_HEAD_DH>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<80>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<144>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -660,7 +752,10 @@ gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
     // share an SM and no TMEM allocation has to wait
     const size_t smem = std::max<size_t>((size_t)kRows * p.K * 2 + (size_t)p.bn * p.K * 2 + 128, 80 * 1024);
     const int grid = (int)std::min<int64_t>(p.n_tiles, (int64_t)sms * (smem <= 100 * 1024 ? 2 : 1));
+    static const char *const kEpiName[6] = {"k_tc_rows:conv", "k_tc_rows:res",    "k_tc_rows:dz",
+                                            "k_tc_rows:dgrad", "k_tc_rows:head_u", "k_tc_rows:head_dh"};
     ProfScope prof("k_tc_rows", st);
+    ProfScope prof_epi(kEpiName[EPI], st);
     k_tc_rows<EPI><<<grid, 256, smem, st>>>(p);
     note_launch();
     GWE_CUDA_TRY(cudaGetLastError());
@@ -718,6 +813,8 @@ gwe_status fp32_bias_grad(const float *G, int ldg, int N, int64_t g_boff, float 
                           int nbranch, cudaStream_t st);
 gwe_status fp32_input_backward(gwe_model *m, int mi, const float *dx0, int64_t rb, const float *sH, const float *sL,
                                int W, int C, float *gw, float *gH, float *gL, cudaStream_t st);
+gwe_status fp32_head_w2_grad(gwe_model *m, const float *ru, int W, int C, const float *dlogit, float *gw,
+                             cudaStream_t st);
 gwe_status fp32_input_proj(gwe_model *m, int mi, const float *sH, const float *sL, int64_t rb, float *x0,
                            cudaStream_t st);
 
@@ -756,6 +853,13 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
         const int64_t n = (int64_t)(t->layer_b / 2) * 2 * L;
         k_pack_bwd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(blob, g, t->img.as<__nv_bfloat16>());
         note_launch();
+        // the head's W_h1 as the B images of u and dh
+        const int64_t nh = (int64_t)d.Hc * 2 * S;
+        GWE_CUDA_TRY(t->head_img.ensure(2 * 2 * (size_t)nh));
+        k_pack_head<<<(unsigned)((nh + 255) / 256), 256, 0, st>>>(blob + off_wh1(d), d.Hc, 2 * S,
+                                                                  t->head_img.as<__half>(),
+                                                                  t->head_img.as<__nv_bfloat16>() + nh);
+        note_launch();
         GWE_CUDA_TRY(cudaGetLastError());
         t->model = mi;
         t->stamp = stamp;
@@ -780,6 +884,16 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
         GWE_CUDA_TRY(t->dx16[i].ensure(2 * rows2 * R));
     }
     GWE_CUDA_TRY(t->da16.ensure(2 * rows2 * 2 * R));
+    // the head on the tensor cores when its widths fit one MMA (N <= 256)
+    const bool tc_head = d.Hc <= 256 && 2 * S <= 256 && d.Hc % 32 == 0;
+    if (tc_head) {
+        GWE_CUDA_TRY(t->hf16.ensure(2 * rows2 * S));
+        GWE_CUDA_TRY(t->hb16.ensure(2 * rows2 * S));
+        GWE_CUDA_TRY(t->hblo16.ensure(2 * rows2 * S));
+        GWE_CUDA_TRY(t->dulo16.ensure(2 * rows * (size_t)d.Hc));
+        GWE_CUDA_TRY(t->du16.ensure(2 * rows * (size_t)d.Hc));
+        GWE_CUDA_TRY(t->ru32.ensure(sizeof(float) * rows * (size_t)d.Hc));
+    }
     GWE_CUDA_TRY(cudaMemsetAsync(gw, 0, sizeof(float) * d.P, st));
     const int64_t Pb = d.Pb;
     int *err = t->err.as<int>();
@@ -868,12 +982,98 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
                 std::swap(xa16, xb16);
             }
         }
-        // ---- head (FP32): dskip
-        r = fp32_head_backward(m, mi, t->skip.as<float>(), rb, W, Cc, dlogit + (int64_t)c0 * W, t->dskip32.as<float>(),
-                               gw, st);
-        if (r != GWE_OK) return r;
-        k_f32_to_bf16<<<1024, 256, 0, st>>>(t->dskip32.as<float>(), t->dskip16.as<__nv_bfloat16>(), 2 * rb * S);
-        note_launch();
+        // ---- head: dskip and the head's gradients
+        if (tc_head) {
+            // h = ReLU(skip) in FP16 and BF16; u = [h_H | h_L] . W_h1^T (FP16 operands, as in the forward)
+            // with du = (u + b_h1 > 0) dlogit w_h2 (BF16 hi and lo) and ReLU(u + b_h1) in its epilogue;
+            // dh = du . W_h1 (BF16 operands) with dskip = (h > 0) dh (FP32 and BF16); dW_h1 = du^T h per
+            // branch half of its columns from the BF16 splits; dw_h2, db_h2 in FP32
+            const int Hc = d.Hc;
+            const int64_t nhw = (int64_t)Hc * 2 * S;
+            const float *dl = dlogit + (int64_t)c0 * W;
+            __nv_bfloat16 *hb16 = t->hb16.as<__nv_bfloat16>(), *du16 = t->du16.as<__nv_bfloat16>();
+            // FP16 bits through the row GEMM's BF16-typed staging (a copy of 16-bit words)
+            const __nv_bfloat16 *hf16 = reinterpret_cast<const __nv_bfloat16 *>(t->hf16.as<__half>());
+            float *ru32 = t->ru32.as<float>();
+            __nv_bfloat16 *hblo16 = t->hblo16.as<__nv_bfloat16>(), *dulo16 = t->dulo16.as<__nv_bfloat16>();
+            k_relu_h<<<1024, 256, 0, st>>>(t->skip.as<float>(), t->hf16.as<__half>(), hb16, hblo16, 2 * rb * S);
+            note_launch();
+            RowGemm pu{};
+            pu.seg[0] = seg(hf16, 0, S, S, 0);
+            pu.seg[1] = seg(hf16 + rb * S, 0, S, S, 0);
+            pu.nseg = 2;
+            pu.K = 2 * S;
+            pu.N = Hc;
+            pu.bimg = reinterpret_cast<const uint8_t *>(t->head_img.as<__nv_bfloat16>());
+            pu.rows = rb;
+            pu.W = W;
+            pu.nbranch = 1;
+            pu.err = err;
+            pu.R = R;
+            pu.bias = blob + off_bh1(d);
+            pu.bias2 = blob + off_wh2(d);
+            pu.aux = dl;
+            pu.o16 = du16;
+            pu.o16_lo = dulo16;
+            pu.o32 = ru32;
+            r = run_rows<EPI_HEAD_U>(pu, sms, st);
+            if (r != GWE_OK) return r;
+            RowGemm pd{};
+            pd.seg[0] = seg(du16, 0, Hc, Hc, 0);
+            pd.nseg = 1;
+            pd.K = Hc;
+            pd.N = 2 * S;
+            pd.bimg = reinterpret_cast<const uint8_t *>(t->head_img.as<__nv_bfloat16>() + nhw);
+            pd.rows = rb;
+            pd.W = W;
+            pd.nbranch = 1;
+            pd.err = err;
+            pd.R = R;
+            pd.mask16 = hb16;
+            pd.mask_boff = rb * S;
+            pd.o32 = t->dskip32.as<float>();
+            pd.o32_boff = rb * S;
+            pd.o16 = t->dskip16.as<__nv_bfloat16>();
+            pd.o16_boff = rb * S;
+            r = run_rows<EPI_HEAD_DH>(pd, sms, st);
+            if (r != GWE_OK) return r;
+            // dW_h1 = du^T h from the BF16 splits du = du_hi + du_lo, h = h_hi + h_lo: the three products
+            // hi.hi, hi.lo and lo.hi accumulate into the same gradient (the lo.lo term is dropped), so
+            // that the sum over the batch keeps about 16 significant bits; db_h1 from the ones column
+            // of the two passes with X = h_hi (du_hi + du_lo summed)
+            const __nv_bfloat16 *Gs[3] = {du16, du16, dulo16}, *Xs[3] = {hb16, hblo16, hb16};
+            for (int m0 = 0; m0 < Hc; m0 += 128) {
+                for (int pass = 0; pass < 3; ++pass) {
+                    WgGemm g{};
+                    g.G = Gs[pass] + m0;
+                    g.g_boff = 0;
+                    g.ldg = Hc;
+                    g.M = std::min(128, Hc - m0);
+                    g.xs[0] = seg(Xs[pass], rb * S, S, S, 0);
+                    g.nxs = 1;
+                    g.nx = S;
+                    g.N = S + 16;
+                    g.db = pass == 1 ? nullptr : gw + off_bh1(d) + m0;
+                    g.db_nb = 1;
+                    g.rows = rb;
+                    g.W = W;
+                    g.dW = gw + off_wh1(d) + (int64_t)m0 * 2 * S;
+                    g.ldw = 2 * S;
+                    g.w_boff = S;
+                    g.err = err;
+                    r = run_wgrad(g, sms, st);
+                    if (r != GWE_OK) return r;
+                }
+            }
+            r = fp32_head_w2_grad(m, ru32, W, Cc, dl, gw, st);
+            if (r != GWE_OK) return r;
+        } else {
+            r = fp32_head_backward(m, mi, t->skip.as<float>(), rb, W, Cc, dlogit + (int64_t)c0 * W,
+                                   t->dskip32.as<float>(), gw, st);
+            if (r != GWE_OK) return r;
+            k_f32_to_bf16<<<1024, 256, 0, st>>>(t->dskip32.as<float>(), t->dskip16.as<__nv_bfloat16>(), 2 * rb * S);
+            note_launch();
+        }
         // ---- branches, stack by stack in reverse
         int hi = 0;   // dx buffers: [hi] = dL/dx_{l+1}
         GWE_CUDA_TRY(cudaMemsetAsync(t->dx32[hi].ptr, 0, sizeof(float) * 2 * rb * R, st));

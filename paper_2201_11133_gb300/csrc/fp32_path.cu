@@ -1018,6 +1018,18 @@ gwe_status fp32_head_backward(gwe_model *m, int mi, const float *skip, int64_t r
     return GWE_OK;
 }
 
+// the head's second layer: dw_h2 = sum over rows of dlogit ReLU(u + b_h1), db_h2 = sum of dlogit
+// (ru = ReLU(u + b_h1) [row][Hc], one launch each)
+gwe_status fp32_head_w2_grad(gwe_model *m, const float *ru, int W, int C, const float *dlogit, float *gw,
+                             cudaStream_t st) {
+    const Dims &d = m->dims;
+    const int Hc = d.Hc;
+    launch_wgrad(wg(ru, Hc, Hc, 0, dlogit, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, C), 1, st);
+    launch_wgrad(wg(dlogit, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W, C), 1, st);
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
 gwe_status fp32_bias_grad(const float *G, int ldg, int N, int64_t g_boff, float *db, int64_t db_boff, int W, int C,
                           int nbranch, cudaStream_t st) {
     launch_wgrad(wg(G, ldg, N, g_boff, nullptr, 0, 0, 0, 0, nullptr, 0, 0, db, db_boff, W, C), nbranch, st);

@@ -40,6 +40,17 @@ def test_bf16_round_matches_torch_casts_and_ties():
     assert ob.bf16_round(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
 
 
+def test_f16_round_matches_torch_casts_and_ties():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    v = np.concatenate([rng.standard_normal(100000) * 10.0 ** rng.integers(-9, 5, 100000),
+                        [0.0, -0.0, 1.0, -1.5, 65504.0, 1e-8,
+                         1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11]])   # ties to even at 1
+    want = torch.from_numpy(v.astype(np.float32)).to(torch.float16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(ob.f16_round(v.astype(np.float32).astype(np.float64)), want)
+    assert ob.f16_round(1.0 + 2.0 ** -11) == 1.0 and ob.f16_round(1.0 + 3 * 2.0 ** -11) == 1.0 + 2.0 ** -9
+
+
 def test_rounding_reaches_every_contraction():
     """Rounding changes the gradient (every contraction's operands are rounded, including the first
     layer's), but keeps its direction: the cosine with the exact gradient stays above 0.99.  The
