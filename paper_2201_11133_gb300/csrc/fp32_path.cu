@@ -935,6 +935,15 @@ BWg wg(const float *G, int ldg, int N, int64_t g_boff, const float *X, int ldx, 
     return p;
 }
 
+// Reductions with one or a few outputs (K <= 1, N <= 256: dw_h2, db_h2, the input projection's
+// gradients) have too few tiles for the default 64 row splits to fill the GPU: split the rows into
+// up to 1024 ranges of at least 512 rows (each adds its partial sums atomically).
+BWg wide(BWg p) {
+    const int64_t rows = (int64_t)p.C * p.W;
+    p.splits = (int)std::max<int64_t>(1, std::min<int64_t>(1024, rows / 512));
+    return p;
+}
+
 BSrc src(const float *A, int lda, int shift, int relu, const float *Wt, int ldw, int K) {
     BSrc s;
     s.A = A; s.lda = lda; s.shift = shift; s.relu = relu; s.Wt = Wt; s.ldw = ldw; s.K = K;
@@ -1012,8 +1021,8 @@ gwe_status fp32_head_backward(gwe_model *m, int mi, const float *skip, int64_t r
     BWg p2 = wg(du, Hc, Hc, 0, skip + rb * S, S, S, 0, 0, g1 + S, 2 * S, 0, nullptr, 0, W, C);
     p2.xrelu = 1;
     launch_wgrad(p2, 1, st);
-    launch_wgrad(wg(ru, Hc, Hc, 0, dlogit, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, C), 1, st);
-    launch_wgrad(wg(dlogit, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W, C), 1, st);
+    launch_wgrad(wide(wg(ru, Hc, Hc, 0, dlogit, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, C)), 1, st);
+    launch_wgrad(wide(wg(dlogit, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W, C)), 1, st);
     GWE_CUDA_TRY(cudaGetLastError());
     return GWE_OK;
 }
@@ -1024,8 +1033,8 @@ gwe_status fp32_head_w2_grad(gwe_model *m, const float *ru, int W, int C, const 
                              cudaStream_t st) {
     const Dims &d = m->dims;
     const int Hc = d.Hc;
-    launch_wgrad(wg(ru, Hc, Hc, 0, dlogit, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, C), 1, st);
-    launch_wgrad(wg(dlogit, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W, C), 1, st);
+    launch_wgrad(wide(wg(ru, Hc, Hc, 0, dlogit, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, C)), 1, st);
+    launch_wgrad(wide(wg(dlogit, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W, C)), 1, st);
     GWE_CUDA_TRY(cudaGetLastError());
     return GWE_OK;
 }
@@ -1042,10 +1051,12 @@ gwe_status fp32_input_backward(gwe_model *m, int mi, const float *dx0, int64_t r
     const Dims &d = m->dims;
     const int R = d.R;
     const float *blob = m->w32.as<float>() + (int64_t)mi * d.P;
-    launch_wgrad(wg(dx0, R, R, 0, sH, 1, 1, 0, 0, gw + off_branch(d, 0), 1, 0, gw + off_branch(d, 0) + R, 0, W, C), 1,
-                 st);
-    launch_wgrad(wg(dx0 + rb * R, R, R, 0, sL, 1, 1, 0, 0, gw + off_branch(d, 1), 1, 0, gw + off_branch(d, 1) + R, 0,
-                    W, C), 1, st);
+    launch_wgrad(wide(wg(dx0, R, R, 0, sH, 1, 1, 0, 0, gw + off_branch(d, 0), 1, 0, gw + off_branch(d, 0) + R, 0, W,
+                         C)),
+                 1, st);
+    launch_wgrad(wide(wg(dx0 + rb * R, R, R, 0, sL, 1, 1, 0, 0, gw + off_branch(d, 1), 1, 0, gw + off_branch(d, 1) + R,
+                         0, W, C)),
+                 1, st);
     const unsigned nb = (unsigned)((rb + 7) / 8);
     if (gH) {
         k_dstrain<<<nb, 256, 0, st>>>(dx0, blob + off_branch(d, 0), R, rb, gH);
