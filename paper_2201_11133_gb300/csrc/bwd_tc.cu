@@ -39,6 +39,7 @@ namespace {
 using namespace tc;
 
 constexpr int kRows = 128;              // rows per tile (the MMA's M)
+constexpr int kWgThreads = 512;         // weight-gradient GEMM: 4 threads per staged row
 constexpr uint64_t kWaitNs = 4000000000ull;
 
 // one K-range of a row GEMM's A operand: columns [0, C) of a row-major BF16 array, taken at row
@@ -482,25 +483,25 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
 // byte offset the step between 8-row K groups.  Two stages: the copies of tile i + 1 are in flight while
 // the MMAs of tile i run.  Channels M..127 of A are zero; columns nx..N-1 of B are [1, 0, ...],
 // so that column nx of D is the column sum of G (the bias gradient).
-template <int N>
-__global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
+template <int N, int NS>
+__global__ void __launch_bounds__(kWgThreads) k_tc_wgrad(const WgGemm p) {
     constexpr uint32_t A_BYTES = 16 * 2048, B_BYTES = (N / 8) * 2048, STAGE = A_BYTES + B_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    __shared__ uint64_t bar[3];
+    __shared__ uint64_t bar[NS + 1];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     constexpr uint32_t NCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) mbar_init(&bar[i], 1);
+        for (int i = 0; i < NS + 1; ++i) mbar_init(&bar[i], 1);
         abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(&tslot, NCOLS);
-    // constant parts of both stages (row k = tid): A channel groups >= M / 8 zero, B groups from
-    // nx / 8 on: 1.0 at column nx, zeros after it
-    for (int s = 0; s < 2; ++s) {
+    // constant parts of both stages (row k = tid < 128): A channel groups >= M / 8 zero, B groups
+    // from nx / 8 on: 1.0 at column nx, zeros after it
+    for (int s = 0; s < NS && tid < kRows; ++s) {
         uint8_t *a = smem + s * STAGE, *bb = a + A_BYTES;
         for (int mi = p.M / 8; mi < 16; ++mi) *reinterpret_cast<uint4 *>(a + mi * 2048 + tid * 16) = make_uint4(0, 0, 0, 0);
         for (int ni = p.nx / 8; ni < N / 8; ++ni)
@@ -514,36 +515,40 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
     const int64_t t_begin = (int64_t)blockIdx.x * p.tiles_per_cta;
     const int64_t t_end = std::min<int64_t>(p.tiles, t_begin + p.tiles_per_cta);
     const int64_t n = t_end - t_begin;
-    // copies of one tile into stage s: rows tid / 2 and tid / 2 + 64, channel groups of parity tid & 1
+    // copies of one tile into stage s: row tid / TPR, 16-byte channel groups of index = tid % TPR
+    // modulo TPR (consecutive threads on consecutive groups of one row)
     auto issue = [&](int64_t tile, int s) {
+        constexpr int TPR = kWgThreads / kRows;
         uint8_t *a = smem + s * STAGE, *bb = a + A_BYTES;
-        const int par = tid & 1;
-        for (int pass = 0; pass < 2; ++pass) {
-            const int k = (tid >> 1) + 64 * pass;
-            const int64_t row = tile * kRows + k;
-            const bool live = row < p.rows;
-            const __nv_bfloat16 *g = p.G + b * p.g_boff + (live ? row : 0) * p.ldg;
-            for (int mi = par; mi < p.M / 8; mi += 2) cp_async16(smem_u32(a + mi * 2048 + k * 16), g + 8 * mi, live);
-            int ni = 0;
-            for (int si = 0; si < p.nxs; ++si) {
-                const RowSeg &sg = p.xs[si];
-                bool valid = false;
-                const __nv_bfloat16 *x0 = live ? seg_addr(sg, b, row, p.W, 0, valid) : sg.p;
-                for (int cc = 0; cc < sg.C / 8; ++cc, ++ni) {
-                    if ((ni & 1) != par) continue;
-                    cp_async16(smem_u32(bb + ni * 2048 + k * 16), valid ? x0 + 8 * cc : sg.p, valid);
-                }
+        const int par = tid % TPR;
+        const int k = tid / TPR;
+        const int64_t row = tile * kRows + k;
+        const bool live = row < p.rows;
+        const __nv_bfloat16 *g = p.G + b * p.g_boff + (live ? row : 0) * p.ldg;
+        for (int mi = par; mi < p.M / 8; mi += TPR) cp_async16(smem_u32(a + mi * 2048 + k * 16), g + 8 * mi, live);
+        int ni = 0;
+        for (int si = 0; si < p.nxs; ++si) {
+            const RowSeg &sg = p.xs[si];
+            bool valid = false;
+            const __nv_bfloat16 *x0 = live ? seg_addr(sg, b, row, p.W, 0, valid) : sg.p;
+            for (int cc = 0; cc < sg.C / 8; ++cc, ++ni) {
+                if (ni % TPR != par) continue;
+                cp_async16(smem_u32(bb + ni * 2048 + k * 16), valid ? x0 + 8 * cc : sg.p, valid);
             }
         }
         cp_async_commit();
     };
     const uint32_t idesc = idesc_f16(128, N, 1) | (1u << 15) | (1u << 16);   // A and B MN-major
-    if (n > 0) issue(t_begin, 0);
-    if (n > 1) issue(t_begin + 1, 1);
+    for (int s = 0; s < NS; ++s)
+        if (s < n) issue(t_begin + s, s);
     bool ok = true;
     for (int64_t i = 0; i < n; ++i) {
-        const int s = (int)(i & 1);
-        if (i + 1 < n)
+        const int s = (int)(i % NS);
+        // groups committed after tile i's: the tiles issued ahead of it, at most NS - 1
+        const int64_t ahead = std::min<int64_t>(n - 1, i + NS - 1) - i;
+        if (ahead >= 2)
+            cp_async_wait_group<2>();
+        else if (ahead == 1)
             cp_async_wait_group<1>();
         else
             cp_async_wait_group<0>();
@@ -561,27 +566,27 @@ __global__ void __launch_bounds__(128) k_tc_wgrad(const WgGemm p) {
             }
             mma_commit(&bar[s]);
         }
-        if (i + 2 < n) {
-            // stage s takes tile i + 2 once the MMAs of tile i have read it
-            const bool w_ok = mbar_wait(&bar[s], (uint32_t)(i >> 1) & 1, &abort_flag, p.err, 80, kWaitNs);
+        if (i + NS < n) {
+            // stage s takes tile i + NS once the MMAs of tile i have read it
+            const bool w_ok = mbar_wait(&bar[s], (uint32_t)(i / NS) & 1, &abort_flag, p.err, 80, kWaitNs);
             if (__syncthreads_or(!w_ok)) {
                 ok = false;
                 break;
             }
-            issue(t_begin + i + 2, s);
+            issue(t_begin + i + NS, s);
         }
     }
     cp_async_wait_all();
     // every MMA of the CTA has completed (and written D) once this commit arrives
     bool d_ok = true;
     if (tid == 0) {
-        mma_commit(&bar[2]);
-        d_ok = mbar_wait_drain(&bar[2], 0, p.err, 81, kWaitNs);
+        mma_commit(&bar[NS]);
+        d_ok = mbar_wait_drain(&bar[NS], 0, p.err, 81, kWaitNs);
     }
     if (__syncthreads_or(!d_ok)) ok = false;
-    if (ok && n > 0) {
+    if (ok && n > 0 && warp < 4) {
         tc_fence_after();
-        // D[m][n] in TMEM lane m: warps whose lanes hold m < M add their rows
+        // D[m][n] in TMEM lane m: warps 0-3 (lanes 0-127) whose lanes hold m < M add their rows
         const int m = tid;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
         for (int c0 = 0; c0 < N; c0 += 16) {
@@ -726,9 +731,9 @@ gwe_status set_attrs() {
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_HEAD_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_rows<EPI_HEAD_DH>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<80>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<144>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<48, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<80, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<144, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     g_rows_smem_set = 1;
     return GWE_OK;
 }
@@ -765,7 +770,8 @@ gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
 gwe_status run_wgrad(WgGemm p, int sms, cudaStream_t st) {
     p.tiles = (p.rows + kRows - 1) / kRows;
     // two stages of [G^T: 128 x 128 | X^T: N x 128] BF16; one CTA per SM when they exceed half of
-    // the shared memory (this also keeps two 256-column TMEM allocations off one SM), else two
+    // the shared memory (this also keeps two 256-column TMEM allocations off one SM), else two.
+    // (Three stages with one CTA per SM for N = 144 measured no faster.)
     const size_t smem = 2 * ((size_t)128 * 128 * 2 + (size_t)p.N * 128 * 2) + 128;
     const int per_sm = smem > 113 * 1024 ? 1 : 2;
     // one wave over both branches, contiguous tile ranges (fewer partial sums to add atomically)
@@ -775,11 +781,11 @@ gwe_status run_wgrad(WgGemm p, int sms, cudaStream_t st) {
     ProfScope prof("k_tc_wgrad", st);
     // N = nx + 16: the segments' columns, then the ones column for the bias gradient (nx = 32, 64, 128)
     if (p.N == 48)
-        k_tc_wgrad<48><<<grid, 128, smem, st>>>(p);
+        k_tc_wgrad<48, 2><<<grid, kWgThreads, smem, st>>>(p);
     else if (p.N == 80)
-        k_tc_wgrad<80><<<grid, 128, smem, st>>>(p);
+        k_tc_wgrad<80, 2><<<grid, kWgThreads, smem, st>>>(p);
     else if (p.N == 144)
-        k_tc_wgrad<144><<<grid, 128, smem, st>>>(p);
+        k_tc_wgrad<144, 2><<<grid, kWgThreads, smem, st>>>(p);
     else {
         set_error("tensor-core backward: unsupported weight-gradient width");
         return GWE_ERR_UNSUPPORTED;
