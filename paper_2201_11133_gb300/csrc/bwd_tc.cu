@@ -170,6 +170,70 @@ __device__ __forceinline__ void st16_bf16(__nv_bfloat16 *dst, const float (&v)[1
     *reinterpret_cast<uint4 *>(dst + 8) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
+// Warp-cooperative stores of 16 consecutive values per lane's row (lane = row, rows 32 lanes apart in
+// memory by the array's row pitch): the values go through a per-warp staging area in shared memory
+// (80-byte row pitch, so that eight consecutive rows hit distinct banks) and come back out so that
+// each store instruction writes whole 32-byte sectors of 8 rows (FP32) or 16 rows (16-bit) instead of
+// half sectors of 32 rows.  Rows whose `live` is false are not stored.  Every lane of the warp calls.
+constexpr uint32_t kWarpStage = 32 * 80;   // bytes of staging per warp
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void wst16_f32(float *dst, const float (&v)[16], bool live, uint32_t stg, int lane) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(stg + lane * 80 + q * 16),
+                     "r"(__float_as_uint(v[4 * q])), "r"(__float_as_uint(v[4 * q + 1])),
+                     "r"(__float_as_uint(v[4 * q + 2])), "r"(__float_as_uint(v[4 * q + 3]))
+                     : "memory");
+    __syncwarp();
+    const unsigned long long d = reinterpret_cast<unsigned long long>(dst);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int rr = 8 * i + (lane >> 2), c = lane & 3;
+        const unsigned long long dr = __shfl_sync(0xffffffffu, d, rr);
+        const int lv = __shfl_sync(0xffffffffu, live ? 1 : 0, rr);
+        const uint4 x = lds128(stg + rr * 80 + c * 16);
+        if (lv) *reinterpret_cast<uint4 *>(reinterpret_cast<float *>(dr) + 4 * c) = x;
+    }
+    __syncwarp();
+}
+__device__ __forceinline__ void wst16_w(void *dst, const uint32_t (&w)[8], bool live, uint32_t stg, int lane) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(stg + lane * 80), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                 "r"(w[3])
+                 : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(stg + lane * 80 + 16), "r"(w[4]), "r"(w[5]),
+                 "r"(w[6]), "r"(w[7])
+                 : "memory");
+    __syncwarp();
+    const unsigned long long d = reinterpret_cast<unsigned long long>(dst);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int rr = 16 * i + (lane >> 1), c = lane & 1;
+        const unsigned long long dr = __shfl_sync(0xffffffffu, d, rr);
+        const int lv = __shfl_sync(0xffffffffu, live ? 1 : 0, rr);
+        const uint4 x = lds128(stg + rr * 80 + c * 16);
+        if (lv) *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(dr) + 16 * c) = x;
+    }
+    __syncwarp();
+}
+__device__ __forceinline__ void pack16_bf16(const float (&v)[16], uint32_t (&w)[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+}
+__device__ __forceinline__ void pack16_f16(const float (&v)[16], uint32_t (&w)[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+}
+
 // D = A . B^T over the row tiles of both branches, fused epilogue EPI.
 // 256 threads: thread (r = tid % 128, h = tid / 128) owns row r of the tile and half h of the
 // epilogue's channels (TMEM lanes of warp w: 32 (w % 4) ..).  Per tile the epilogue's global
@@ -188,6 +252,9 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
     const int KC = p.K / 8;                                   // 16-byte chunks per row
     const uint32_t a_bytes = (uint32_t)kRows * p.K * 2;   // B image follows the A tile
     uint8_t *sA = smem, *sB = smem + a_bytes;
+    // epilogues with staged (coalesced) stores: a per-warp staging area after the B image
+    const uint32_t stg = smem_u32(smem + a_bytes + (uint32_t)p.bn * p.K * 2) + (tid >> 5) * kWarpStage;
+    const int lane = tid & 31;
     const uint32_t ncols = tmem_cols_for(p.N);
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -289,7 +356,6 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
                 tmem_ld16(tl + c0, fr);
                 tmem_ld16(tl + R + c0, gr);
                 tmem_ld_wait();
-                if (!live) continue;
                 float th[16], sg[16], z[16];
                 // the forward kernel's gate arithmetic: tanh.approx, and sigmoid(g) = 0.5 tanh(g/2) + 0.5
 #pragma unroll
@@ -298,12 +364,16 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
                     sg[j] = fmaf(tanh_approx(0.5f * (__uint_as_float(gr[j]) + __ldg(bc + R + c0 + j))), 0.5f, 0.5f);
                     z[j] = th[j] * sg[j];
                 }
+                uint32_t w[8];
                 if (p.gate_out) {   // the backward's gate cache: tanh(f), sigmoid(g) in FP16
                     __half *go = p.gate_out + b * p.gate_boff + row * 2 * R;
-                    st16_f16(go + c0, th);
-                    st16_f16(go + R + c0, sg);
+                    pack16_f16(th, w);
+                    wst16_w(go + c0, w, live, stg, lane);
+                    pack16_f16(sg, w);
+                    wst16_w(go + R + c0, w, live, stg, lane);
                 }
-                st16_bf16(p.o16 + b * p.o16_boff + row * R + c0, z);
+                pack16_bf16(z, w);
+                wst16_w(p.o16 + b * p.o16_boff + row * R + c0, w, live, stg, lane);
             }
         } else if (EPI == EPI_RES) {
             const float *br = p.bias + b * p.bias_boff;
@@ -316,7 +386,6 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
                 uint32_t rr[16];
                 tmem_ld16(tl + c0, rr);
                 tmem_ld_wait();
-                if (!live) continue;
                 float v[16];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -327,8 +396,10 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(rr[j]) + __ldg(br + c0 + j);
-                st16_f32(p.o32 + b * p.o32_boff + row * R + c0, v);
-                st16_bf16(p.o16 + b * p.o16_boff + row * R + c0, v);
+                wst16_f32(p.o32 + b * p.o32_boff + row * R + c0, v, live, stg, lane);
+                uint32_t w[8];
+                pack16_bf16(v, w);
+                wst16_w(p.o16 + b * p.o16_boff + row * R + c0, w, live, stg, lane);
             }
             const float *bs = p.bias2 ? p.bias2 + b * p.bias_boff : nullptr;
             // the skip sums of this thread's half, all loads in flight together
@@ -364,7 +435,6 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
                 uint32_t dr[16];
                 tmem_ld16(tl + c0, dr);
                 tmem_ld_wait();
-                if (!live) continue;
                 float th[16], sg[16], df[16], dg[16];
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
@@ -388,8 +458,11 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
                     dg[j] = dz * th[j] * sg[j] * (1.f - sg[j]);
                 }
                 __nv_bfloat16 *d16 = p.o16 + b * p.o16_boff + row * 2 * R;
-                st16_bf16(d16 + c0, df);
-                st16_bf16(d16 + R + c0, dg);
+                uint32_t w[8];
+                pack16_bf16(df, w);
+                wst16_w(d16 + c0, w, live, stg, lane);
+                pack16_bf16(dg, w);
+                wst16_w(d16 + R + c0, w, live, stg, lane);
             }
         } else if (EPI == EPI_HEAD_U) {
             // this thread's u channels [h N/2, h N/2 + N/2) of its row
@@ -754,8 +827,11 @@ gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
     p.n_tiles = tpb * p.nbranch;
     if (p.bn < p.N) p.bn = p.N;
     // at least 80 KB of shared memory per CTA, so that at most two CTAs (2 x <= 256 TMEM columns)
-    // share an SM and no TMEM allocation has to wait
-    const size_t smem = std::max<size_t>((size_t)kRows * p.K * 2 + (size_t)p.bn * p.K * 2 + 128, 80 * 1024);
+    // share an SM and no TMEM allocation has to wait; the conv, residual and dz epilogues stage
+    // their stores per warp after the B image (dgrad, whose stages leave no room for it at two CTAs
+    // per SM, stores directly: staged at 48-byte pitch it measured no faster)
+    const size_t staging = EPI <= EPI_DZ ? (size_t)8 * kWarpStage : 0;
+    const size_t smem = std::max<size_t>((size_t)kRows * p.K * 2 + (size_t)p.bn * p.K * 2 + staging + 128, 80 * 1024);
     const int grid = (int)std::min<int64_t>(p.n_tiles, (int64_t)sms * (smem <= 100 * 1024 ? 2 : 1));
     static const char *const kEpiName[6] = {"k_tc_rows:conv", "k_tc_rows:res",    "k_tc_rows:dz",
                                             "k_tc_rows:dgrad", "k_tc_rows:head_u", "k_tc_rows:head_dh"};
