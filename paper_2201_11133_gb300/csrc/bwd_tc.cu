@@ -16,11 +16,13 @@
 //                                                                  channels, K = rows)
 // Row GEMMs stage their A tile (thread = row, window boundaries zero-filled) and keep the
 // layer's B image in shared memory; the MMA accumulates in TMEM and the epilogue (thread = row)
-// applies the fused step.  Weight-gradient GEMMs stage G^T and X^T tiles (transposed while
-// staging), accumulate over a range of row tiles in TMEM and add their partial sums atomically.
+// applies the fused step.  Weight-gradient GEMMs bring in G^T and X^T tiles (tensor-map copies with
+// the 128-byte swizzle where every operand has 64 or 128 channels, else per-thread copies),
+// accumulate over a range of row tiles in TMEM and add their partial sums atomically.
 // The stack inputs and skip sums that the per-stack recomputation starts from come, for BF16
 // handles, from the fused forward kernel (one launch per chunk, training save mode); otherwise from
 // a forward pass of row GEMMs.  The head, the input projection and dL/dstrain use the FP32 kernels.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -686,6 +688,191 @@ __global__ void __launch_bounds__(kWgThreads) k_tc_wgrad(const WgGemm p) {
     }
 }
 
+// ---------------------------------------------------------------- weight gradients through TMA
+// dW += G^T X as in k_tc_wgrad, with the operands brought in by tensor-map copies
+// (cp.async.bulk.tensor) instead of per-thread 16-byte copies: one thread issues a tile's copies,
+// another its MMAs, and the copies of up to `stages` tiles are in flight at once.  A tile is
+// kTmaRows rows of one window.  Each 64-channel block of a tile lands as kTmaRows rows of 128 bytes
+// with the 128-byte swizzle (16-byte chunk j of row k at chunk position j ^ (k % 8)), which is the
+// canonical MN-major operand layout with that swizzle: 64-channel blocks kTmaBlk bytes apart (the
+// descriptor's leading byte offset) and 8-row K groups 1024 bytes apart (its stride byte offset).
+// A = G^T takes blocks 0 and 1 (block 1 stays zero when M = 64); B = X^T takes the segments'
+// nx / 64 blocks and a last block holding the ones column (column nx) for the bias gradient.
+// Rows outside [0, W) of a shifted segment are zero-filled by the copy (out-of-range coordinates).
+constexpr int kTmaRows = 64;
+constexpr int kTmaBlk = kTmaRows * 128;
+constexpr int kTmaMaxStages = 6;
+constexpr size_t kTmaSmem = 226 * 1024;   // dynamic shared memory of the tensor-map weight-gradient kernels
+
+struct WgTma {
+    CUtensorMap g_map;        // G: {M channels, rows, branches}
+    CUtensorMap x_map[2];     // segments: {C channels, W, windows, branches}
+    int g_blocks;             // M / 64
+    int g_nb;                 // 2 when the branches read their own G, else 1
+    int x_blocks[2];          // C / 64 of each segment
+    int x_shift[2];
+    int x_nb[2];
+    int nxs;
+    int W;
+    int64_t tiles;            // kTmaRows-row tiles per branch
+    int tiles_per_cta;
+    int stages;
+    int M, nx, ldw;
+    float *dW;                // dW[m][n] at dW + m * ldw + n (16-byte aligned rows), branch 1 at + w_boff
+    int64_t w_boff;
+    float *db;
+    int db_nb;
+    int *err;
+};
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// shared-memory descriptor of an operand in the 128-byte swizzled layout (layout type 2)
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+    return sdesc(saddr, lbo_bytes, sbo_bytes) | (2ull << 61);
+}
+
+// NB: B blocks (nx / 64 + 1); N = nx + 16
+template <int NB>
+__global__ void __launch_bounds__(128, 1) k_tc_wgrad_tma(const __grid_constant__ WgTma p) {
+    constexpr int N = (NB - 1) * 64 + 16;
+    constexpr uint32_t NCOLS = N <= 128 ? 128 : 256;
+    constexpr uint32_t A_BYTES = 2 * kTmaBlk, STAGE = (2 + NB) * kTmaBlk;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full[kTmaMaxStages], empty[kTmaMaxStages], done;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int ns = p.stages;
+    if (tid == 0) {
+        for (int s = 0; s < ns; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tslot, NCOLS);
+    // constant blocks of every stage (never written by the copies): A block 1 when M = 64 (zeros);
+    // B's last block: 1.0 at its column 0 (logical chunk 0 of row k sits at position k % 8)
+    for (int s = 0; s < ns; ++s) {
+        uint8_t *st = smem + s * STAGE;
+        if (p.g_blocks == 1)
+            for (int i = tid; i < kTmaBlk / 16; i += 128) *reinterpret_cast<uint4 *>(st + kTmaBlk + i * 16) = make_uint4(0, 0, 0, 0);
+        uint8_t *ones = st + A_BYTES + (NB - 1) * kTmaBlk;
+        for (int i = tid; i < kTmaBlk / 16; i += 128)
+            *reinterpret_cast<uint4 *>(ones + i * 16) = make_uint4((i % 8) == ((i / 8) % 8) ? 0x3F80u : 0u, 0, 0, 0);
+    }
+    // the constant blocks are read by the tensor cores (async proxy)
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    const int b = blockIdx.y;
+    const int64_t t_begin = (int64_t)blockIdx.x * p.tiles_per_cta;
+    const int64_t n = std::max<int64_t>(0, std::min<int64_t>(p.tiles, t_begin + p.tiles_per_cta) - t_begin);
+    int xb = 0;
+    for (int si = 0; si < p.nxs; ++si) xb += p.x_blocks[si];
+    const uint32_t tile_bytes = (uint32_t)(p.g_blocks + xb) * kTmaBlk;
+    bool ok = true;
+    if (tid == 0 && n > 0) {
+        // producer: stage s takes tile i once the MMAs of tile i - ns have read it
+        int64_t armed = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            const int s = (int)(i % ns);
+            const uint32_t u = (uint32_t)(i / ns);
+            if (i >= ns && !mbar_wait(&empty[s], (u - 1) & 1, &abort_flag, p.err, 82, kWaitNs)) {
+                ok = false;
+                break;
+            }
+            const int64_t row0 = (t_begin + i) * kTmaRows;
+            const int w = (int)(row0 / p.W), t0 = (int)(row0 - (int64_t)w * p.W);
+            const uint32_t a = smem_u32(smem + s * STAGE), bb = a + A_BYTES, fb = smem_u32(&full[s]);
+            mbar_arrive_expect_tx(&full[s], tile_bytes);
+            for (int j = 0; j < p.g_blocks; ++j) tma_load_3d(a + j * kTmaBlk, &p.g_map, fb, 64 * j, (int)row0, p.g_nb > 1 ? b : 0);
+            int blk = 0;
+            for (int si = 0; si < p.nxs; ++si)
+                for (int j = 0; j < p.x_blocks[si]; ++j, ++blk)
+                    tma_load_4d(bb + blk * kTmaBlk, &p.x_map[si], fb, 64 * j, t0 + p.x_shift[si], w,
+                                p.x_nb[si] > 1 ? b : 0);
+            armed = i + 1;
+        }
+        // copies armed for tiles that an aborted MMA thread never consumed land before the CTA exits
+        for (int64_t i = std::max<int64_t>(0, armed - ns); i < armed; ++i)
+            mbar_wait_drain(&full[i % ns], (uint32_t)(i / ns) & 1, p.err, 85, kWaitNs);
+    } else if (tid == 32 && n > 0) {
+        // MMA issuer: K = 16 rows per instruction, 2048 bytes per step within each block
+        const uint32_t idesc = idesc_f16(128, N, 1) | (1u << 15) | (1u << 16);   // A and B MN-major
+        for (int64_t i = 0; i < n; ++i) {
+            const int s = (int)(i % ns);
+            if (!mbar_wait(&full[s], (uint32_t)(i / ns) & 1, &abort_flag, p.err, 83, kWaitNs)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = smem_u32(smem + s * STAGE), bb = a + A_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < kTmaRows / 16; ++ks)
+                mma_f16(tmem, sdesc_sw128(a + ks * 2048, kTmaBlk, 1024), sdesc_sw128(bb + ks * 2048, kTmaBlk, 1024),
+                        idesc, (i > 0 || ks > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        // arrives once every MMA issued above has completed (also after an abort)
+        mma_commit(&done);
+    }
+    __syncwarp();
+    bool d_ok = true;
+    if (n > 0) d_ok = mbar_wait_drain(&done, 0, p.err, 84, kWaitNs);
+    const bool bad = __syncthreads_or(!ok || !d_ok);
+    if (!bad && n > 0) {
+        tc_fence_after();
+        // D[m][c] in TMEM lane m = tid; columns [0, nx) into dW (four columns per atomic), column nx into db
+        const int m = tid;
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tl + c0, v);
+            tmem_ld_wait();
+            if (m >= p.M) continue;
+            if (c0 < p.nx) {
+                float4 *dw = reinterpret_cast<float4 *>(p.dW + b * p.w_boff + (int64_t)m * p.ldw + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    atomicAdd(dw + q, make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                                  __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])));
+            } else if (c0 == p.nx && p.db && (p.db_nb == 0 || b < p.db_nb)) {
+                atomicAdd(p.db + b * p.w_boff + m, __uint_as_float(v[0]));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, NCOLS);
+    }
+}
+
 // h = ReLU(skip) (skip: the pre-ReLU skip sums with their biases, both branches) in FP16, the
 // forward kernel's head operand, and in BF16 (hi, and lo = BF16(h - hi)), the weight-gradient
 // operands; hi is also the dskip mask
@@ -807,6 +994,8 @@ gwe_status set_attrs() {
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<48, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<80, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad<144, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem));
+    GWE_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem));
     g_rows_smem_set = 1;
     return GWE_OK;
 }
@@ -843,7 +1032,113 @@ gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
     return GWE_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver through the runtime (no link-time dependency on libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// BF16 tensor of `rank` dimensions (dims[0] channels, contiguous), boxes of 64 channels x kTmaRows
+// rows (x 1 in the higher dimensions), 128-byte swizzle, zero fill out of range
+bool encode_bf16_map(CUtensorMap *map, const void *base, int rank, const uint64_t *dims, const uint64_t *strides) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    cuuint64_t gd[4], gs[3];
+    cuuint32_t box[4], es[4];
+    for (int i = 0; i < rank; ++i) {
+        gd[i] = dims[i];
+        box[i] = i == 0 ? 64 : (i == 1 ? kTmaRows : 1);
+        es[i] = 1;
+        if (i + 1 < rank) {
+            gs[i] = strides[i];
+            if (strides[i] % 16) return false;
+        }
+    }
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(base), gd, gs, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tensor-map form of a weight-gradient GEMM, when its shapes allow one: 64 or 128 channels of
+// G and of every segment, windows a multiple of kTmaRows, 16-byte aligned rows of dW.  Returns
+// false (and the caller takes the per-thread-copy kernel) otherwise.
+bool make_wg_tma(const WgGemm &p, WgTma &t) {
+    if (p.W % kTmaRows || p.rows % p.W || p.rows >= (int64_t(1) << 31) || (p.M != 64 && p.M != 128)) return false;
+    if (p.nxs < 1 || p.nxs > 2 || p.N != p.nx + 16 || (p.nx != 64 && p.nx != 128)) return false;
+    if ((reinterpret_cast<uintptr_t>(p.dW) & 15) || p.ldw % 4 || p.w_boff % 4) return false;
+    std::memset(&t, 0, sizeof(t));
+    const int64_t nwin = p.rows / p.W;
+    {
+        const uint64_t dims[3] = {(uint64_t)p.M, (uint64_t)p.rows, p.g_boff ? 2u : 1u};
+        const uint64_t strides[2] = {(uint64_t)p.ldg * 2, (uint64_t)(p.g_boff ? p.g_boff : p.rows * p.ldg) * 2};
+        if (!encode_bf16_map(&t.g_map, p.G, 3, dims, strides)) return false;
+    }
+    int csum = 0;
+    for (int si = 0; si < p.nxs; ++si) {
+        const RowSeg &s = p.xs[si];
+        if (s.C != 64 && s.C != 128) return false;
+        const uint64_t dims[4] = {(uint64_t)s.C, (uint64_t)p.W, (uint64_t)nwin, s.boff ? 2u : 1u};
+        const uint64_t strides[3] = {(uint64_t)s.ld * 2, (uint64_t)p.W * s.ld * 2,
+                                     (uint64_t)(s.boff ? s.boff : nwin * p.W * s.ld) * 2};
+        if (!encode_bf16_map(&t.x_map[si], s.p, 4, dims, strides)) return false;
+        t.x_blocks[si] = s.C / 64;
+        t.x_shift[si] = s.shift;
+        t.x_nb[si] = s.boff ? 2 : 1;
+        csum += s.C;
+    }
+    if (csum != p.nx) return false;
+    t.g_blocks = p.M / 64;
+    t.g_nb = p.g_boff ? 2 : 1;
+    t.nxs = p.nxs;
+    t.W = p.W;
+    t.tiles = p.rows / kTmaRows;
+    t.M = p.M;
+    t.nx = p.nx;
+    t.ldw = p.ldw;
+    t.dW = p.dW;
+    t.w_boff = p.w_boff;
+    t.db = p.db;
+    t.db_nb = p.db_nb;
+    t.err = p.err;
+    return true;
+}
+
+gwe_status run_wgrad_tma(WgTma &t, int sms, cudaStream_t st) {
+    const int NB = t.nx / 64 + 1;
+    const size_t stage = (size_t)(2 + NB) * kTmaBlk;
+    t.stages = (int)std::min<size_t>(kTmaMaxStages, (kTmaSmem - 1024) / stage);
+    const size_t smem = t.stages * stage + 1024;
+    // one CTA per SM (the stages fill its shared memory), one wave over both branches, contiguous
+    // tile ranges
+    const int64_t per_branch = std::max<int64_t>(1, sms / 2);
+    t.tiles_per_cta = (int)std::max<int64_t>(1, (t.tiles + per_branch - 1) / per_branch);
+    dim3 grid((unsigned)((t.tiles + t.tiles_per_cta - 1) / t.tiles_per_cta), 2);
+    ProfScope prof("k_tc_wgrad", st);
+    if (NB == 2)
+        k_tc_wgrad_tma<2><<<grid, 128, smem, st>>>(t);
+    else
+        k_tc_wgrad_tma<3><<<grid, 128, smem, st>>>(t);
+    note_launch();
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
+}
+
 gwe_status run_wgrad(WgGemm p, int sms, cudaStream_t st) {
+    {
+        WgTma t;
+        if (make_wg_tma(p, t)) return run_wgrad_tma(t, sms, st);
+    }
     p.tiles = (p.rows + kRows - 1) / kRows;
     // two stages of [G^T: 128 x 128 | X^T: N x 128] BF16; one CTA per SM when they exceed half of
     // the shared memory (this also keeps two 256-column TMEM allocations off one SM), else two.
