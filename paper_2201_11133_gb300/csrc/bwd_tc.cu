@@ -14,8 +14,9 @@
 //             dWconv += da^T [x(t-d) | x(t)], dW_res += dx_{l+1}^T z, dW_skip += dskip^T z
 //                                                                 (weight gradients: M = output
 //                                                                  channels, K = rows)
-// Row GEMMs stage their A tile (thread = row, window boundaries zero-filled) and keep the
-// layer's B image in shared memory; the MMA accumulates in TMEM and the epilogue (thread = row)
+// Row GEMMs bring in their A tile (tensor-map copies with the 128-byte swizzle where the shapes
+// allow, else per-thread copies; window boundaries zero-filled) and keep the layer's B image in
+// shared memory; the MMA accumulates in TMEM and the epilogue (thread = row)
 // applies the fused step.  Weight-gradient GEMMs bring in G^T and X^T tiles (tensor-map copies with
 // the 128-byte swizzle where every operand has 64 or 128 channels, else per-thread copies),
 // accumulate over a range of row tiles in TMEM and add their partial sums atomically.
@@ -58,7 +59,36 @@ struct RowSeg {
 // EPI_HEAD_DH: dh = du . W_h1 (N = 2S, K = Hc), dskip_b = (h_b > 0) ? dh_b : 0 (thread half = branch)
 enum { EPI_CONV = 0, EPI_RES = 1, EPI_DZ = 2, EPI_DGRAD = 3, EPI_HEAD_U = 4, EPI_HEAD_DH = 5 };
 
+// ---------------------------------------------------------------- tensor-map copies
+// Tiled global -> shared copies through a tensor map (a kernel parameter), completion counted in
+// bytes on the mbarrier at `bar`; out-of-range coordinates are zero-filled.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// shared-memory descriptor of an operand in the 128-byte swizzled layout (layout type 2)
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+    return sdesc(saddr, lbo_bytes, sbo_bytes) | (2ull << 61);
+}
+
 struct RowGemm {
+    CUtensorMap a_map[2];             // a_tma: the segments as {C channels, W, windows, branches}
+    int a_tma;                        // 1: A tiles by tensor-map copies (128-byte swizzle, K-major)
+    int a_nb[2];                      // 2 when the branches have their own segment array, else 1
     RowSeg seg[2];
     int nseg;
     int K, N;                         // K = sum of the segments' C; N = MMA columns
@@ -243,10 +273,10 @@ __device__ __forceinline__ void pack16_f16(const float (&v)[16], uint32_t (&w)[8
 // (and B image, at a branch change) are issued as soon as the MMA has read shared memory, so that
 // they are in flight while the epilogue runs.
 template <int EPI>
-__global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
+__global__ void __launch_bounds__(256, 2) k_tc_rows(const __grid_constant__ RowGemm p) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    __shared__ uint64_t bar[2];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t bar[3];   // MMA done; final drain; A tile landed (tensor-map copies)
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -261,6 +291,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
         abort_flag = 0;
         fence_mbar_init();
     }
@@ -271,6 +302,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
     const uint32_t tmem = tslot;
     const int64_t tpb = (p.rows + kRows - 1) / kRows;         // tiles per branch
     int cur_b = -1;
+    uint32_t a_issued = 0, a_landed = 0;                      // thread 0: tensor-map A tiles
     // cp.async copies of one tile: B image at a branch change, A tile in chunk-column layout
     // (chunks 2j and 2j + 1 of row tid / 2 by threads tid & ~1 and tid | 1, so that a lane pair
     // reads one 32-byte sector; window boundaries zero-filled)
@@ -282,6 +314,22 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
             const int n16 = p.bn * p.K * 2 / 16;
             for (int i = tid; i < n16; i += 256) cp_async16(smem_u32(sB + 16 * i), src + 16 * i, true);
             cur_b = b;
+        }
+        if (p.a_tma) {
+            // one thread: each 64-channel block of the segments as 128 rows of 128 bytes (128-byte
+            // swizzle), block j at sA + j * 16 KB; the tile lies in one window (W % 128 == 0)
+            if (tid == 0) {
+                const int w = (int)(r0 / p.W), t0 = (int)(r0 - (int64_t)w * p.W);
+                const uint32_t a = smem_u32(sA), fb = smem_u32(&bar[2]);
+                mbar_arrive_expect_tx(&bar[2], (uint32_t)kRows * p.K * 2);
+                int blk = 0;
+                for (int si = 0; si < p.nseg; ++si)
+                    for (int j = 0; j < p.seg[si].C / 64; ++j, ++blk)
+                        tma_load_4d(a + blk * (kRows * 128), &p.a_map[si], fb, 64 * j, t0 + p.seg[si].shift, w,
+                                    p.a_nb[si] > 1 ? b : 0);
+                ++a_issued;
+            }
+            return;
         }
         const int cr = tid >> 1, par = tid & 1;
         const int64_t row = r0 + cr;
@@ -330,14 +378,22 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
         tc_fence_before();
         __syncthreads();
         if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            for (int ks = 0; ks < KC / 2; ++ks) {
-                const uint64_t ad = sdesc(a0 + ks * 2 * kRows * 16, kRows * 16, 128);
-                const uint64_t bd = sdesc(b0 + ks * 2 * p.bn * 16, p.bn * 16, 128);
-                mma_f16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+            // a wait that gives up sets abort_flag, so that every thread's MMA wait below gives up too
+            const bool a_ok = !p.a_tma || mbar_wait(&bar[2], a_landed & 1, &abort_flag, p.err, 90 + EPI, kWaitNs);
+            if (a_ok) {
+                a_landed += p.a_tma ? 1 : 0;
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+                for (int ks = 0; ks < KC / 2; ++ks) {
+                    // K-major A with the 128-byte swizzle: K step ks at byte 32 (ks % 4) of 64-channel
+                    // block ks / 4 (8-row groups 1024 bytes apart); else the chunk-column layout
+                    const uint64_t ad = p.a_tma ? sdesc_sw128(a0 + (ks >> 2) * (kRows * 128) + (ks & 3) * 32, 16, 1024)
+                                                : sdesc(a0 + ks * 2 * kRows * 16, kRows * 16, 128);
+                    const uint64_t bd = sdesc(b0 + ks * 2 * p.bn * 16, p.bn * 16, 128);
+                    mma_f16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                }
+                mma_commit(&bar[0]);
             }
-            mma_commit(&bar[0]);
         }
         const bool w_ok = mbar_wait(&bar[0], ph & 1, &abort_flag, p.err, 60 + EPI, kWaitNs);
         ++ph;
@@ -537,6 +593,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const RowGemm p) {
     }
     // copies issued for a tile that an aborted loop never reached complete before the CTA exits
     cp_async_wait_all();
+    if (tid == 0 && a_issued > a_landed) mbar_wait_drain(&bar[2], (a_issued - 1) & 1, p.err, 100 + EPI, kWaitNs);
     // no MMA of this thread may be in flight when TMEM is released
     if (tid == 0) {
         mma_commit(&bar[1]);
@@ -724,29 +781,6 @@ struct WgTma {
     int db_nb;
     int *err;
 };
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
-                                            int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-        "[%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
-                                            int c2, int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
-        "%6}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-        : "memory");
-}
-
-// shared-memory descriptor of an operand in the 128-byte swizzled layout (layout type 2)
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
-    return sdesc(saddr, lbo_bytes, sbo_bytes) | (2ull << 61);
-}
 
 // NB: B blocks (nx / 64 + 1); N = nx + 16
 template <int NB>
@@ -1010,28 +1044,6 @@ RowSeg seg(const __nv_bfloat16 *p, int64_t boff, int ld, int C, int shift) {
     return s;
 }
 
-template <int EPI>
-gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
-    const int64_t tpb = (p.rows + kRows - 1) / kRows;
-    p.n_tiles = tpb * p.nbranch;
-    if (p.bn < p.N) p.bn = p.N;
-    // at least 80 KB of shared memory per CTA, so that at most two CTAs (2 x <= 256 TMEM columns)
-    // share an SM and no TMEM allocation has to wait; the conv, residual and dz epilogues stage
-    // their stores per warp after the B image (dgrad, whose stages leave no room for it at two CTAs
-    // per SM, stores directly: staged at 48-byte pitch it measured no faster)
-    const size_t staging = EPI <= EPI_DZ ? (size_t)8 * kWarpStage : 0;
-    const size_t smem = std::max<size_t>((size_t)kRows * p.K * 2 + (size_t)p.bn * p.K * 2 + staging + 128, 80 * 1024);
-    const int grid = (int)std::min<int64_t>(p.n_tiles, (int64_t)sms * (smem <= 100 * 1024 ? 2 : 1));
-    static const char *const kEpiName[6] = {"k_tc_rows:conv", "k_tc_rows:res",    "k_tc_rows:dz",
-                                            "k_tc_rows:dgrad", "k_tc_rows:head_u", "k_tc_rows:head_dh"};
-    ProfScope prof("k_tc_rows", st);
-    ProfScope prof_epi(kEpiName[EPI], st);
-    k_tc_rows<EPI><<<grid, 256, smem, st>>>(p);
-    note_launch();
-    GWE_CUDA_TRY(cudaGetLastError());
-    return GWE_OK;
-}
-
 // cuTensorMapEncodeTiled from the driver through the runtime (no link-time dependency on libcuda)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -1049,16 +1061,17 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// BF16 tensor of `rank` dimensions (dims[0] channels, contiguous), boxes of 64 channels x kTmaRows
+// 16-bit tensor of `rank` dimensions (dims[0] channels, contiguous), boxes of 64 channels x box_rows
 // rows (x 1 in the higher dimensions), 128-byte swizzle, zero fill out of range
-bool encode_bf16_map(CUtensorMap *map, const void *base, int rank, const uint64_t *dims, const uint64_t *strides) {
+bool encode_bf16_map(CUtensorMap *map, const void *base, int rank, const uint64_t *dims, const uint64_t *strides,
+                     int box_rows) {
     const EncodeTiledFn fn = encode_tiled();
     if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
     cuuint64_t gd[4], gs[3];
     cuuint32_t box[4], es[4];
     for (int i = 0; i < rank; ++i) {
         gd[i] = dims[i];
-        box[i] = i == 0 ? 64 : (i == 1 ? kTmaRows : 1);
+        box[i] = i == 0 ? 64 : (i == 1 ? box_rows : 1);
         es[i] = 1;
         if (i + 1 < rank) {
             gs[i] = strides[i];
@@ -1068,6 +1081,48 @@ bool encode_bf16_map(CUtensorMap *map, const void *base, int rank, const uint64_
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(base), gd, gs, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tensor-map form of a row GEMM's A tiles, where the shapes allow one: windows a multiple of 128
+// rows (a tile lies in one window), segments of a multiple of 64 channels.  Otherwise (e.g. R = 32)
+// the per-thread copies stage A in the chunk-column layout.
+void make_rows_tma(RowGemm &p) {
+    p.a_tma = 0;
+    if (p.W % kRows || p.rows % p.W || p.rows >= (int64_t(1) << 31)) return;
+    const int64_t nwin = p.rows / p.W;
+    for (int si = 0; si < p.nseg; ++si) {
+        const RowSeg &s = p.seg[si];
+        if (s.C % 64 || s.C > s.ld) return;
+        const uint64_t dims[4] = {(uint64_t)s.C, (uint64_t)p.W, (uint64_t)nwin, s.boff ? 2u : 1u};
+        const uint64_t strides[3] = {(uint64_t)s.ld * 2, (uint64_t)p.W * s.ld * 2,
+                                     (uint64_t)(s.boff ? s.boff : nwin * p.W * s.ld) * 2};
+        if (!encode_bf16_map(&p.a_map[si], s.p, 4, dims, strides, kRows)) return;
+        p.a_nb[si] = s.boff ? 2 : 1;
+    }
+    p.a_tma = 1;
+}
+
+template <int EPI>
+gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
+    make_rows_tma(p);
+    const int64_t tpb = (p.rows + kRows - 1) / kRows;
+    p.n_tiles = tpb * p.nbranch;
+    if (p.bn < p.N) p.bn = p.N;
+    // at least 80 KB of shared memory per CTA, so that at most two CTAs (2 x <= 256 TMEM columns)
+    // share an SM and no TMEM allocation has to wait; the conv, residual and dz epilogues stage
+    // their stores per warp after the B image (dgrad, whose stages leave no room for it at two CTAs
+    // per SM, stores directly: staged at 48-byte pitch it measured no faster)
+    const size_t staging = EPI <= EPI_DZ ? (size_t)8 * kWarpStage : 0;
+    const size_t smem = std::max<size_t>((size_t)kRows * p.K * 2 + (size_t)p.bn * p.K * 2 + staging + 1024, 80 * 1024);
+    const int grid = (int)std::min<int64_t>(p.n_tiles, (int64_t)sms * (smem <= 100 * 1024 ? 2 : 1));
+    static const char *const kEpiName[6] = {"k_tc_rows:conv", "k_tc_rows:res",    "k_tc_rows:dz",
+                                            "k_tc_rows:dgrad", "k_tc_rows:head_u", "k_tc_rows:head_dh"};
+    ProfScope prof("k_tc_rows", st);
+    ProfScope prof_epi(kEpiName[EPI], st);
+    k_tc_rows<EPI><<<grid, 256, smem, st>>>(p);
+    note_launch();
+    GWE_CUDA_TRY(cudaGetLastError());
+    return GWE_OK;
 }
 
 // The tensor-map form of a weight-gradient GEMM, when its shapes allow one: 64 or 128 channels of
@@ -1082,7 +1137,7 @@ bool make_wg_tma(const WgGemm &p, WgTma &t) {
     {
         const uint64_t dims[3] = {(uint64_t)p.M, (uint64_t)p.rows, p.g_boff ? 2u : 1u};
         const uint64_t strides[2] = {(uint64_t)p.ldg * 2, (uint64_t)(p.g_boff ? p.g_boff : p.rows * p.ldg) * 2};
-        if (!encode_bf16_map(&t.g_map, p.G, 3, dims, strides)) return false;
+        if (!encode_bf16_map(&t.g_map, p.G, 3, dims, strides, kTmaRows)) return false;
     }
     int csum = 0;
     for (int si = 0; si < p.nxs; ++si) {
@@ -1091,7 +1146,7 @@ bool make_wg_tma(const WgGemm &p, WgTma &t) {
         const uint64_t dims[4] = {(uint64_t)s.C, (uint64_t)p.W, (uint64_t)nwin, s.boff ? 2u : 1u};
         const uint64_t strides[3] = {(uint64_t)s.ld * 2, (uint64_t)p.W * s.ld * 2,
                                      (uint64_t)(s.boff ? s.boff : nwin * p.W * s.ld) * 2};
-        if (!encode_bf16_map(&t.x_map[si], s.p, 4, dims, strides)) return false;
+        if (!encode_bf16_map(&t.x_map[si], s.p, 4, dims, strides, kTmaRows)) return false;
         t.x_blocks[si] = s.C / 64;
         t.x_shift[si] = s.shift;
         t.x_nb[si] = s.boff ? 2 : 1;
