@@ -251,6 +251,29 @@ __device__ __forceinline__ void wst16_w(void *dst, const uint32_t (&w)[8], bool 
     }
     __syncwarp();
 }
+// The same through a narrower staging area (48-byte row pitch, 32 bytes per row and pass: eight
+// FP32 or sixteen 16-bit values), for the dgrad epilogue, whose tiles leave only 12 KB of shared
+// memory at two CTAs per SM; each store instruction writes whole sectors of 16 rows.
+constexpr uint32_t kWarpStageNarrow = 32 * 48;
+__device__ __forceinline__ void wst32b_p48(void *dst, uint4 lo, uint4 hi, bool live, uint32_t stg, int lane) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(stg + lane * 48), "r"(lo.x), "r"(lo.y), "r"(lo.z),
+                 "r"(lo.w)
+                 : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(stg + lane * 48 + 16), "r"(hi.x), "r"(hi.y),
+                 "r"(hi.z), "r"(hi.w)
+                 : "memory");
+    __syncwarp();
+    const unsigned long long d = reinterpret_cast<unsigned long long>(dst);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int rr = 16 * i + (lane >> 1), c = lane & 1;
+        const unsigned long long dr = __shfl_sync(0xffffffffu, d, rr);
+        const int lv = __shfl_sync(0xffffffffu, live ? 1 : 0, rr);
+        const uint4 x = lds128(stg + rr * 48 + c * 16);
+        if (lv) *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(dr) + 16 * c) = x;
+    }
+    __syncwarp();
+}
 __device__ __forceinline__ void pack16_bf16(const float (&v)[16], uint32_t (&w)[8]) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -285,7 +308,8 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const __grid_constant__ RowG
     const uint32_t a_bytes = (uint32_t)kRows * p.K * 2;   // B image follows the A tile
     uint8_t *sA = smem, *sB = smem + a_bytes;
     // epilogues with staged (coalesced) stores: a per-warp staging area after the B image
-    const uint32_t stg = smem_u32(smem + a_bytes + (uint32_t)p.bn * p.K * 2) + (tid >> 5) * kWarpStage;
+    const uint32_t stg = smem_u32(smem + a_bytes + (uint32_t)p.bn * p.K * 2) +
+                         (tid >> 5) * (EPI == EPI_DGRAD ? kWarpStageNarrow : kWarpStage);
     const int lane = tid & 31;
     const uint32_t ncols = tmem_cols_for(p.N);
     if (tid == 0) {
@@ -574,7 +598,6 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const __grid_constant__ RowG
                 uint32_t dr[16];
                 tmem_ld16(tl + c0, dr);
                 tmem_ld_wait();
-                if (!live) continue;
                 float v[16];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -583,8 +606,22 @@ __global__ void __launch_bounds__(256, 2) k_tc_rows(const __grid_constant__ RowG
                     v[4 * q + 2] = pa[4 * g + q].z + __uint_as_float(dr[4 * q + 2]);
                     v[4 * q + 3] = pa[4 * g + q].w + __uint_as_float(dr[4 * q + 3]);
                 }
-                st16_f32(p.o32 + b * p.o32_boff + row * R + c0, v);
-                st16_bf16(p.o16 + b * p.o16_boff + row * R + c0, v);
+                // staged: FP32 values 0-7, then 8-15, then the sixteen BF16 values
+                float *o32 = p.o32 + b * p.o32_boff + row * R + c0;
+                wst32b_p48(o32, make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]),
+                                           __float_as_uint(v[3])),
+                           make_uint4(__float_as_uint(v[4]), __float_as_uint(v[5]), __float_as_uint(v[6]),
+                                      __float_as_uint(v[7])),
+                           live, stg, lane);
+                wst32b_p48(o32 + 8, make_uint4(__float_as_uint(v[8]), __float_as_uint(v[9]), __float_as_uint(v[10]),
+                                               __float_as_uint(v[11])),
+                           make_uint4(__float_as_uint(v[12]), __float_as_uint(v[13]), __float_as_uint(v[14]),
+                                      __float_as_uint(v[15])),
+                           live, stg, lane);
+                uint32_t w[8];
+                pack16_bf16(v, w);
+                wst32b_p48(p.o16 + b * p.o16_boff + row * R + c0, make_uint4(w[0], w[1], w[2], w[3]),
+                           make_uint4(w[4], w[5], w[6], w[7]), live, stg, lane);
             }
         }
         // every thread's TMEM reads of this tile end before the next tile's MMA
@@ -1112,9 +1149,9 @@ gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
     // share an SM and no TMEM allocation has to wait; the conv, residual and dz epilogues stage
     // their stores per warp after the B image (dgrad, whose stages leave no room for it at two CTAs
     // per SM, stores directly: staged at 48-byte pitch it measured no faster)
-    const size_t staging = EPI <= EPI_DZ ? (size_t)8 * kWarpStage : 0;
+    const size_t staging = EPI <= EPI_DZ ? (size_t)8 * kWarpStage : (EPI == EPI_DGRAD ? (size_t)8 * kWarpStageNarrow : 0);
     const size_t smem = std::max<size_t>((size_t)kRows * p.K * 2 + (size_t)p.bn * p.K * 2 + staging + 1024, 80 * 1024);
-    const int grid = (int)std::min<int64_t>(p.n_tiles, (int64_t)sms * (smem <= 100 * 1024 ? 2 : 1));
+    const int grid = (int)std::min<int64_t>(p.n_tiles, (int64_t)sms * (smem <= 112 * 1024 ? 2 : 1));
     static const char *const kEpiName[6] = {"k_tc_rows:conv", "k_tc_rows:res",    "k_tc_rows:dz",
                                             "k_tc_rows:dgrad", "k_tc_rows:head_u", "k_tc_rows:head_dh"};
     ProfScope prof("k_tc_rows", st);
