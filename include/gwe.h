@@ -252,16 +252,34 @@ gwe_status gwe_forward_logits(gwe_model *model, const float *x_H, const float *x
  * gradients) as a BF16 tensor-core GEMM with FP32 accumulation on BF16 copies
  * of the FP32 weights, keeps dL/dx, the residual stream and the skip sums in
  * FP32, and uses the FP32 kernels for the head, the biases and the input
- * projection (windows in chunks of 64, about 8 GB of workspace per chunk);
- * its gradients differ from the FP32 ones by the BF16 rounding of the
- * operands.  Weight gradients are reduced with atomic additions, so their
- * summation order is not fixed.  The workspace is owned by the handle.
- * GWE_ERR_UNSUPPORTED for channel counts the kernels do not cover;
- * GWE_ERR_TIMEOUT if a device-side wait of the tensor-core kernels gave up.
+ * projection (windows in chunks of 128, about 13.5 GB of workspace per chunk
+ * for the 30-layer R = 64, S = 128, Hc = 256 model); the head's contractions
+ * run on the tensor cores too when Hc <= 256 and 2 S <= 256 (u with FP16
+ * operands as in the forward, dh with BF16 operands, dW_h1 from BF16 hi/lo
+ * splits of both operands); its gradients differ from the FP32 ones by the
+ * 16-bit rounding of the operands.  Weight gradients are reduced with atomic
+ * additions, so their summation order is not fixed.  The workspace is owned
+ * by the handle.  GWE_ERR_UNSUPPORTED for channel counts the kernels do not
+ * cover; GWE_ERR_TIMEOUT if a device-side wait of the tensor-core kernels
+ * gave up.
  */
 gwe_status gwe_backward(gwe_model *model, int model_index, const float *x_H, const float *x_L, int batch,
                         int window, const float *dlogit, float *grad_weights, float *grad_H, float *grad_L,
                         void *stream);
+
+/*
+ * Operand staging of the tensor-core backward's GEMMs, from now on
+ * (process-wide).  on = 1 (the default): the row GEMMs' A tiles and both
+ * operands of the weight-gradient GEMMs arrive by tensor-map copies
+ * (cp.async.bulk.tensor with the 128-byte swizzle) where the shapes allow
+ * (segments of a multiple of 64 channels; windows a multiple of 128 samples
+ * for the row GEMMs, of 64 for the weight gradients; 64 or 128 channels per
+ * weight-gradient operand); elsewhere, and everywhere with on = 0, per-thread
+ * 16-byte copies stage them.  Both give the same row-GEMM products, so
+ * dLoss/dstrain is the same bit for bit; the weight gradients differ only in
+ * the order of their atomic partial sums.  GWE_ERR_ARG unless on is 0 or 1.
+ */
+gwe_status gwe_set_tensor_map_copies(int on);
 
 /*
  * Ensemble forward over a batch of science segments of uneven length in one

@@ -25,6 +25,7 @@ __all__ = [
     "gwe_trigger_sweep", "gwe_trigger_sweep_segments", "gwe_forward", "gwe_forward_segments", "gwe_triggers_segments", "gwe_forward_logits", "gwe_backward", "gwe_triggers", "gwe_whiten", "gwe_whiten_ex", "GWE_PSD_MEAN", "GWE_PSD_MEDIAN", "gwe_last_error",
     "gwe_version", "gwe_sync", "gwe_set_cross_window_reuse", "gwe_forward_static",
     "gwe_plan_create", "gwe_plan_execute", "gwe_plan_shape", "gwe_set_slide_shape", "gwe_plan_destroy", "GWE_PLAN_AUTOTUNE",
+    "gwe_set_tensor_map_copies",
     "gwe_search_create", "gwe_search_run", "gwe_search_run_range", "gwe_search_chunks", "gwe_search_resumable",
     "gwe_search_destroy", "GWE_INPUT_F32", "GWE_INPUT_F16", "gwe_logits_autograd", "gwe_profile_enable", "gwe_profile_read", "Model", "TRIGGER_DTYPE",
 ]
@@ -121,6 +122,7 @@ def load():
             "gwe_plan_execute": (I, [P, P]),
             "gwe_plan_shape": (I, [P, P, P, P, P, P, P]),
             "gwe_set_slide_shape": (I, [I, I, I]),
+            "gwe_set_tensor_map_copies": (I, [I]),
             "gwe_plan_destroy": (None, [P]),
             "gwe_search_create": (I, [P, P, P]),
             "gwe_search_run": (I, [P, P, P, I64, I, P, I64, P, P]),
@@ -433,6 +435,12 @@ def gwe_set_slide_shape(window_tile: int = 4, offset_tile: int = 8, pieces_per_b
     without GWE_PLAN_AUTOTUNE), process-wide, from now on."""
     _check(load().gwe_set_slide_shape(int(window_tile), int(offset_tile), int(pieces_per_block)),
            "gwe_set_slide_shape")
+
+
+def gwe_set_tensor_map_copies(on: bool) -> None:
+    """Operand staging of the tensor-core backward's GEMMs, process-wide, from now on: tensor-map copies
+    where the shapes allow (True, the default) or per-thread copies everywhere (False)."""
+    _check(load().gwe_set_tensor_map_copies(1 if on else 0), "gwe_set_tensor_map_copies")
 
 
 def gwe_plan_destroy(plan: int) -> None:

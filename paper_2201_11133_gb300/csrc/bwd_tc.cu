@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -44,6 +45,8 @@ using namespace tc;
 constexpr int kRows = 128;              // rows per tile (the MMA's M)
 constexpr int kWgThreads = 512;         // weight-gradient GEMM: 4 threads per staged row
 constexpr uint64_t kWaitNs = 4000000000ull;
+// 1: operands by tensor-map copies where the shapes allow (gwe_set_tensor_map_copies)
+std::atomic<int> g_tma_copies{1};
 
 // one K-range of a row GEMM's A operand: columns [0, C) of a row-major BF16 array, taken at row
 // t + shift of the same window (zero outside [0, W))
@@ -1125,7 +1128,7 @@ bool encode_bf16_map(CUtensorMap *map, const void *base, int rank, const uint64_
 // the per-thread copies stage A in the chunk-column layout.
 void make_rows_tma(RowGemm &p) {
     p.a_tma = 0;
-    if (p.W % kRows || p.rows % p.W || p.rows >= (int64_t(1) << 31)) return;
+    if (!g_tma_copies.load() || p.W % kRows || p.rows % p.W || p.rows >= (int64_t(1) << 31)) return;
     const int64_t nwin = p.rows / p.W;
     for (int si = 0; si < p.nseg; ++si) {
         const RowSeg &s = p.seg[si];
@@ -1166,7 +1169,7 @@ gwe_status run_rows(RowGemm p, int sms, cudaStream_t st) {
 // G and of every segment, windows a multiple of kTmaRows, 16-byte aligned rows of dW.  Returns
 // false (and the caller takes the per-thread-copy kernel) otherwise.
 bool make_wg_tma(const WgGemm &p, WgTma &t) {
-    if (p.W % kTmaRows || p.rows % p.W || p.rows >= (int64_t(1) << 31) || (p.M != 64 && p.M != 128)) return false;
+    if (!g_tma_copies.load() || p.W % kTmaRows || p.rows % p.W || p.rows >= (int64_t(1) << 31) || (p.M != 64 && p.M != 128)) return false;
     if (p.nxs < 1 || p.nxs > 2 || p.N != p.nx + 16 || (p.nx != 64 && p.nx != 128)) return false;
     if ((reinterpret_cast<uintptr_t>(p.dW) & 15) || p.ldw % 4 || p.w_boff % 4) return false;
     std::memset(&t, 0, sizeof(t));
@@ -1680,3 +1683,10 @@ gwe_status tc_backward(gwe_model *m, void *&state, int mi, const float *xH, cons
 }
 
 }  // namespace gwe
+
+extern "C" gwe_status gwe_set_tensor_map_copies(int on) {
+    gwe::clear_error();
+    GWE_ARG_CHECK(on == 0 || on == 1, "on must be 0 or 1");
+    gwe::g_tma_copies.store(on);
+    return GWE_OK;
+}

@@ -269,3 +269,35 @@ def test_tc_backward_central_differences_of_handle_forward():
         print(f"central differences of the handle forward ({tag}): fd {fd:.6e} analytic {an:.6e} rel {rel:.2e}")
         assert rel <= tol, (tag, fd, an)
     m.close()
+
+
+def test_tensor_map_and_per_thread_staging_agree():
+    """The backward with its GEMM operands brought in by tensor-map copies (128-byte swizzled tiles, the
+    default) against the same backward with per-thread copies, on the 30-layer model with 1024-sample
+    windows, where every GEMM takes the tensor-map form: dL/dstrain bit for bit (the row GEMMs multiply
+    the same operands in the same K order), and the weight gradients within 1e-3 of each parameter
+    tensor's largest entry (their atomic partial sums come in another order; a misplaced tile would
+    move them by O(1))."""
+    import paper_2201_11133_gb300 as gwe
+    cfg = workload.config("ensemble", n_models=1)
+    wb = workload.init_weights(cfg, seed=3800, bias_std=0.1)
+    rng = np.random.default_rng(9)
+    B, W = 2, 1024
+    xh = rng.standard_normal((B, W)).astype(np.float32)
+    xl = rng.standard_normal((B, W)).astype(np.float32)
+    dlogit = (rng.standard_normal((B, W)) / (B * W)).astype(np.float32)
+    try:
+        gwe.gwe_set_tensor_map_copies(False)
+        pw, ph, pl = _grads(cfg, wb, xh, xl, dlogit, gwe.GWE_BF16)
+    finally:
+        gwe.gwe_set_tensor_map_copies(True)
+    tw, th, tl = _grads(cfg, wb, xh, xl, dlogit, gwe.GWE_BF16)
+    assert np.array_equal(th, ph) and np.array_equal(tl, pl)
+    worst = 0.0
+    for name, (o, sh) in workload.param_offsets(cfg).items():
+        n = int(np.prod(sh))
+        ref = pw[o:o + n]
+        e = float(np.max(np.abs(tw[o:o + n] - ref))) / max(float(np.max(np.abs(ref))), 1e-30)
+        worst = max(worst, e)
+        assert e <= 1e-3, (name, e)
+    print(f"tensor-map vs per-thread staging: dL/dstrain identical; weights worst per-tensor {worst:.2e}")
