@@ -881,6 +881,75 @@ __global__ void __launch_bounds__(256) k_wgrad(const BWg p) {
     if (do_bias && tid < BT && n0 + tid < p.N) atomicAdd(p.db + b * p.db_boff + n0 + tid, bacc);
 }
 
+// Weighted column sums of a row-major FP32 matrix, for the reductions with few outputs (dw_h2 and
+// db_h2; the input projection's gradients): out_w[n] += sum_r G[r][n] x[r], out_b[n] += sum_r G[r][n],
+// out_x += sum_r x[r] (each output optional), N a multiple of 4 up to 256, rows of G 16-byte aligned.
+// 256 threads = row lanes x N/4 float4 columns; a block sums a contiguous range of rows (loads of
+// several rows in flight per thread), adds its row lanes in shared memory and issues one atomic per
+// output.
+__global__ void __launch_bounds__(256) k_colsum(const float *__restrict__ G, int ldg, int N, const float *__restrict__ x,
+                                                int64_t rows, int64_t rows_per_block, float *out_w, float *out_b,
+                                                float *out_x) {
+    __shared__ float4 sw[256], sb[256];
+    __shared__ float sx[256];
+    const int NQ = N / 4, RP = 256 / NQ;
+    const int tid = threadIdx.x, q = tid % NQ, rl = tid / NQ;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(rows, r0 + rows_per_block);
+    float4 aw = make_float4(0.f, 0.f, 0.f, 0.f), ab = aw;
+    float ax = 0.f;
+    if (rl < RP) {
+#pragma unroll 4
+        for (int64_t r = r0 + rl; r < r1; r += RP) {
+            const float4 g = __ldg(reinterpret_cast<const float4 *>(G + r * ldg) + q);
+            const float xv = x ? __ldg(x + r) : 0.f;
+            aw.x = fmaf(g.x, xv, aw.x);
+            aw.y = fmaf(g.y, xv, aw.y);
+            aw.z = fmaf(g.z, xv, aw.z);
+            aw.w = fmaf(g.w, xv, aw.w);
+            ab.x += g.x;
+            ab.y += g.y;
+            ab.z += g.z;
+            ab.w += g.w;
+            ax += xv;
+        }
+    }
+    sw[tid] = aw;
+    sb[tid] = ab;
+    sx[tid] = (rl < RP && q == 0) ? ax : 0.f;
+    __syncthreads();
+    if (tid < NQ) {
+        float4 w = sw[tid], bsum = sb[tid];
+        for (int k = 1; k < RP; ++k) {
+            const float4 a = sw[k * NQ + tid], c = sb[k * NQ + tid];
+            w.x += a.x;
+            w.y += a.y;
+            w.z += a.z;
+            w.w += a.w;
+            bsum.x += c.x;
+            bsum.y += c.y;
+            bsum.z += c.z;
+            bsum.w += c.w;
+        }
+        if (out_w) {
+            atomicAdd(out_w + 4 * tid, w.x);
+            atomicAdd(out_w + 4 * tid + 1, w.y);
+            atomicAdd(out_w + 4 * tid + 2, w.z);
+            atomicAdd(out_w + 4 * tid + 3, w.w);
+        }
+        if (out_b) {
+            atomicAdd(out_b + 4 * tid, bsum.x);
+            atomicAdd(out_b + 4 * tid + 1, bsum.y);
+            atomicAdd(out_b + 4 * tid + 2, bsum.z);
+            atomicAdd(out_b + 4 * tid + 3, bsum.w);
+        }
+    }
+    if (out_x && tid == 0) {
+        float t = 0.f;
+        for (int k = 0; k < RP; ++k) t += sx[k * NQ];
+        atomicAdd(out_x, t);
+    }
+}
+
 // x_0 = w_in s + b_in for both branches; rows of branch b follow branch b-1
 __global__ void k_input_proj(const float *__restrict__ sH, const float *__restrict__ sL,
                              const float *__restrict__ blob, int64_t Pb, int R, int64_t rows, float *__restrict__ x0) {
@@ -920,6 +989,18 @@ void launch_wgrad(const BWg &p, int nbranch, cudaStream_t st) {
     ProfScope prof("k_wgrad", st);
     k_wgrad<<<grid, 256, 0, st>>>(p);
     note_launch();
+}
+
+// k_colsum where the shapes allow it (N a multiple of 4 up to 256, 16-byte aligned rows); false otherwise
+bool launch_colsum(const float *G, int ldg, int N, const float *x, int64_t rows, float *out_w, float *out_b,
+                   float *out_x, cudaStream_t st) {
+    if (N <= 0 || N % 4 || N > 256 || ldg % 4 || (reinterpret_cast<uintptr_t>(G) & 15) || rows <= 0) return false;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(1024, rows / 512));
+    const int64_t rpb = (rows + blocks - 1) / blocks;
+    ProfScope prof("k_wgrad", st);
+    k_colsum<<<(unsigned)blocks, 256, 0, st>>>(G, ldg, N, x, rows, rpb, out_w, out_b, out_x);
+    note_launch();
+    return true;
 }
 
 BWg wg(const float *G, int ldg, int N, int64_t g_boff, const float *X, int ldx, int K, int shift, int64_t x_boff,
@@ -1028,13 +1109,15 @@ gwe_status fp32_head_backward(gwe_model *m, int mi, const float *skip, int64_t r
 }
 
 // the head's second layer: dw_h2 = sum over rows of dlogit ReLU(u + b_h1), db_h2 = sum of dlogit
-// (ru = ReLU(u + b_h1) [row][Hc], one launch each)
+// (ru = ReLU(u + b_h1) [row][Hc]; one pass over ru, or one launch each for widths k_colsum does not take)
 gwe_status fp32_head_w2_grad(gwe_model *m, const float *ru, int W, int C, const float *dlogit, float *gw,
                              cudaStream_t st) {
     const Dims &d = m->dims;
     const int Hc = d.Hc;
-    launch_wgrad(wide(wg(ru, Hc, Hc, 0, dlogit, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, C)), 1, st);
-    launch_wgrad(wide(wg(dlogit, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W, C)), 1, st);
+    if (!launch_colsum(ru, Hc, Hc, dlogit, (int64_t)C * W, gw + off_wh2(d), nullptr, gw + off_bh2(d), st)) {
+        launch_wgrad(wide(wg(ru, Hc, Hc, 0, dlogit, 1, 1, 0, 0, gw + off_wh2(d), 1, 0, nullptr, 0, W, C)), 1, st);
+        launch_wgrad(wide(wg(dlogit, 1, 1, 0, nullptr, 0, 0, 0, 0, nullptr, 0, 0, gw + off_bh2(d), 0, W, C)), 1, st);
+    }
     GWE_CUDA_TRY(cudaGetLastError());
     return GWE_OK;
 }
@@ -1051,12 +1134,15 @@ gwe_status fp32_input_backward(gwe_model *m, int mi, const float *dx0, int64_t r
     const Dims &d = m->dims;
     const int R = d.R;
     const float *blob = m->w32.as<float>() + (int64_t)mi * d.P;
-    launch_wgrad(wide(wg(dx0, R, R, 0, sH, 1, 1, 0, 0, gw + off_branch(d, 0), 1, 0, gw + off_branch(d, 0) + R, 0, W,
-                         C)),
-                 1, st);
-    launch_wgrad(wide(wg(dx0 + rb * R, R, R, 0, sL, 1, 1, 0, 0, gw + off_branch(d, 1), 1, 0, gw + off_branch(d, 1) + R,
-                         0, W, C)),
-                 1, st);
+    // dw_in = sum_r dx_0[r] s[r], db_in = sum_r dx_0[r], per branch
+    if (!launch_colsum(dx0, R, R, sH, rb, gw + off_branch(d, 0), gw + off_branch(d, 0) + R, nullptr, st))
+        launch_wgrad(wide(wg(dx0, R, R, 0, sH, 1, 1, 0, 0, gw + off_branch(d, 0), 1, 0, gw + off_branch(d, 0) + R, 0,
+                             W, C)),
+                     1, st);
+    if (!launch_colsum(dx0 + rb * R, R, R, sL, rb, gw + off_branch(d, 1), gw + off_branch(d, 1) + R, nullptr, st))
+        launch_wgrad(wide(wg(dx0 + rb * R, R, R, 0, sL, 1, 1, 0, 0, gw + off_branch(d, 1), 1, 0,
+                             gw + off_branch(d, 1) + R, 0, W, C)),
+                     1, st);
     const unsigned nb = (unsigned)((rb + 7) / 8);
     if (gH) {
         k_dstrain<<<nb, 256, 0, st>>>(dx0, blob + off_branch(d, 0), R, rb, gH);
