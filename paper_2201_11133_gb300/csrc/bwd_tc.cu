@@ -297,7 +297,9 @@ __device__ __forceinline__ void pack16_f16(const float (&v)[16], uint32_t (&w)[8
 // epilogue's channels (TMEM lanes of warp w: 32 (w % 4) ..).  Per tile the epilogue's global
 // operands are loaded into registers before the MMA is waited for, and the next tile's A copies
 // (and B image, at a branch change) are issued as soon as the MMA has read shared memory, so that
-// they are in flight while the epilogue runs.
+// they are in flight while the epilogue runs.  With p.a_tma thread 0 issues the A tile as
+// tensor-map boxes (one per 64-channel block, 128-byte swizzle, completion on bar[2]) and waits for
+// them before the MMAs; otherwise every thread stages its share with 16-byte copies.
 template <int EPI>
 __global__ void __launch_bounds__(256, 2) k_tc_rows(const __grid_constant__ RowGemm p) {
     extern __shared__ uint8_t smem_raw[];
